@@ -15,9 +15,11 @@ readings coincide for a == 1. A is symmetric positive definite.
 Section 3.3 ("eigs_1D") factorizes A_l = V_l diag(lambda^(l)) V_l^T with the
 eigenvectors as the columns of the orthogonal V_l; the 3D operator is the
 Kronecker sum A = A_1 (+) A_2 (+) A_3 ("eqn_low_rank_lap").
-Eigenvector signs are arbitrary; the oracle fixes them so that the first
-component of every column is positive (it is nonzero for an irreducible
-tridiagonal matrix).
+Eigenvector signs are arbitrary; the oracle fixes each column v so that
+sum_i v_i g_i > 0 with the fixed weights g_i = 2 frac(i * 0.6180339887498949) - 1
+(i = 1..n, a Weyl sequence). The first entry is not used because high modes
+of a variable-coefficient operator localize and their first entry can
+underflow; the weighted sum is of order one for every column.
 """
 from __future__ import annotations
 
@@ -29,6 +31,7 @@ __all__ = [
     "dense",
     "eig",
     "normalise_signs",
+    "sign_weights",
     "stencil_apply",
     "kron_sum_dense",
 ]
@@ -58,9 +61,16 @@ def dense(d: np.ndarray, e: np.ndarray) -> np.ndarray:
     return np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
 
 
+def sign_weights(n: int) -> np.ndarray:
+    """g_i = 2 frac(i * 0.6180339887498949) - 1, i = 1..n."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return 2.0 * np.mod(i * 0.6180339887498949, 1.0) - 1.0
+
+
 def normalise_signs(V: np.ndarray) -> np.ndarray:
-    """Flip columns so that V[0, k] > 0 for every k."""
-    s = np.where(V[0, :] < 0.0, -1.0, 1.0)
+    """Flip columns so that sum_i V[i, k] g_i > 0 for every k."""
+    d = sign_weights(V.shape[0]) @ V
+    s = np.where(d < 0.0, -1.0, 1.0)
     return V * s[None, :]
 
 

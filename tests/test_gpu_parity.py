@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Every input is seeded and synthetic (paper_2006_09314_gb300.inputs). Every
+expected value is computed by oracle/ on the same inputs.
+
+Tolerances (derived from the arithmetic):
+  * eigenvalues: backward-stable solvers, |dlambda| <= c n eps ||A||  -> 1e-13 ||A||;
+  * eigenvectors: angle <= eps ||A|| / gap (min relative gap ~6e-4 at n=2048) -> 5e-9;
+  * full-grid solve (no truncation, FP64): 1e-10 relative L2;
+  * single applies / truncation: eps_trunc (1e-6) + separable F2 error (1e-8);
+  * PCG: 1e-5 relative L2 (10 eps_trunc), and 1e-6 as the solve-quality target.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import expsum as es
+from oracle import formats as F
+from oracle import fullgrid as fg
+from oracle import operator as op
+from oracle import truncation as otr
+from paper_2006_09314_gb300.inputs import make_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # the marker deselects these on CPU hosts
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2006_09314_gb300 import tensorctl as T  # noqa: E402
+
+
+def _oracle_eigs(pr):
+    lams, Vs = [], []
+    for l in range(3):
+        lam, V = op.eig(*op.assemble(pr.coeffs[l]))
+        lams.append(lam)
+        Vs.append(V)
+    return lams, Vs
+
+
+def _full_from_gpu(x: "T.CP"):
+    w, U = x.to_numpy()
+    return F.cp_full(w, U)
+
+
+# ------------------------------------------------------------------ eigenbasis
+@pytest.mark.parametrize("n", [8, 33, 257, 1024])
+def test_eigs_match_lapack(n):
+    pr = make_problem(n, 0.5, 1e-2, 1, 200 + n)
+    lams, Vs = _oracle_eigs(pr)
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6) as ctx:
+        for l in range(3):
+            lam, V = ctx.eigs(l)
+            assert np.max(np.abs(lam - lams[l])) <= 1e-13 * lams[l].max()
+            assert np.max(np.abs(V - Vs[l])) <= 5e-9
+            assert np.max(np.abs(V.T @ V - np.eye(n))) <= 5e-9
+
+
+def test_eigs_laplacian_closed_form():
+    n = 100
+    coeffs = np.ones((3, n + 1))
+    h = 1.0 / (n + 1)
+    k = np.arange(1, n + 1)
+    with T.Context(coeffs, n, 0.5, 1e-2, 1e-6) as ctx:
+        lam, V = ctx.eigs(0)
+    cf = 4.0 / h ** 2 * np.sin(k * math.pi * h / 2) ** 2
+    assert np.max(np.abs(lam - cf)) <= 1e-13 * cf.max()
+    x = np.arange(1, n + 1) * h
+    Vcf = math.sqrt(2 * h) * np.sin(np.outer(x, k) * math.pi)
+    Vcf *= np.where(op.sign_weights(n) @ Vcf < 0, -1.0, 1.0)[None, :]
+    assert np.max(np.abs(V - Vcf)) <= 1e-10
+
+
+def test_paper_end_rows_option():
+    n = 24
+    pr = make_problem(n, 0.5, 1e-2, 1, 7)
+    o = T.tctl_default_opts(paper_end_rows=1)
+    lam_o, _ = op.eig(*op.assemble(pr.coeffs[1], paper_end_rows=True))
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6, opts=o) as ctx:
+        lam, _ = ctx.eigs(1)
+    assert np.max(np.abs(lam - lam_o)) <= 1e-13 * lam_o.max()
+
+
+# ------------------------------------------------------------------ full grid
+@pytest.mark.parametrize("n,alpha,beta", [(16, 0.5, 1e-2), (33, 0.25, 1e-4), (64, 0.75, 1.0),
+                                          (70, 1.0, 1e-2)])
+def test_fullgrid_solve_matches_oracle(n, alpha, beta):
+    pr = make_problem(n, alpha, beta, 5, 300 + n)
+    lams, Vs = _oracle_eigs(pr)
+    Y = F.cp_full(pr.yw, pr.yU)
+    ustar = fg.solve_exact(Y, lams, Vs, alpha, beta)
+    with T.Context(pr.coeffs, n, alpha, beta, 1e-6) as ctx:
+        yd = torch.from_numpy(np.asfortranarray(Y).reshape(-1, order="F")).cuda()
+        u = ctx.fullgrid_solve(yd).cpu().numpy().reshape((n, n, n), order="F")
+        assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) <= 1e-10
+        st = ctx.fullgrid_state(torch.from_numpy(np.asfortranarray(ustar).reshape(-1, order="F")).cuda())
+        st = st.cpu().numpy().reshape((n, n, n), order="F")
+        ref = fg.state_exact(ustar, lams, Vs, alpha)
+        assert np.linalg.norm(st - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+# ------------------------------------------------------------------ truncation
+@pytest.mark.parametrize("n,R,eps", [(20, 30, 1e-6), (37, 12, 1e-3), (48, 60, 1e-8)])
+def test_truncate_error_bound_and_oracle(n, R, eps):
+    rng = np.random.default_rng(400 + n)
+    w = np.exp(-0.8 * np.arange(R)) * rng.choice([-1.0, 1.0], R)
+    U = [rng.standard_normal((n, R)) for _ in range(3)]
+    X = F.cp_full(w, U)
+    pr = make_problem(n, 0.5, 1e-2, 1, 1)
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6) as ctx:
+        y = ctx.truncate(T.CP.from_numpy(w, U), eps)
+    Yg = _full_from_gpu(y)
+    err = np.linalg.norm(Yg - X) / np.linalg.norm(X)
+    assert err <= eps
+    ow, oU = otr.trunc(w, U, eps)
+    assert np.linalg.norm(Yg - F.cp_full(ow, oU)) <= 2 * eps * np.linalg.norm(X)
+
+
+def test_truncate_recovers_exact_tucker_rank_and_in_place():
+    rng = np.random.default_rng(5)
+    n = 30
+    Q = [np.linalg.qr(rng.standard_normal((n, r)))[0] for r in (2, 3, 4)]
+    core = rng.standard_normal((2, 3, 4))
+    X = F.tucker_full(core, Q)
+    w, U = [], [[], [], []]
+    for a in range(2):
+        for b in range(3):
+            for c in range(4):
+                w.append(core[a, b, c])
+                U[0].append(Q[0][:, a]); U[1].append(Q[1][:, b]); U[2].append(Q[2][:, c])
+    U = [np.array(u).T for u in U]
+    pr = make_problem(n, 0.5, 1e-2, 1, 1)
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6) as ctx:
+        x = T.CP.from_numpy(np.array(w), U, cap=64)
+        y = ctx.truncate(x, 1e-10)
+        assert y.rank <= 2 * 4
+        assert np.linalg.norm(_full_from_gpu(y) - X) <= 1e-11 * np.linalg.norm(X)
+        # in place: y = x
+        s = x._struct()
+        code = T.load().tctl_truncate(ctx.handle, T.ctypes.byref(s), T.ctypes.byref(s), 1e-10)
+        assert code == 0
+        x.rank = s.rank
+        assert np.linalg.norm(_full_from_gpu(x) - X) <= 1e-11 * np.linalg.norm(X)
+
+
+# ------------------------------------------------------------------ applies
+@pytest.mark.parametrize("n,alpha,beta", [(32, 0.5, 1e-2), (29, 0.25, 1e-4), (40, 0.75, 1.0),
+                                          (24, 1.0, 1e-2)])
+def test_apply_op_matches_oracle(n, alpha, beta):
+    pr = make_problem(n, alpha, beta, 3, 500 + n)
+    lams, Vs = _oracle_eigs(pr)
+    S = fg.spectral_sum(lams)
+    X = F.cp_full(pr.yw, pr.yU)
+    exact = fg.apply_spectral(fg.F2(S, alpha, beta), X, Vs)
+    rep = es.F2_expsum(alpha, beta, S.min(), S.max(), 1e-8)
+    sep = fg.apply_spectral(es.F2_expsum_eval(rep, S.ravel()).reshape(S.shape), X, Vs)
+    with T.Context(pr.coeffs, n, alpha, beta, 1e-6) as ctx:
+        st = ctx.stats()
+        assert st["op_rank"] == len(rep["t1"]) + 3 * max(len(rep["t2"]), 1)
+        y = ctx.apply_op(T.CP.from_numpy(pr.yw, pr.yU))
+    Yg = _full_from_gpu(y)
+    nrm = np.linalg.norm(exact)
+    assert np.linalg.norm(Yg - sep) <= 1.1e-6 * nrm
+    assert np.linalg.norm(Yg - exact) <= 1.2e-6 * nrm
+
+
+@pytest.mark.parametrize("n,alpha,beta", [(32, 0.5, 1e-2), (27, 0.75, 1.0)])
+def test_apply_precond_matches_oracle(n, alpha, beta):
+    pr = make_problem(n, alpha, beta, 3, 600 + n)
+    lams, Vs = _oracle_eigs(pr)
+    S = fg.spectral_sum(lams)
+    X = F.cp_full(pr.yw, pr.yU)
+    th, p = es.precond_expsum(alpha, beta, S.min(), S.max(), 24)
+    Pv = es.precond_eval(th, p, S.ravel()).reshape(S.shape)
+    ref = fg.apply_spectral(Pv, X, Vs)
+    with T.Context(pr.coeffs, n, alpha, beta, 1e-6) as ctx:
+        y = ctx.apply_precond(T.CP.from_numpy(pr.yw, pr.yU))
+    Yg = _full_from_gpu(y)
+    # two independent NNLS fits of the same problem: weights may differ slightly
+    assert np.linalg.norm(Yg - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+# ------------------------------------------------------------------ PCG solve
+def _pcg_case(n, alpha, beta, rank, seed, basis=1, eps=1e-6):
+    pr = make_problem(n, alpha, beta, rank, seed)
+    lams, Vs = _oracle_eigs(pr)
+    ustar = fg.solve_exact(F.cp_full(pr.yw, pr.yU), lams, Vs, alpha, beta)
+    o = T.tctl_default_opts(basis=basis)
+    with T.Context(pr.coeffs, n, alpha, beta, eps, opts=o) as ctx:
+        x, st, code = ctx.pcg_solve(T.CP.from_numpy(pr.yw, pr.yU))
+        launches = ctx.launch_count()
+    u = _full_from_gpu(x)
+    return np.linalg.norm(u - ustar) / np.linalg.norm(ustar), st, launches
+
+
+def test_pcg_small_config():
+    """n = 32, alpha = 0.5, beta = 1e-2, design rank 3, eps = 1e-6."""
+    err, st, launches = _pcg_case(32, 0.5, 1e-2, 3, 0)
+    assert st["rel_res"] <= 1e-7
+    assert err <= 1e-6, (err, st)
+    assert launches > 0
+
+
+@pytest.mark.parametrize("n,alpha,beta", [(33, 0.25, 1e-4), (40, 0.75, 1.0), (24, 1.0, 1e-2),
+                                          (48, 0.1, 1.0)])
+def test_pcg_matches_exact(n, alpha, beta):
+    err, st, _ = _pcg_case(n, alpha, beta, 5, 700 + n)
+    assert err <= 1e-5, (err, st)
+
+
+def test_pcg_paper_form_basis0_agrees():
+    e1, s1, _ = _pcg_case(30, 0.5, 1e-2, 3, 11, basis=1)
+    e0, s0, _ = _pcg_case(30, 0.5, 1e-2, 3, 11, basis=0)
+    assert e0 <= 1e-5 and e1 <= 1e-5
+    assert abs(s0["iters"] - s1["iters"]) <= 1
+
+
+def test_solve_host_buffers():
+    n, alpha, beta = 26, 0.5, 1e-2
+    pr = make_problem(n, alpha, beta, 3, 13)
+    lams, Vs = _oracle_eigs(pr)
+    ustar = fg.solve_exact(F.cp_full(pr.yw, pr.yU), lams, Vs, alpha, beta)
+    uw, uU, st = T.tctl_solve_host(pr.coeffs, n, alpha, beta, 1e-6, pr.yw, pr.yU)
+    assert np.linalg.norm(F.cp_full(uw, uU) - ustar) <= 1e-5 * np.linalg.norm(ustar)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_edge_cases_and_errors():
+    n = 12
+    pr = make_problem(n, 0.5, 1e-2, 2, 17)
+    with pytest.raises(T.TctlError) as ei:
+        T.tctl_setup(pr.coeffs, n, 0.0, 1e-2, 1e-6)
+    assert ei.value.code == -1
+    bad = pr.coeffs.copy()
+    bad[1, 3] = -0.1
+    with pytest.raises(T.TctlError) as ei:
+        T.tctl_setup(bad, n, 0.5, 1e-2, 1e-6)
+    assert ei.value.code == -2
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6) as ctx:
+        # empty right-hand side -> empty solution
+        z = T.CP(n, 4)
+        x, st, code = ctx.pcg_solve(z)
+        assert code == 0 and x.rank == 0
+        # rank capacity too small
+        b = T.CP.from_numpy(pr.yw, pr.yU)
+        with pytest.raises(T.TctlError) as ei:
+            ctx.apply_op(b, cap=1)
+        assert ei.value.code == -5
+    o = T.tctl_default_opts(max_iter=1, pcg_rtol=1e-14, r_pre=2)
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6, opts=o) as ctx:
+        x, st, code = ctx.pcg_solve(T.CP.from_numpy(pr.yw, pr.yU), check=False)
+        assert code == -6 and st["iters"] == 1 and x.rank > 0
+
+
+def test_minimum_size_n2():
+    n = 2
+    pr = make_problem(n, 0.5, 1e-2, 1, 19)
+    lams, Vs = _oracle_eigs(pr)
+    ustar = fg.solve_exact(F.cp_full(pr.yw, pr.yU), lams, Vs, 0.5, 1e-2)
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6) as ctx:
+        x, st, code = ctx.pcg_solve(T.CP.from_numpy(pr.yw, pr.yU))
+    assert np.linalg.norm(_full_from_gpu(x) - ustar) <= 1e-5 * np.linalg.norm(ustar)
