@@ -1,0 +1,177 @@
+/*
+ * tensorctl — C ABI of the GPU solver for the control equation of the tensor
+ * method for optimal control constrained by a fractional 3D elliptic operator
+ * with separable variable coefficients (arXiv 2006.09314).
+ *
+ * The library solves, on one GPU, the discrete control equation
+ *
+ *     F2(A) u = y_Omega,   F2(A) = A^-alpha + beta A^alpha                  (1)
+ *
+ * (Section 3.1, eq. "Lagrange_cont", with the paper's beta_p = 1 and
+ * gamma = beta; a general (beta_p, gamma) pair maps to beta = gamma/beta_p^2
+ * and u_paper = u/beta_p), where A = A_1 (+) A_2 (+) A_3 is the Kronecker sum
+ * of the 1D finite-difference Sturm-Liouville matrices of Section 3.2 on n
+ * interior points per axis (h = 1/(n+1)), by rank-truncated preconditioned CG
+ * (Appendix 2, Algorithm 1) in the eigenbasis of the three 1D operators
+ * (Section 3.3, eqs. "DiagGen", "DiagKron3D").
+ *
+ * Conventions shared by every entry point
+ *   - Return value: TCTL_OK (0) or a negative TCTL_E_* code. No exception
+ *     crosses the ABI; the library never exits, aborts or traps on the device.
+ *     tctl_last_error() returns a message for the last failing call.
+ *   - All work of a context is ordered on the CUDA stream given at setup.
+ *   - Canonical tensors (tctl_cp) live in DEVICE memory and are owned by the
+ *     caller (tctl_cp_alloc/tctl_cp_free are conveniences). Factor matrices
+ *     are column-major with leading dimension n: U[l][i + k*n] is entry i of
+ *     the factor of term k in mode l. Used terms: 0..rank-1 <= cap.
+ *   - Full-grid arrays are DEVICE n^3 arrays with x1 fastest:
+ *     y[i1 + n*i2 + n*n*i3].
+ *   - Inputs and outputs must not alias, except where stated.
+ *   - The context owns everything it allocates and frees it in tctl_destroy.
+ */
+#ifndef TENSORCTL_H
+#define TENSORCTL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TCTL_OK = 0,
+  TCTL_E_ARG = -1,          /* invalid argument (sizes, pointers, ranges)        */
+  TCTL_E_COEFF = -2,        /* a coefficient a_l(x) <= 0 or not finite           */
+  TCTL_E_CUDA = -3,         /* a CUDA runtime call failed                        */
+  TCTL_E_NOMEM = -4,        /* device allocation failed                          */
+  TCTL_E_RANK_CAP = -5,     /* output rank exceeded a capacity; result is capped */
+  TCTL_E_NOT_CONVERGED = -6,/* PCG reached max_iter; x holds the last iterate    */
+  TCTL_E_NAN = -7,          /* a NaN/Inf appeared in a reduction                 */
+  TCTL_E_NUMERIC = -8       /* a numerical kernel failed (e.g. no convergence)   */
+};
+
+typedef struct tctl_ctx tctl_ctx;
+
+/* Canonical tensor T = sum_k w[k] U[0][:,k] x U[1][:,k] x U[2][:,k]
+ * (Appendix 1, "CP_form"), DEVICE memory, caller-owned. */
+typedef struct {
+  int n[3];      /* mode sizes (all equal to the context's n)        */
+  int rank;      /* number of terms in use                           */
+  int cap;       /* allocated number of terms                        */
+  double *w;     /* [cap] weights                                    */
+  double *U[3];  /* U[l]: n[l] x cap, column-major, leading dim n[l] */
+} tctl_cp;
+
+typedef struct {
+  double pcg_rtol;    /* stop when ||R_k|| <= pcg_rtol ||B|| (default 1e-7)          */
+  int max_iter;       /* Algorithm 1's k_max (default 100)                            */
+  double op_tol;      /* target max relative error of the separable F2 on the
+                         spectral interval (default 1e-8)                              */
+  int r_pre;          /* nodes of the preconditioner exp-sum (default 24)             */
+  int rank_cap;       /* maximal Tucker rank per mode inside the solver (default and
+                         maximum 64)                                                  */
+  int precision;      /* 0 = FP64 (only value implemented)                            */
+  int basis;          /* 1 = PCG vectors kept in eigenbasis coordinates (default);
+                         0 = paper form, mode products with V_l in every apply         */
+  int expsum_src;     /* 0 = sinc quadrature (only value implemented)                 */
+  int paper_end_rows; /* 1 = the paper's printed end rows of A_(l) (default 0)        */
+  double eps_final;   /* truncation of the returned solution; <= 0 means eps/10       */
+  unsigned long long seed; /* seed of the sketching random numbers (default 1)       */
+} tctl_opts;
+
+typedef struct {
+  int iters;             /* PCG iterations performed                                 */
+  double rel_res;        /* final recursive ||R||/||B||                               */
+  int rank_x[3];         /* Tucker ranks of the solution before the final T2C         */
+  int max_rank;          /* largest Tucker rank met inside the iteration              */
+  int op_rank;           /* canonical rank R of the separable F2                      */
+  int op_basis[3];       /* per-mode compressed operator basis size                   */
+  int pre_rank;          /* canonical rank of the preconditioner                      */
+  double op_rel_err;     /* measured max rel. error of the separable F2 (sample)      */
+  double s_min, s_max;   /* spectral interval of A                                    */
+  double t_setup_ms;     /* time of tctl_setup                                       */
+  double t_solve_ms;     /* time of the last tctl_pcg_solve                          */
+} tctl_stats;
+
+/* Fills *o with the defaults listed above. */
+int tctl_default_opts(tctl_opts *o);
+
+/* Builds the solver for one coefficient set (Sections 3.2-3.5):
+ * assembles A_(l) from coeffs (HOST, 3 x (n+1) doubles, row l holds
+ * a_l(x_{i-1/2}) for i = 1..n+1), computes the 1D eigenpairs on the GPU in
+ * FP64, the spectral interval, the sinc exp-sum of F2 (Section 3.4) and the
+ * preconditioner exp-sum (Section 3.5, case (B)), and their factor matrices.
+ * n >= 2, 0 < alpha <= 1, beta > 0, eps_trunc in (0, 1). opts may be NULL.
+ * cuda_stream: a cudaStream_t (NULL = default stream). Synchronizes once.
+ * Errors: TCTL_E_ARG, TCTL_E_COEFF, TCTL_E_NOMEM, TCTL_E_CUDA, TCTL_E_NUMERIC. */
+int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha,
+               double beta, double eps_trunc, const tctl_opts *opts,
+               void *cuda_stream);
+
+/* y = trunc(F2(A) x, eps_trunc) with the separable F2 (eq. "Gen3DtimesX").
+ * x, y: canonical, physical (grid) coordinates. y->cap must hold the result
+ * (TCTL_E_RANK_CAP otherwise, y then holds the first y->cap terms). */
+int tctl_apply_op(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y);
+
+/* y = trunc(P(A) x, eps_trunc), P ~ F2^-1 the preconditioner (Section 3.5 (B)). */
+int tctl_apply_precond(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y);
+
+/* y = trunc(x, eps) (Appendix 1: canonical-to-Tucker by reduced HOSVD, core
+ * truncation, Tucker-to-canonical). ||x - y|| <= eps ||x||. y may equal x. */
+int tctl_truncate(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, double eps);
+
+/* Solves (1) for b = y_Omega by Algorithm 1 (Appendix 2). x: output
+ * (canonical, physical coordinates; any input content is ignored, X0 = 0).
+ * st may be NULL. Errors: TCTL_E_NOT_CONVERGED (x holds the last iterate),
+ * TCTL_E_RANK_CAP, TCTL_E_NAN, TCTL_E_CUDA. */
+int tctl_pcg_solve(tctl_ctx *ctx, const tctl_cp *b, tctl_cp *x, tctl_stats *st);
+
+/* Exact full-grid solve u = (xV)[((xV^T) y) ./ F2(lambda_i+lambda_j+lambda_k)]
+ * (Sections 3.3-3.4, "DiagFGen2D"), six dense mode products and the
+ * pointwise spectral divide. y, u: DEVICE n^3 arrays (x1 fastest), must not
+ * alias. Uses 2 n^3 doubles of context workspace (allocated on first use). */
+int tctl_fullgrid_solve(tctl_ctx *ctx, const double *y, double *u);
+
+/* State equation ("State"): y = A^-alpha u on the full grid (DEVICE n^3). */
+int tctl_fullgrid_state(tctl_ctx *ctx, const double *u, double *y);
+
+/* One-shot solve from HOST buffers: setup, host-to-device copies, PCG,
+ * device-to-host copy of the canonical solution, teardown. coeffs as in
+ * tctl_setup; yw (S) and yU (3 x n x S, mode-major, column-major per mode)
+ * the canonical y_Omega; uw (cap) and uU (3 x n x cap) receive the solution,
+ * *u_rank its rank. Returns the same codes as tctl_pcg_solve. */
+int tctl_solve_host(const double *coeffs, int n, double alpha, double beta,
+                    double eps_trunc, const tctl_opts *opts, const double *yw,
+                    const double *yU, int S, double *uw, double *uU, int cap,
+                    int *u_rank, tctl_stats *st);
+
+/* Allocates a canonical tensor with cap terms (device memory, zero rank). */
+int tctl_cp_alloc(tctl_ctx *ctx, int cap, tctl_cp *out);
+void tctl_cp_free(tctl_ctx *ctx, tctl_cp *cp);
+
+/* Copies the 1D eigenpairs of mode l to HOST buffers lam (n) and V (n x n,
+ * column-major, eigenvectors as columns; the sign of column v is fixed by
+ * sum_i v_i g_i > 0, g_i = 2 frac(i * 0.6180339887498949) - 1, i = 1..n). */
+int tctl_get_eigs(tctl_ctx *ctx, int mode, double *lam, double *V);
+
+/* Copies the statistics of the context (setup data and last solve) to *st. */
+int tctl_get_stats(tctl_ctx *ctx, tctl_stats *st);
+
+/* Number of GPU kernel launches issued by the context since setup (counter
+ * kept by the library's own launch wrappers). */
+long long tctl_launch_count(const tctl_ctx *ctx);
+
+/* Per-kernel timing (tracing): when enabled, the context records a pair of
+ * CUDA events on its stream around every kernel it launches. The report is a
+ * JSON object {kernel: {"launches", "ms", "flops"}} aggregated over the
+ * launches since the last report (flops: algorithmic 2mnk for GEMMs, 0 for
+ * other kernels); it synchronizes the stream and clears the records.
+ * Errors: TCTL_E_ARG (NULL, or buffer too small). */
+int tctl_profile_enable(tctl_ctx *ctx, int on);
+int tctl_profile_report(tctl_ctx *ctx, char *buf, int buflen);
+
+void tctl_destroy(tctl_ctx *ctx);
+const char *tctl_last_error(const tctl_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TENSORCTL_H */

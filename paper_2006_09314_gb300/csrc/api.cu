@@ -1,0 +1,452 @@
+// extern "C" entry points of tensorctl and the PCG driver (Appendix 2,
+// Algorithm 1). Every entry point catches the library's internal errors and
+// returns a status code; nothing throws across the ABI.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "tctl_internal.cuh"
+
+using namespace tctl;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr int kCap = 64;
+
+int handle(Ctx *c, const Error &e) {
+  if (c) c->err = e.msg;
+  g_last_error = e.msg;
+  return e.code;
+}
+
+void check_cp(const Ctx &c, const tctl_cp *t, const char *name, bool need_terms) {
+  if (!t) fail(TCTL_E_ARG, std::string(name) + " is NULL");
+  for (int l = 0; l < 3; ++l)
+    if (t->n[l] != c.n) fail(TCTL_E_ARG, std::string(name) + ": mode size differs from n");
+  if (t->rank < 0 || t->cap < 0 || t->rank > t->cap)
+    fail(TCTL_E_ARG, std::string(name) + ": invalid rank/cap");
+  if (need_terms && t->rank > 0 && (!t->w || !t->U[0] || !t->U[1] || !t->U[2]))
+    fail(TCTL_E_ARG, std::string(name) + ": NULL factor pointer");
+  if (!need_terms && t->cap > 0 && (!t->w || !t->U[0] || !t->U[1] || !t->U[2]))
+    fail(TCTL_E_ARG, std::string(name) + ": NULL factor pointer");
+}
+
+struct Timer {
+  cudaEvent_t a, b;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    TCTL_CUDA(cudaEventCreate(&a));
+    TCTL_CUDA(cudaEventCreate(&b));
+    TCTL_CUDA(cudaEventRecord(a, st));
+  }
+  double stop_ms() {
+    TCTL_CUDA(cudaEventRecord(b, st));
+    TCTL_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    TCTL_CUDA(cudaEventElapsedTime(&ms, a, b));
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+// fun / precond of Algorithm 1 on Tucker vectors; in the paper form (basis 0)
+// the vectors are in grid coordinates and every apply goes through V_l^T / V_l.
+void apply_sep(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, Tucker &tmp, double eps) {
+  if (c.o.basis == 1) {
+    sep_apply_trunc(c, D, x, y, eps);
+  } else {
+    tucker_copy(c, x, tmp);
+    tucker_basis_change(c, tmp, true);
+    sep_apply_trunc(c, D, tmp, y, eps);
+    tucker_basis_change(c, y, false);
+  }
+}
+
+}  // namespace
+
+namespace tctl {
+
+int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
+  Timer timer(c.st);
+  const double eps = c.eps;
+  const double eps_x = c.o.eps_final > 0 ? c.o.eps_final : 0.1 * eps;
+  const bool eig = (c.o.basis == 1);
+  size_t mk = c.ws.mark();
+  Tucker B, X, R, Z, P, S, T1, T2;
+  for (Tucker *t : {&B, &X, &R, &Z, &P, &S, &T1, &T2}) tucker_alloc(c, *t, kCap);
+  cp_to_tucker(c, b->rank, b->w, b->U, eig, B, 1e-12);
+  const double bnorm = std::sqrt(std::max(tucker_inner(c, B, B), 0.0));
+  int status = TCTL_OK;
+  int iters = 0;
+  double rel = 0.0;
+  int maxr = 0;
+  auto track = [&](const Tucker &t) {
+    for (int l = 0; l < 3; ++l) maxr = std::max(maxr, t.r[l]);
+  };
+  X.r[0] = X.r[1] = X.r[2] = 0;
+  if (bnorm == 0.0) {
+    x->rank = 0;
+  } else {
+    tucker_copy(c, B, R);                       // R0 = B - fun(X0), X0 = 0
+    apply_sep(c, c.pre, R, Z, T1, eps);         // Z0 = trunc(precond(R0))
+    tucker_copy(c, Z, P);                       // P0 = Z0
+    double rz = tucker_inner(c, R, Z);
+    rel = 1.0;
+    while (iters < c.o.max_iter) {
+      apply_sep(c, c.op, P, S, T1, eps);        // S = trunc(fun(P))
+      track(S);
+      const double pS = tucker_inner(c, P, S);
+      if (!(pS > 0.0) || !std::isfinite(pS)) fail(TCTL_E_NUMERIC, "PCG breakdown: <P, S> <= 0");
+      const double a = rz / pS;
+      tucker_axpby_trunc(c, 1.0, X, a, P, T2, eps_x);   // X = trunc(X + a P)
+      std::swap(X, T2);
+      tucker_axpby_trunc(c, 1.0, R, -a, S, T2, eps);    // R = trunc(R - a S)
+      std::swap(R, T2);
+      track(X);
+      track(R);
+      ++iters;
+      rel = std::sqrt(std::max(tucker_inner(c, R, R), 0.0)) / bnorm;
+      if (!std::isfinite(rel)) fail(TCTL_E_NAN, "non-finite residual");
+      if (rel <= c.o.pcg_rtol) break;
+      apply_sep(c, c.pre, R, Z, T1, eps);       // Z = trunc(precond(R))
+      const double rz_new = tucker_inner(c, R, Z);
+      const double beta = rz_new / rz;
+      rz = rz_new;
+      tucker_axpby_trunc(c, 1.0, Z, beta, P, T2, eps);  // P = trunc(Z + beta P)
+      std::swap(P, T2);
+      track(P);
+    }
+    if (rel > c.o.pcg_rtol) status = TCTL_E_NOT_CONVERGED;
+    const int s2 = tucker_to_cp(c, X, eig, eps_x, x);
+    if (status == TCTL_OK) status = s2;
+  }
+  c.stats.iters = iters;
+  c.stats.rel_res = rel;
+  for (int l = 0; l < 3; ++l) c.stats.rank_x[l] = X.r[l];
+  c.stats.max_rank = maxr;
+  c.ws.reset(mk);
+  c.stats.t_solve_ms = timer.stop_ms();
+  if (st) *st = c.stats;
+  return status;
+}
+
+}  // namespace tctl
+
+extern "C" {
+
+int tctl_default_opts(tctl_opts *o) {
+  if (!o) return TCTL_E_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->pcg_rtol = 1e-7;
+  o->max_iter = 100;
+  o->op_tol = 1e-8;
+  o->r_pre = 24;
+  o->rank_cap = kCap;
+  o->precision = 0;
+  o->basis = 1;
+  o->expsum_src = 0;
+  o->paper_end_rows = 0;
+  o->eps_final = 0.0;
+  o->seed = 1;
+  return TCTL_OK;
+}
+
+int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double beta,
+               double eps_trunc, const tctl_opts *opts, void *cuda_stream) {
+  Ctx *c = nullptr;
+  try {
+    if (!ctx) fail(TCTL_E_ARG, "ctx is NULL");
+    *ctx = nullptr;
+    if (!coeffs) fail(TCTL_E_ARG, "coeffs is NULL");
+    if (n < 2 || n > 32768) fail(TCTL_E_ARG, "n must be in [2, 32768]");
+    if (!(alpha > 0.0 && alpha <= 1.0)) fail(TCTL_E_ARG, "alpha must be in (0, 1]");
+    if (!(beta > 0.0) || !std::isfinite(beta)) fail(TCTL_E_ARG, "beta must be positive");
+    if (!(eps_trunc > 0.0 && eps_trunc < 1.0)) fail(TCTL_E_ARG, "eps_trunc must be in (0, 1)");
+    for (long long i = 0; i < 3ll * (n + 1); ++i)
+      if (!(coeffs[i] > 0.0) || !std::isfinite(coeffs[i]))
+        fail(TCTL_E_COEFF, "coefficient a_l(x) must be positive and finite");
+    c = new (std::nothrow) Ctx();
+    if (!c) fail(TCTL_E_NOMEM, "host allocation failed");
+    tctl_default_opts(&c->o);
+    if (opts) c->o = *opts;
+    if (c->o.precision != 0) fail(TCTL_E_ARG, "only precision 0 (FP64) is implemented");
+    if (c->o.expsum_src != 0) fail(TCTL_E_ARG, "only expsum_src 0 (sinc) is implemented");
+    if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
+    if (!(c->o.op_tol > 0 && c->o.op_tol < 1e-2)) fail(TCTL_E_ARG, "op_tol must be in (0, 1e-2)");
+    if (c->o.r_pre < 1 || c->o.r_pre > 200) fail(TCTL_E_ARG, "r_pre must be in [1, 200]");
+    if (c->o.max_iter < 1) fail(TCTL_E_ARG, "max_iter must be >= 1");
+    if (!(c->o.pcg_rtol > 0)) fail(TCTL_E_ARG, "pcg_rtol must be positive");
+    c->n = n;
+    c->alpha = alpha;
+    c->beta = beta;
+    c->eps = eps_trunc;
+    c->st = static_cast<cudaStream_t>(cuda_stream);
+    auto t0 = std::chrono::steady_clock::now();
+    const size_t arena = (size_t)6 * n * n * sizeof(double) + ((size_t)3 << 30);
+    void *base = nullptr;
+    check_cuda(cudaMalloc(&base, arena), "cudaMalloc(workspace)");
+    c->owned.push_back(base);
+    c->ws.base = static_cast<char *>(base);
+    c->ws.size = arena;
+    c->coef = c->dmalloc((size_t)3 * (n + 1));
+    to_dev(*c, c->coef, coeffs, (size_t)3 * (n + 1));
+    setup_eigs(*c);
+    setup_spectral(*c);
+    TCTL_CUDA(cudaStreamSynchronize(c->st));
+    auto t1 = std::chrono::steady_clock::now();
+    c->stats.t_setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    c->stats.op_rank = c->op.R;
+    c->stats.pre_rank = c->pre.R;
+    for (int l = 0; l < 3; ++l) c->stats.op_basis[l] = c->op.rD[l];
+    c->stats.op_rel_err = c->op_rel_err;
+    c->stats.s_min = c->s_min;
+    c->stats.s_max = c->s_max;
+    *ctx = reinterpret_cast<tctl_ctx *>(c);
+    return TCTL_OK;
+  } catch (const Error &e) {
+    const int code = handle(c, e);
+    if (c) tctl_destroy(reinterpret_cast<tctl_ctx *>(c));
+    return code;
+  }
+}
+
+static int apply_common(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, bool precond) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return TCTL_E_ARG;
+  try {
+    check_cp(*c, x, "x", true);
+    check_cp(*c, y, "y", false);
+    size_t mk = c->ws.mark();
+    Tucker tx, ty;
+    tucker_alloc(*c, tx, kCap);
+    tucker_alloc(*c, ty, kCap);
+    const double e2 = c->eps / std::sqrt(2.0);
+    cp_to_tucker(*c, x->rank, x->w, x->U, true, tx, 1e-12);
+    sep_apply_trunc(*c, precond ? c->pre : c->op, tx, ty, e2);
+    const int s = tucker_to_cp(*c, ty, true, e2, y);
+    c->ws.reset(mk);
+    return s;
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
+}
+
+int tctl_apply_op(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y) { return apply_common(ctx, x, y, false); }
+
+int tctl_apply_precond(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y) {
+  return apply_common(ctx, x, y, true);
+}
+
+int tctl_truncate(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, double eps) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return TCTL_E_ARG;
+  try {
+    check_cp(*c, x, "x", true);
+    check_cp(*c, y, "y", false);
+    if (!(eps > 0.0 && eps < 1.0)) fail(TCTL_E_ARG, "eps must be in (0, 1)");
+    size_t mk = c->ws.mark();
+    Tucker t;
+    tucker_alloc(*c, t, kCap);
+    cp_to_tucker(*c, x->rank, x->w, x->U, false, t, eps / std::sqrt(2.0));
+    const int s = tucker_to_cp(*c, t, false, eps / std::sqrt(2.0), y);
+    c->ws.reset(mk);
+    return s;
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
+}
+
+int tctl_pcg_solve(tctl_ctx *ctx, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return TCTL_E_ARG;
+  try {
+    check_cp(*c, b, "b", true);
+    check_cp(*c, x, "x", false);
+    return pcg_solve(*c, b, x, st);
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
+}
+
+int tctl_fullgrid_solve(tctl_ctx *ctx, const double *y, double *u) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return TCTL_E_ARG;
+  try {
+    if (!y || !u || y == u) fail(TCTL_E_ARG, "y and u must be distinct device arrays");
+    fullgrid_apply(*c, y, u, 0);
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
+}
+
+int tctl_fullgrid_state(tctl_ctx *ctx, const double *u, double *y) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return TCTL_E_ARG;
+  try {
+    if (!y || !u || y == u) fail(TCTL_E_ARG, "u and y must be distinct device arrays");
+    fullgrid_apply(*c, u, y, 1);
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
+}
+
+int tctl_cp_alloc(tctl_ctx *ctx, int cap, tctl_cp *out) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || !out || cap < 0) return TCTL_E_ARG;
+  std::memset(out, 0, sizeof(*out));
+  for (int l = 0; l < 3; ++l) out->n[l] = c->n;
+  out->cap = cap;
+  if (cap == 0) return TCTL_OK;
+  if (cudaMalloc(&out->w, sizeof(double) * cap) != cudaSuccess) return TCTL_E_NOMEM;
+  for (int l = 0; l < 3; ++l)
+    if (cudaMalloc(&out->U[l], sizeof(double) * cap * (size_t)c->n) != cudaSuccess) {
+      tctl_cp_free(ctx, out);
+      return TCTL_E_NOMEM;
+    }
+  return TCTL_OK;
+}
+
+void tctl_cp_free(tctl_ctx *ctx, tctl_cp *cp) {
+  (void)ctx;
+  if (!cp) return;
+  cudaFree(cp->w);
+  for (int l = 0; l < 3; ++l) cudaFree(cp->U[l]);
+  cp->w = nullptr;
+  cp->U[0] = cp->U[1] = cp->U[2] = nullptr;
+  cp->rank = cp->cap = 0;
+}
+
+int tctl_get_eigs(tctl_ctx *ctx, int mode, double *lam, double *V) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || mode < 0 || mode > 2) return TCTL_E_ARG;
+  try {
+    if (lam) to_host(*c, lam, c->lam[mode], c->n);
+    if (V) to_host(*c, V, c->V[mode], (size_t)c->n * c->n);
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
+}
+
+int tctl_get_stats(tctl_ctx *ctx, tctl_stats *st) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || !st) return TCTL_E_ARG;
+  *st = c->stats;
+  return TCTL_OK;
+}
+
+long long tctl_launch_count(const tctl_ctx *ctx) {
+  const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+  return c ? c->launches : 0;
+}
+
+int tctl_solve_host(const double *coeffs, int n, double alpha, double beta, double eps_trunc,
+                    const tctl_opts *opts, const double *yw, const double *yU, int S, double *uw,
+                    double *uU, int cap, int *u_rank, tctl_stats *st) {
+  if (!yw || !yU || S < 0 || !uw || !uU || cap < 0 || !u_rank) return TCTL_E_ARG;
+  tctl_ctx *ctx = nullptr;
+  int s = tctl_setup(&ctx, coeffs, n, alpha, beta, eps_trunc, opts, nullptr);
+  if (s != TCTL_OK) return s;
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  tctl_cp b{}, x{};
+  try {
+    s = tctl_cp_alloc(ctx, S, &b);
+    if (s != TCTL_OK) fail(s, "allocation of y_Omega failed");
+    s = tctl_cp_alloc(ctx, cap, &x);
+    if (s != TCTL_OK) fail(s, "allocation of the solution failed");
+    b.rank = S;
+    to_dev(*c, b.w, yw, S);
+    for (int l = 0; l < 3; ++l) to_dev(*c, b.U[l], yU + (size_t)l * n * S, (size_t)n * S);
+    s = pcg_solve(*c, &b, &x, st);
+    *u_rank = x.rank;
+    to_host(*c, uw, x.w, x.rank);
+    for (int l = 0; l < 3; ++l) to_host(*c, uU + (size_t)l * n * cap, x.U[l], (size_t)n * x.rank);
+  } catch (const Error &e) {
+    s = handle(c, e);
+  }
+  tctl_cp_free(ctx, &b);
+  tctl_cp_free(ctx, &x);
+  tctl_destroy(ctx);
+  return s;
+}
+
+int tctl_profile_enable(tctl_ctx *ctx, int on) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return TCTL_E_ARG;
+  c->prof = (on != 0);
+  c->prof_recs.clear();
+  c->prof_used = 0;
+  return TCTL_OK;
+}
+
+int tctl_profile_report(tctl_ctx *ctx, char *buf, int buflen) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || !buf || buflen <= 0) return TCTL_E_ARG;
+  try {
+    TCTL_CUDA(cudaStreamSynchronize(c->st));
+    struct Agg {
+      std::string name;
+      long long launches = 0;
+      double ms = 0, flops = 0;
+    };
+    std::vector<Agg> agg;
+    for (const ProfRec &r : c->prof_recs) {
+      std::string nm(r.name);
+      nm.erase(std::remove(nm.begin(), nm.end(), '('), nm.end());
+      const size_t lt = nm.find('<');
+      if (lt != std::string::npos) nm = nm.substr(0, lt);
+      float ms = 0;
+      TCTL_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      auto it = std::find_if(agg.begin(), agg.end(), [&](const Agg &a) { return a.name == nm; });
+      if (it == agg.end()) {
+        agg.push_back(Agg{nm});
+        it = agg.end() - 1;
+      }
+      it->launches++;
+      it->ms += ms;
+      it->flops += r.flops;
+    }
+    std::string js = "{";
+    for (size_t i = 0; i < agg.size(); ++i) {
+      char tmp[512];
+      std::snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e}",
+                    i ? ", " : "", agg[i].name.c_str(), agg[i].launches, agg[i].ms, agg[i].flops);
+      js += tmp;
+    }
+    js += "}";
+    if ((int)js.size() + 1 > buflen) fail(TCTL_E_ARG, "profile report buffer too small");
+    std::memcpy(buf, js.c_str(), js.size() + 1);
+    c->prof_recs.clear();
+    c->prof_used = 0;
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
+}
+
+void tctl_destroy(tctl_ctx *ctx) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+  for (void *p : c->owned) cudaFree(p);
+  delete c;
+}
+
+const char *tctl_last_error(const tctl_ctx *ctx) {
+  const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+  if (c && !c->err.empty()) return c->err.c_str();
+  return g_last_error.c_str();
+}
+
+}  // extern "C"

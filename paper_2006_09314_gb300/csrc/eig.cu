@@ -1,0 +1,219 @@
+// 1D Sturm-Liouville operators and their eigenbasis on the GPU, FP64.
+//
+// Section 3.2: A_(l) is tridiagonal with diagonal (a_{i-1/2} + a_{i+1/2})/h^2
+// and off-diagonal -a_{i+1/2}/h^2 (h = 1/(n+1)); with paper_end_rows the
+// first and last diagonal entries are the printed 2 a_{3/2}/h^2 and
+// 2 a_{n-1/2}/h^2.
+// Section 3.3 ("eigs_1D"): A_(l) = V_l diag(lambda^(l)) V_l^T. The paper
+// calls this cubic-cost step negligible; here it is done in parallel:
+//   * eigenvalues: Sturm-sequence bisection, one thread per eigenvalue
+//     (inertia counts of T - x I are monotone in x);
+//   * eigenvectors: one twisted factorization of T - lambda I per
+//     eigenvalue (forward and backward LDL-type recurrences, twist index at
+//     the smallest |gamma_k|), which gives (T - lambda I) z = gamma_r e_r;
+//     z is normalised and its sign fixed so that sum_i z_i g_i > 0 with the
+//     Weyl weights g_i = 2 frac(i * 0.6180339887498949) - 1, i = 1..n (the
+//     first entry of a localized high mode can underflow, so it cannot fix
+//     the sign).
+// Eigenvalues are ascending; V_l is column-major with eigenvectors as columns.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "tctl_internal.cuh"
+
+namespace tctl {
+
+__global__ void assemble_kernel(int n, const double *__restrict__ coef, int paper_end_rows,
+                                double *d0, double *d1, double *d2, double *e0, double *e1,
+                                double *e2) {
+  const int l = blockIdx.y;
+  double *d = l == 0 ? d0 : (l == 1 ? d1 : d2);
+  double *e = l == 0 ? e0 : (l == 1 ? e1 : e2);
+  const double *a = coef + (long long)l * (n + 1);
+  const double h = 1.0 / (n + 1);
+  const double ih2 = 1.0 / (h * h);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double di = (a[i] + a[i + 1]) * ih2;
+    if (paper_end_rows && i == 0) di = 2.0 * a[1] * ih2;
+    if (paper_end_rows && i == n - 1) di = 2.0 * a[n - 1] * ih2;
+    d[i] = di;
+    if (i < n - 1) e[i] = -a[i + 1] * ih2;
+  }
+}
+
+// Gershgorin interval and pivmin per mode (one block per mode).
+__global__ void gersh_kernel(int n, const double *d0, const double *d1, const double *d2,
+                             const double *e0, const double *e1, const double *e2,
+                             double *bounds) {
+  const int l = blockIdx.x;
+  const double *d = l == 0 ? d0 : (l == 1 ? d1 : d2);
+  const double *e = l == 0 ? e0 : (l == 1 ? e1 : e2);
+  double lo = 1e300, hi = -1e300, emax = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i < n - 1) emax = fmax(emax, e[i] * e[i]);
+  }
+  __shared__ double s_lo[256], s_hi[256], s_e[256];
+  s_lo[threadIdx.x] = lo;
+  s_hi[threadIdx.x] = hi;
+  s_e[threadIdx.x] = emax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_lo[threadIdx.x] = fmin(s_lo[threadIdx.x], s_lo[threadIdx.x + o]);
+      s_hi[threadIdx.x] = fmax(s_hi[threadIdx.x], s_hi[threadIdx.x + o]);
+      s_e[threadIdx.x] = fmax(s_e[threadIdx.x], s_e[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double span = s_hi[0] - s_lo[0];
+    bounds[4 * l + 0] = s_lo[0] - 2.0 * DBL_EPSILON * span - DBL_MIN;
+    bounds[4 * l + 1] = s_hi[0] + 2.0 * DBL_EPSILON * span + DBL_MIN;
+    bounds[4 * l + 2] = DBL_MIN * fmax(1.0, s_e[0]);
+  }
+}
+
+// number of eigenvalues of T strictly below x
+__device__ __forceinline__ int sturm_count(int n, const double *__restrict__ d,
+                                           const double *__restrict__ e, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += (q < 0.0);
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0);
+  }
+  return cnt;
+}
+
+__global__ void bisect_kernel(int n, const double *d0, const double *d1, const double *d2,
+                              const double *e0, const double *e1, const double *e2,
+                              const double *bounds, double *l0, double *l1, double *l2) {
+  const int l = blockIdx.y;
+  const double *d = l == 0 ? d0 : (l == 1 ? d1 : d2);
+  const double *e = l == 0 ? e0 : (l == 1 ? e1 : e2);
+  double *lam = l == 0 ? l0 : (l == 1 ? l1 : l2);
+  const double glo = bounds[4 * l], ghi = bounds[4 * l + 1], pivmin = bounds[4 * l + 2];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    double lo = glo, hi = ghi;
+    // invariant: count(lo) <= k < count(hi)
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
+      if (sturm_count(n, d, e, mid, pivmin) > k) hi = mid; else lo = mid;
+    }
+    lam[k] = 0.5 * (lo + hi);
+  }
+}
+
+// One thread per eigenvector. Scratch: Dp (n x n) holds D+ then nothing,
+// Um (n x n) holds the backward multipliers; V's column first holds the
+// forward multipliers, then the eigenvector.
+__global__ void twisted_kernel(int n, const double *d0, const double *d1, const double *d2,
+                               const double *e0, const double *e1, const double *e2,
+                               const double *bounds, const double *l0, const double *l1,
+                               const double *l2, double *V0, double *V1, double *V2, double *Dp,
+                               double *Um) {
+  const int l = blockIdx.y;
+  const double *d = l == 0 ? d0 : (l == 1 ? d1 : d2);
+  const double *e = l == 0 ? e0 : (l == 1 ? e1 : e2);
+  const double *lam = l == 0 ? l0 : (l == 1 ? l1 : l2);
+  double *V = l == 0 ? V0 : (l == 1 ? V1 : V2);
+  const double pivmin = bounds[4 * l + 2];
+  double *DpL = Dp + (long long)l * n * n;
+  double *UmL = Um + (long long)l * n * n;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const double lk = lam[k];
+    double *z = V + (long long)k * n;
+    double *dp = DpL + (long long)k * n;
+    double *um = UmL + (long long)k * n;
+    // forward: D+_0 = c_0; L_i = b_i / D+_i; D+_{i+1} = c_{i+1} - L_i b_i
+    double dplus = d[0] - lk;
+    if (fabs(dplus) < pivmin) dplus = pivmin;
+    dp[0] = dplus;
+    for (int i = 0; i < n - 1; ++i) {
+      const double Li = e[i] / dplus;
+      z[i] = Li;
+      dplus = (d[i + 1] - lk) - Li * e[i];
+      if (fabs(dplus) < pivmin) dplus = pivmin;
+      dp[i + 1] = dplus;
+    }
+    // backward: D-_{n-1} = c_{n-1}; U_i = b_i / D-_{i+1}; D-_i = c_i - U_i b_i
+    double dminus = d[n - 1] - lk;
+    if (fabs(dminus) < pivmin) dminus = pivmin;
+    int r = n - 1;
+    double gbest = fabs(dp[n - 1]);  // gamma_{n-1} = D+_{n-1}
+    for (int i = n - 2; i >= 0; --i) {
+      const double Ui = e[i] / dminus;
+      um[i] = Ui;
+      const double ci = d[i] - lk;
+      dminus = ci - Ui * e[i];
+      if (fabs(dminus) < pivmin) dminus = pivmin;
+      const double gam = dp[i] + dminus - ci;
+      if (fabs(gam) < gbest) { gbest = fabs(gam); r = i; }
+    }
+    // solve: z_r = 1, z_i = -L_i z_{i+1} (i < r), z_{i+1} = -U_i z_i (i >= r)
+    double zi = 1.0;
+    double nrm2 = 1.0;
+    for (int i = r - 1; i >= 0; --i) {
+      zi = -z[i] * zi;
+      z[i] = zi;
+      nrm2 = fma(zi, zi, nrm2);
+    }
+    z[r] = 1.0;
+    zi = 1.0;
+    for (int i = r; i < n - 1; ++i) {
+      zi = -um[i] * zi;
+      z[i + 1] = zi;
+      nrm2 = fma(zi, zi, nrm2);
+    }
+    double dot = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double x = (double)(i + 1) * 0.6180339887498949;
+      dot = fma(z[i], 2.0 * (x - floor(x)) - 1.0, dot);
+    }
+    const double s = (dot < 0.0 ? -1.0 : 1.0) / sqrt(nrm2);
+    for (int i = 0; i < n; ++i) z[i] *= s;
+  }
+}
+
+void setup_eigs(Ctx &c) {
+  const int n = c.n;
+  for (int l = 0; l < 3; ++l) {
+    c.d[l] = c.dmalloc(n);
+    c.e[l] = c.dmalloc(std::max(n - 1, 1));
+    c.lam[l] = c.dmalloc(n);
+    c.V[l] = c.dmalloc((size_t)n * n);
+  }
+  dim3 ga((n + 255) / 256, 3);
+  LAUNCH(c, assemble_kernel, ga, 256, 0, n, c.coef, c.o.paper_end_rows, c.d[0], c.d[1], c.d[2],
+         c.e[0], c.e[1], c.e[2]);
+  size_t mk = c.ws.mark();
+  double *bounds = c.ws.dbl(12);
+  LAUNCH(c, gersh_kernel, 3, 256, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds);
+  dim3 gb((n + 63) / 64, 3);
+  LAUNCH(c, bisect_kernel, gb, 64, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds,
+         c.lam[0], c.lam[1], c.lam[2]);
+  double *Dp = c.ws.dbl((size_t)3 * n * n);
+  double *Um = c.ws.dbl((size_t)3 * n * n);
+  LAUNCH(c, twisted_kernel, gb, 64, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds,
+         c.lam[0], c.lam[1], c.lam[2], c.V[0], c.V[1], c.V[2], Dp, Um);
+  for (int l = 0; l < 3; ++l) {
+    c.lam_host[l].resize(n);
+    to_host(c, c.lam_host[l].data(), c.lam[l], n);
+  }
+  c.ws.reset(mk);
+  c.s_min = c.lam_host[0][0] + c.lam_host[1][0] + c.lam_host[2][0];
+  c.s_max = c.lam_host[0][n - 1] + c.lam_host[1][n - 1] + c.lam_host[2][n - 1];
+  if (!(c.s_min > 0.0) || !std::isfinite(c.s_max))
+    fail(TCTL_E_NUMERIC, "eigensolver produced a non-positive or non-finite spectrum");
+}
+
+}  // namespace tctl

@@ -1,0 +1,631 @@
+// Dense FP64 building blocks: batched GEMM (mode products, Gram matrices,
+// projections), Khatri-Rao columns, small symmetric eigensolver, orthonormal
+// bases by pivoted Cholesky, and elementwise helpers.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, so these kernels
+// are arithmetic-bound: shared-memory tiles, register micro-tiles, split-K for
+// tall-skinny reductions (Gram matrices with K = n) so that every SM has work.
+#include <algorithm>
+#include <cmath>
+
+#include "tctl_internal.cuh"
+
+namespace tctl {
+
+[[noreturn]] void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what) {
+  if (e != cudaSuccess) {
+    fail(e == cudaErrorMemoryAllocation ? TCTL_E_NOMEM : TCTL_E_CUDA,
+         std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+void *Arena::alloc(size_t bytes) {
+  size_t off = (top + 255) & ~size_t(255);
+  if (off + bytes > size) {
+    fail(TCTL_E_NOMEM, "workspace arena exhausted (need " + std::to_string(off + bytes) +
+                           " bytes of " + std::to_string(size) + ")");
+  }
+  top = off + bytes;
+  peak = std::max(peak, top);
+  return base + off;
+}
+
+double *Ctx::dmalloc(size_t count) {
+  void *p = nullptr;
+  check_cuda(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(double)), "cudaMalloc");
+  owned.push_back(p);
+  return static_cast<double *>(p);
+}
+
+cudaEvent_t Ctx::prof_event() {
+  if (prof_used == prof_pool.size()) {
+    cudaEvent_t e;
+    check_cuda(cudaEventCreate(&e), "cudaEventCreate");
+    prof_pool.push_back(e);
+  }
+  return prof_pool[prof_used++];
+}
+
+// ------------------------------------------------------------------ GEMM
+constexpr int GEMM_BK = 16;
+
+template <int BM, int BN, bool TA, bool TB>
+__global__ void __launch_bounds__(256)
+dgemm_kernel(int m, int n, int k, double alpha, const double *__restrict__ A, int lda,
+             long long sA, int divA, const double *__restrict__ B, int ldb, long long sB,
+             int divB, double beta, double *__restrict__ C, int ldc, long long sC, int splits,
+             int kchunk, double *__restrict__ part) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ double As[GEMM_BK][BM + 1];
+  __shared__ double Bs[GEMM_BK][BN + 1];
+  const int bz = blockIdx.z;
+  const int b = bz / splits, split = bz % splits;
+  A += (long long)(b / divA) * sA;
+  B += (long long)(b / divB) * sB;
+  const int k0 = split * kchunk;
+  const int k1 = min(k, k0 + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  for (int kb = k0; kb < k1; kb += GEMM_BK) {
+    for (int e = threadIdx.x; e < BM * GEMM_BK; e += 256) {
+      int i, kk;
+      if (!TA) { i = e % BM; kk = e / BM; } else { kk = e % GEMM_BK; i = e / GEMM_BK; }
+      const int gi = row0 + i, gk = kb + kk;
+      double v = 0.0;
+      if (gi < m && gk < k1) v = TA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda];
+      As[kk][i] = v;
+    }
+    for (int e = threadIdx.x; e < BN * GEMM_BK; e += 256) {
+      int j, kk;
+      if (!TB) { kk = e % GEMM_BK; j = e / GEMM_BK; } else { j = e % BN; kk = e / BN; }
+      const int gj = col0 + j, gk = kb + kk;
+      double v = 0.0;
+      if (gj < n && gk < k1) v = TB ? B[gj + (long long)gk * ldb] : B[gk + (long long)gj * ldb];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GEMM_BK; ++kk) {
+      double a[TM], bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  if (splits == 1) {
+    double *Cb = C + (long long)b * sC;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int gi = row0 + ty + 16 * i, gj = col0 + tx + 16 * j;
+        if (gi < m && gj < n) {
+          double *p = Cb + gi + (long long)gj * ldc;
+          *p = (beta == 0.0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *p);
+        }
+      }
+  } else {
+    double *P = part + (long long)bz * m * n;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int gi = row0 + ty + 16 * i, gj = col0 + tx + 16 * j;
+        if (gi < m && gj < n) P[gi + (long long)gj * m] = acc[i][j];
+      }
+  }
+}
+
+__global__ void splitk_reduce(int m, int n, int splits, int batch, double alpha,
+                              const double *__restrict__ part, double beta, double *C, int ldc,
+                              long long sC) {
+  const long long total = (long long)m * n * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ((long long)m * n));
+    const long long r = t - (long long)b * m * n;
+    const int i = (int)(r % m), j = (int)(r / m);
+    double s = 0.0;
+    for (int q = 0; q < splits; ++q) s += part[((long long)b * splits + q) * m * n + r];
+    double *p = C + (long long)b * sC + i + (long long)j * ldc;
+    *p = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *p);
+  }
+}
+
+template <int BM, int BN>
+static void gemm_launch(Ctx &c, bool ta, bool tb, dim3 grid, int m, int n, int k, double alpha,
+                        const double *A, int lda, long long sA, int divA, const double *B,
+                        int ldb, long long sB, int divB, double beta, double *C, int ldc,
+                        long long sC, int splits, int kchunk, double *part) {
+#define TCTL_G(TA_, TB_)                                                                   \
+  LAUNCH(c, (dgemm_kernel<BM, BN, TA_, TB_>), grid, 256, 0, m, n, k, alpha, A, lda, sA,   \
+         divA, B, ldb, sB, divB, beta, C, ldc, sC, splits, kchunk, part)
+  if (!ta && !tb) TCTL_G(false, false);
+  else if (!ta && tb) TCTL_G(false, true);
+  else if (ta && !tb) TCTL_G(true, false);
+  else TCTL_G(true, true);
+#undef TCTL_G
+}
+
+void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const double *A, int lda,
+          long long sA, const double *B, int ldb, long long sB, double beta, double *C, int ldc,
+          long long sC, int batch, int divA, int divB) {
+  if (m <= 0 || n <= 0 || batch <= 0) return;
+  if (k <= 0) {
+    // C = beta C
+    if (beta == 0.0) {
+      for (int b = 0; b < batch; ++b)
+        for (int j = 0; j < n; ++j)
+          TCTL_CUDA(cudaMemsetAsync(C + b * sC + (long long)j * ldc, 0, sizeof(double) * m, c.st));
+    }
+    return;
+  }
+  const bool small = (m <= 32 && n <= 32);
+  const int BM = small ? 32 : 64, BN = small ? 32 : 64;
+  const int gx = (m + BM - 1) / BM, gy = (n + BN - 1) / BN;
+  const long long tiles = (long long)gx * gy * batch;
+  int splits = 1;
+  const int target = 2 * 152;
+  if (tiles < target && k >= 512) {
+    splits = (int)std::min<long long>((target + tiles - 1) / tiles, (k + 255) / 256);
+    splits = std::max(1, std::min(splits, 64));
+  }
+  int kchunk = (k + splits - 1) / splits;
+  kchunk = ((kchunk + GEMM_BK - 1) / GEMM_BK) * GEMM_BK;
+  splits = (k + kchunk - 1) / kchunk;
+  if (gy > 65535 || (long long)batch * splits > 65535) {
+    // split the batch to respect grid limits
+    if ((long long)batch * splits > 65535 && batch > 1) {
+      const int q = std::max(divA, divB) % std::min(divA, divB) == 0
+                        ? std::max(divA, divB)
+                        : divA * divB;  // batch chunks must keep whole divisor groups
+      int chunk = std::max(1, 65535 / splits);
+      chunk = std::max(q, chunk - chunk % q);
+      for (int b0 = 0; b0 < batch; b0 += chunk) {
+        const int nb = std::min(chunk, batch - b0);
+        // divisors: only valid if b0 is a multiple of the divisors
+        gemm(c, ta, tb, m, n, k, alpha, A + (long long)(b0 / divA) * sA, lda, sA,
+             B + (long long)(b0 / divB) * sB, ldb, sB, beta, C + (long long)b0 * sC, ldc, sC, nb,
+             divA, divB);
+      }
+      return;
+    }
+    if (gy > 65535) {
+      const int ncol = 65535 * BN;
+      for (int j0 = 0; j0 < n; j0 += ncol) {
+        const int nn = std::min(ncol, n - j0);
+        gemm(c, ta, tb, m, nn, k, alpha, A, lda, sA,
+             tb ? B + j0 : B + (long long)j0 * ldb, ldb, sB, beta, C + (long long)j0 * ldc, ldc,
+             sC, batch, divA, divB);
+      }
+      return;
+    }
+  }
+  double *part = nullptr;
+  size_t mk = c.ws.mark();
+  if (splits > 1) part = c.ws.dbl((size_t)m * n * batch * splits);
+  dim3 grid(gx, gy, batch * splits);
+  c.next_flops = 2.0 * m * n * (double)k * batch;
+  if (small)
+    gemm_launch<32, 32>(c, ta, tb, grid, m, n, k, alpha, A, lda, sA, divA, B, ldb, sB, divB, beta,
+                        C, ldc, sC, splits, kchunk, part);
+  else
+    gemm_launch<64, 64>(c, ta, tb, grid, m, n, k, alpha, A, lda, sA, divA, B, ldb, sB, divB, beta,
+                        C, ldc, sC, splits, kchunk, part);
+  if (splits > 1) {
+    const long long total = (long long)m * n * batch;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    LAUNCH(c, splitk_reduce, blocks, 256, 0, m, n, splits, batch, alpha, part, beta, C, ldc, sC);
+  }
+  c.ws.reset(mk);
+}
+
+// ------------------------------------------------------------------ elementwise
+__global__ void khatri_rao_kernel(int n, const double *__restrict__ A, int lda, int ra,
+                                  const double *__restrict__ B, int ldb, int rb, double *out,
+                                  int ldo) {
+  const long long total = (long long)n * ra * rb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n);
+    const long long col = t / n;
+    const int a = (int)(col % ra), bcol = (int)(col / ra);
+    out[i + col * ldo] = A[i + (long long)a * lda] * B[i + (long long)bcol * ldb];
+  }
+}
+
+void khatri_rao(Ctx &c, int n, const double *A, int lda, int ra, const double *B, int ldb, int rb,
+                double *out, int ldo) {
+  const long long total = (long long)n * ra * rb;
+  if (total == 0) return;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+  LAUNCH(c, khatri_rao_kernel, blocks, 256, 0, n, A, lda, ra, B, ldb, rb, out, ldo);
+}
+
+__global__ void col_norms_kernel(int n, int m, const double *__restrict__ A, int lda,
+                                 double *out) {
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = A[i + (long long)j * lda];
+    s = fma(v, v, s);
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[j] = sqrt(s);
+  }
+}
+
+void col_norms(Ctx &c, int n, int m, const double *A, int lda, double *out) {
+  if (m <= 0) return;
+  LAUNCH(c, col_norms_kernel, m, 256, 0, n, m, A, lda, out);
+}
+
+__global__ void scale_cols_kernel(int n, int m, double *A, int lda, const double *s, int inv) {
+  const long long total = (long long)n * m;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    const double f = s[j];
+    A[i + (long long)j * lda] *= inv ? (f != 0.0 ? 1.0 / f : 0.0) : f;
+  }
+}
+
+void scale_cols(Ctx &c, int n, int m, double *A, int lda, const double *s, bool inverse) {
+  const long long total = (long long)n * m;
+  if (total == 0) return;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  LAUNCH(c, scale_cols_kernel, blocks, 256, 0, n, m, A, lda, s, inverse ? 1 : 0);
+}
+
+// splitmix64 counter hash -> two uniforms -> Box-Muller normal
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void gaussian_kernel(double *x, size_t count, uint64_t seed) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t h1 = mix64(seed ^ mix64(2 * t));
+    const uint64_t h2 = mix64(seed ^ mix64(2 * t + 1));
+    const double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
+    const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);          // [0, 1)
+    x[t] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+void fill_gaussian(Ctx &c, double *x, size_t count, uint64_t seed) {
+  if (count == 0) return;
+  const int blocks = (int)std::min<size_t>((count + 255) / 256, 4096);
+  LAUNCH(c, gaussian_kernel, blocks, 256, 0, x, count, seed);
+}
+
+void fill_zero(Ctx &c, double *x, size_t count) {
+  if (count) TCTL_CUDA(cudaMemsetAsync(x, 0, count * sizeof(double), c.st));
+}
+
+void copy_d(Ctx &c, double *dst, const double *src, size_t count) {
+  if (count && dst != src)
+    TCTL_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+}
+
+__global__ void axpby_kernel(size_t count, double a, const double *x, double b, double *y) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+       t += (size_t)gridDim.x * blockDim.x)
+    y[t] = (b == 0.0) ? a * x[t] : fma(a, x[t], b * y[t]);
+}
+
+void axpby(Ctx &c, size_t count, double a, const double *x, double b, double *y) {
+  if (count == 0) return;
+  const int blocks = (int)std::min<size_t>((count + 255) / 256, 4096);
+  LAUNCH(c, axpby_kernel, blocks, 256, 0, count, a, x, b, y);
+}
+
+void to_host(Ctx &c, double *dst, const double *src, size_t count) {
+  if (!count) return;
+  TCTL_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  TCTL_CUDA(cudaStreamSynchronize(c.st));
+}
+
+void to_dev(Ctx &c, double *dst, const double *src, size_t count) {
+  if (!count) return;
+  TCTL_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, c.st));
+}
+
+// ------------------------------------------------------------------ Jacobi
+// Parallel cyclic Jacobi (round-robin pairing) for symmetric m x m, m <= 64.
+// One CTA per matrix; A and V in shared memory (padded to even size mp).
+constexpr int JMAX = 64;
+
+__global__ void __launch_bounds__(256) jacobi_kernel(int m, const double *__restrict__ Ain,
+                                                     double *__restrict__ lam,
+                                                     double *__restrict__ Vout) {
+  extern __shared__ double sm[];
+  const int mp = (m + 1) & ~1;
+  const int ld = mp + 1;
+  double *A = sm;               // mp x ld
+  double *V = A + mp * ld;      // mp x ld
+  double *cs = V + mp * ld;     // 2 * (mp/2)
+  int *pq = reinterpret_cast<int *>(cs + mp);  // 2 * (mp/2)
+  __shared__ double red[8];
+  __shared__ int done;
+  const int b = blockIdx.x;
+  const double *Ab = Ain + (long long)b * m * m;
+  for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
+    const int i = t % mp, j = t / mp;
+    A[i + j * ld] = (i < m && j < m) ? Ab[i + j * m] : 0.0;
+    V[i + j * ld] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int half = mp / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    // convergence test: off-diagonal vs total Frobenius mass
+    double off = 0.0, tot = 0.0;
+    for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
+      const int i = t % mp, j = t / mp;
+      const double v = A[i + j * ld];
+      tot = fma(v, v, tot);
+      if (i != j) off = fma(v, v, off);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_down_sync(0xffffffffu, off, o);
+      tot += __shfl_down_sync(0xffffffffu, tot, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = off;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      red[0] = s;
+    }
+    __syncthreads();
+    off = red[0];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      done = (off <= 1e-32 * s) || (s == 0.0);
+    }
+    __syncthreads();
+    if (done) break;
+    for (int step = 0; step < mp - 1; ++step) {
+      for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        // round robin: position 0 fixed, others rotate
+        auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (mp - 1); };
+        int p = at(t), q = at(mp - 1 - t);
+        if (p > q) { const int tmp = p; p = q; q = tmp; }
+        const double apq = A[p + q * ld];
+        double cc = 1.0, ss = 0.0;
+        if (fabs(apq) > 1e-300) {
+          const double tau = (A[q + q * ld] - A[p + p * ld]) / (2.0 * apq);
+          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          cc = 1.0 / sqrt(1.0 + tt * tt);
+          ss = tt * cc;
+        }
+        cs[2 * t] = cc;
+        cs[2 * t + 1] = ss;
+        pq[2 * t] = p;
+        pq[2 * t + 1] = q;
+      }
+      __syncthreads();
+      // rows p, q of A
+      for (int t = threadIdx.x; t < half * mp; t += blockDim.x) {
+        const int pr = t % half, j = t / half;
+        const double cc = cs[2 * pr], ss = cs[2 * pr + 1];
+        const int p = pq[2 * pr], q = pq[2 * pr + 1];
+        const double ap = A[p + j * ld], aq = A[q + j * ld];
+        A[p + j * ld] = cc * ap - ss * aq;
+        A[q + j * ld] = ss * ap + cc * aq;
+      }
+      __syncthreads();
+      // columns p, q of A and V
+      for (int t = threadIdx.x; t < half * mp; t += blockDim.x) {
+        const int pr = t % half, i = t / half;
+        const double cc = cs[2 * pr], ss = cs[2 * pr + 1];
+        const int p = pq[2 * pr], q = pq[2 * pr + 1];
+        const double ap = A[i + p * ld], aq = A[i + q * ld];
+        A[i + p * ld] = cc * ap - ss * aq;
+        A[i + q * ld] = ss * ap + cc * aq;
+        const double vp = V[i + p * ld], vq = V[i + q * ld];
+        V[i + p * ld] = cc * vp - ss * vq;
+        V[i + q * ld] = ss * vp + cc * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // sort eigenvalues descending (selection by rank, m <= 64)
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double di = A[i + i * ld];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double dj = A[j + j * ld];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    lam[(long long)b * m + rank] = di;
+    for (int r = 0; r < m; ++r) Vout[(long long)b * m * m + r + (long long)rank * m] = V[r + i * ld];
+  }
+}
+
+void sym_eig(Ctx &c, int m, int batch, const double *A, double *lam, double *Vout) {
+  if (m <= 0 || batch <= 0) return;
+  if (m > JMAX) fail(TCTL_E_ARG, "sym_eig: m > 64");
+  const int mp = (m + 1) & ~1;
+  const size_t smem = sizeof(double) * (2 * mp * (mp + 1) + mp) + sizeof(int) * mp;
+  static bool attr = false;
+  if (!attr) {
+    TCTL_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   100 * 1024));
+    attr = true;
+  }
+  LAUNCH(c, jacobi_kernel, batch, 256, smem, m, A, lam, Vout);
+}
+
+// ------------------------------------------------------------------ orth
+// Pivoted Cholesky of the Gram matrix G (m x m): P^T G P = L L^T on the first
+// r pivots, stopping when the largest remaining Schur diagonal is <= thr.
+// Writes perm[0..r) and L (r x r, lower, ld 64) and r to out_r.
+__global__ void pivchol_kernel(int m, const double *__restrict__ Gin, double thr_rel_or_abs,
+                               int relative, int rcap, int *perm_out, double *L_out, int *out_r) {
+  __shared__ double G[JMAX][JMAX + 1];
+  __shared__ int perm[JMAX];
+  __shared__ int piv;
+  __shared__ double thr;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) G[t % m][t / m] = Gin[t];
+  for (int t = threadIdx.x; t < m; t += blockDim.x) perm[t] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double dmax = 0.0;
+    for (int i = 0; i < m; ++i) dmax = fmax(dmax, G[i][i]);
+    thr = relative ? thr_rel_or_abs * thr_rel_or_abs * dmax : thr_rel_or_abs * thr_rel_or_abs;
+    if (!(dmax > 0.0)) thr = 1e300;
+  }
+  __syncthreads();
+  int r = 0;
+  const int rmax = min(m, rcap);
+  for (int j = 0; j < rmax; ++j) {
+    if (threadIdx.x == 0) {
+      int best = j;
+      double bv = G[j][j];
+      for (int i = j + 1; i < m; ++i)
+        if (G[i][i] > bv) { bv = G[i][i]; best = i; }
+      piv = (bv > thr && isfinite(bv)) ? best : -1;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p < 0) break;
+    // symmetric swap of rows/cols j and p
+    if (p != j) {
+      for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const double tmp = G[j][t];
+        G[j][t] = G[p][t];
+        G[p][t] = tmp;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const double tmp = G[t][j];
+        G[t][j] = G[t][p];
+        G[t][p] = tmp;
+      }
+      if (threadIdx.x == 0) {
+        const int tmp = perm[j];
+        perm[j] = perm[p];
+        perm[p] = tmp;
+      }
+      __syncthreads();
+    }
+    const double ljj = sqrt(G[j][j]);
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) G[i][j] /= ljj;
+    __syncthreads();
+    if (threadIdx.x == 0) G[j][j] = ljj;
+    for (int t = threadIdx.x; t < (m - j - 1) * (m - j - 1); t += blockDim.x) {
+      const int i = j + 1 + t % (m - j - 1), k = j + 1 + t / (m - j - 1);
+      if (k <= i) G[i][k] -= G[i][j] * G[k][j];
+    }
+    __syncthreads();
+    // keep symmetric copy of the trailing block for the next pivot search
+    for (int t = threadIdx.x; t < (m - j - 1) * (m - j - 1); t += blockDim.x) {
+      const int i = j + 1 + t % (m - j - 1), k = j + 1 + t / (m - j - 1);
+      if (k > i) G[i][k] = G[k][i];
+    }
+    __syncthreads();
+    r = j + 1;
+  }
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+    const int i = t % r, k = t / r;
+    L_out[i + k * JMAX] = (k <= i) ? G[i][k] : 0.0;
+  }
+  for (int t = threadIdx.x; t < r; t += blockDim.x) perm_out[t] = perm[t];
+  if (threadIdx.x == 0) *out_r = r;
+}
+
+// Q[i, :] = Y[i, perm] L^{-T}: forward substitution per row (x L^T = y).
+__global__ void trsm_rows_kernel(int n, int r, const double *__restrict__ Y, int ldy,
+                                 const int *__restrict__ perm, const double *__restrict__ Lg,
+                                 double *__restrict__ Q, int ldq) {
+  __shared__ double L[JMAX][JMAX + 1];
+  __shared__ int pm[JMAX];
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) L[t % r][t / r] = Lg[(t % r) + (t / r) * JMAX];
+  for (int t = threadIdx.x; t < r; t += blockDim.x) pm[t] = perm[t];
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double x[JMAX];
+#pragma unroll 1
+    for (int j = 0; j < r; ++j) {
+      double s = Y[i + (long long)pm[j] * ldy];
+      for (int k = 0; k < j; ++k) s -= x[k] * L[j][k];
+      x[j] = s / L[j][j];
+    }
+#pragma unroll 1
+    for (int j = 0; j < r; ++j) Q[i + (long long)j * ldq] = x[j];
+  }
+}
+
+int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relative, int rcap,
+         double *Q) {
+  if (m <= 0) return 0;
+  if (m > JMAX) fail(TCTL_E_ARG, "orth: more than 64 columns");
+  size_t mk = c.ws.mark();
+  double *G = c.ws.dbl((size_t)m * m);
+  double *L = c.ws.dbl((size_t)JMAX * JMAX);
+  int *perm = c.ws.i32(JMAX);
+  int *rdev = c.ws.i32(4);
+  double *Q2 = c.ws.dbl((size_t)n * std::min(m, rcap > 0 ? rcap : 1));
+  const int blocks = std::min((n + 127) / 128, 1024);
+  auto read_r = [&]() {
+    int r = 0;
+    TCTL_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    TCTL_CUDA(cudaStreamSynchronize(c.st));
+    return r;
+  };
+  // pass 1: pivoted Cholesky of Y^T Y picks the columns and the rank
+  gemm(c, true, false, m, m, n, 1.0, Y, ldy, 0, Y, ldy, 0, 0.0, G, m, 0);
+  LAUNCH(c, pivchol_kernel, 1, 256, 0, m, G, tol, relative ? 1 : 0, rcap, perm, L, rdev);
+  int r = read_r();
+  if (r > 0) {
+    LAUNCH(c, trsm_rows_kernel, blocks, 128, 0, n, r, Y, ldy, perm, L, Q, n);
+    // passes 2 and 3 (Cholesky QR on the result) restore orthogonality to rounding
+    // level; a column whose residual has fallen to rounding noise (kept in pass 1 at
+    // the edge of the tolerance) is dropped here instead of breaking the factorization.
+    for (int pass = 0; pass < 2 && r > 0; ++pass) {
+      gemm(c, true, false, r, r, n, 1.0, Q, n, 0, Q, n, 0, 0.0, G, r, 0);
+      LAUNCH(c, pivchol_kernel, 1, 256, 0, r, G, 1e-10, 1, r, perm, L, rdev);
+      const int r2 = read_r();
+      if (r2 > 0) {
+        LAUNCH(c, trsm_rows_kernel, blocks, 128, 0, n, r2, Q, n, perm, L, Q2, n);
+        copy_d(c, Q, Q2, (size_t)n * r2);
+      }
+      r = r2;
+    }
+  }
+  c.ws.reset(mk);
+  return r;
+}
+
+}  // namespace tctl

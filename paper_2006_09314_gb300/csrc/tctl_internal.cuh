@@ -1,0 +1,182 @@
+// Internal declarations of the tensorctl library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/tensorctl.h"
+
+namespace tctl {
+
+// Errors are C++ exceptions inside the library; every extern "C" entry point
+// catches them and turns them into a status code plus tctl_last_error().
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what);
+#define TCTL_CUDA(call) ::tctl::check_cuda((call), #call)
+
+// Bump allocator over one device buffer; mark()/reset() scope temporaries.
+struct Arena {
+  char *base = nullptr;
+  size_t size = 0;
+  size_t top = 0;
+  size_t peak = 0;
+  void *alloc(size_t bytes);
+  double *dbl(size_t count) { return static_cast<double *>(alloc(count * sizeof(double))); }
+  int *i32(size_t count) { return static_cast<int *>(alloc(count * sizeof(int))); }
+  size_t mark() const { return top; }
+  void reset(size_t m) { top = m; }
+};
+
+// Separable diagonal operator in the tensor eigenbasis:
+//   D = sum_k w[k] diag(E_1[:,k]) x diag(E_2[:,k]) x diag(E_3[:,k]),
+// plus a per-mode orthonormal basis B_l (n x rD_l) of span(E_l) with
+// E_l = B_l Z_l (Z_l: rD_l x R), used to keep the cost of applications
+// proportional to rD_l rather than R.
+struct Sep {
+  int R = 0;
+  double *w = nullptr;
+  double *E[3] = {nullptr, nullptr, nullptr};
+  int rD[3] = {0, 0, 0};
+  double *B[3] = {nullptr, nullptr, nullptr};
+  double *Z[3] = {nullptr, nullptr, nullptr};
+  std::vector<double> w_host;
+};
+
+// Tucker tensor in arena/context memory: Q[l] n x r[l] (ld n, orthonormal
+// columns), core r0 x r1 x r2 (first index fastest).
+struct Tucker {
+  int r[3] = {0, 0, 0};
+  double *Q[3] = {nullptr, nullptr, nullptr};
+  double *core = nullptr;
+  int cap = 0;
+};
+
+// One profiled launch (opt-in: events around every kernel of the context).
+struct ProfRec {
+  const char *name;
+  cudaEvent_t a, b;
+  double flops;
+};
+
+struct Ctx {
+  int n = 0;
+  double alpha = 0, beta = 0, eps = 0;
+  tctl_opts o{};
+  cudaStream_t st = nullptr;
+  double *coef = nullptr;            // 3 x (n+1)
+  double *d[3] = {}, *e[3] = {};     // tridiagonal A_(l)
+  double *lam[3] = {}, *V[3] = {};   // eigenpairs
+  std::vector<double> lam_host[3];
+  double s_min = 0, s_max = 0;
+  Sep op, pre;
+  double op_rel_err = 0;
+  Arena ws;
+  double *full_tmp = nullptr;        // 2 n^3 for the full-grid solve
+  tctl_stats stats{};
+  std::string err;
+  long long launches = 0;
+  uint64_t rng_counter = 0;
+  std::vector<void *> owned;         // device allocations freed at destroy
+  bool prof = false;                 // record events around every launch
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  size_t prof_used = 0;
+  double next_flops = 0;             // algorithmic flops of the next launch (GEMMs)
+  double *dmalloc(size_t count);
+  cudaEvent_t prof_event();
+};
+
+// ------------------------------------------------------------ launch wrapper
+// Every kernel launch of the library goes through LAUNCH so the context can
+// count them and check the launch status.
+#define LAUNCH(ctx, kernel, grid, block, smem, ...)                                \
+  do {                                                                            \
+    cudaEvent_t tctl_ev_a = nullptr, tctl_ev_b = nullptr;                         \
+    if ((ctx).prof) {                                                             \
+      tctl_ev_a = (ctx).prof_event();                                             \
+      tctl_ev_b = (ctx).prof_event();                                             \
+      ::tctl::check_cuda(cudaEventRecord(tctl_ev_a, (ctx).st), "cudaEventRecord"); \
+    }                                                                             \
+    kernel<<<(grid), (block), (smem), (ctx).st>>>(__VA_ARGS__);                   \
+    ::tctl::check_cuda(cudaGetLastError(), #kernel);                              \
+    (ctx).launches++;                                                             \
+    if ((ctx).prof) {                                                             \
+      ::tctl::check_cuda(cudaEventRecord(tctl_ev_b, (ctx).st), "cudaEventRecord"); \
+      (ctx).prof_recs.push_back({#kernel, tctl_ev_a, tctl_ev_b, (ctx).next_flops}); \
+    }                                                                             \
+    (ctx).next_flops = 0;                                                         \
+  } while (0)
+
+// ------------------------------------------------------------ linalg.cu
+// C = alpha op(A) op(B) + beta C, column-major, batched with element strides;
+// batch item b uses A + (b / divA) * sA, B + (b / divB) * sB, C + b * sC.
+void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha,
+          const double *A, int lda, long long sA, const double *B, int ldb,
+          long long sB, double beta, double *C, int ldc, long long sC,
+          int batch = 1, int divA = 1, int divB = 1);
+// out[:, a + ra*b] = A[:, a] .* B[:, b]   (n rows, Khatri-Rao of columns)
+void khatri_rao(Ctx &c, int n, const double *A, int lda, int ra, const double *B,
+                int ldb, int rb, double *out, int ldo);
+// Symmetric eigendecomposition (one-sided cyclic Jacobi, parallel ordering) of
+// `batch` m x m matrices (ld m, contiguous); eigenvalues descending in lam
+// (batch x m), eigenvectors as columns in Vout (batch x m x m). m <= 64.
+void sym_eig(Ctx &c, int m, int batch, const double *A, double *lam, double *Vout);
+// Orthonormal basis of span(Y) (n x m, m <= 64) by pivoted Cholesky of Y^T Y:
+// columns whose residual norm falls below tol * (reference) are dropped, where
+// reference = max column norm (relative=true) or 1 (relative=false). Writes Q
+// (n x r, ld n) and returns r (r <= min(m, rcap)). Two passes (CholeskyQR2).
+int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relative,
+         int rcap, double *Q);
+// Column 2-norms of an n x m matrix.
+void col_norms(Ctx &c, int n, int m, const double *A, int lda, double *out);
+void scale_cols(Ctx &c, int n, int m, double *A, int lda, const double *s, bool inverse);
+void fill_gaussian(Ctx &c, double *x, size_t count, uint64_t seed);
+void fill_zero(Ctx &c, double *x, size_t count);
+void copy_d(Ctx &c, double *dst, const double *src, size_t count);
+void axpby(Ctx &c, size_t count, double a, const double *x, double b, double *y);
+// Host copies (synchronous on the context stream).
+void to_host(Ctx &c, double *dst, const double *src, size_t count);
+void to_dev(Ctx &c, double *dst, const double *src, size_t count);
+
+// ------------------------------------------------------------ eig.cu
+// Assemble A_(l) from coef and compute all three eigendecompositions in FP64.
+void setup_eigs(Ctx &c);
+
+// ------------------------------------------------------------ spectral.cu
+void setup_spectral(Ctx &c);
+void fullgrid_apply(Ctx &c, const double *y, double *u, int which);
+
+// ------------------------------------------------------------ tucker.cu
+struct TuckerOps;
+// canonical (device) -> Tucker in the tensor eigenbasis (to_eig=true: factors
+// are first multiplied by V_l^T), lossless up to the pivoting tolerance.
+void cp_to_tucker(Ctx &c, int m, const double *w, double *const U[3], bool to_eig,
+                  Tucker &out, double eps_core);
+// Tucker -> canonical (T2C, slice SVDs), optional back transform with V_l.
+int tucker_to_cp(Ctx &c, const Tucker &x, bool from_eig, double eps, tctl_cp *y);
+void tucker_alloc(Ctx &c, Tucker &t, int cap);
+void tucker_copy(Ctx &c, const Tucker &src, Tucker &dst);
+// y = trunc(D .* x) with D separable (eigenbasis), eps relative.
+void sep_apply_trunc(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, double eps);
+// z = trunc(a x + b y)
+void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucker &y,
+                        Tucker &z, double eps);
+double tucker_inner(Ctx &c, const Tucker &x, const Tucker &y);
+// Truncate a Tucker tensor in place by HOSVD of its core (eps relative).
+void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps);
+// Apply V_l (from_eig) or V_l^T (to_eig) to the Tucker factors in place.
+void tucker_basis_change(Ctx &c, Tucker &x, bool to_eig);
+
+// ------------------------------------------------------------ pcg.cu
+int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st);
+
+}  // namespace tctl

@@ -1,0 +1,658 @@
+// Rank-structured tensor algebra on the GPU (Appendix 1 of the paper):
+// canonical-to-Tucker by reduced HOSVD of the side matrices, Tucker core
+// truncation (HOSVD of the core), Tucker-to-canonical by slice SVDs, the
+// Euclidean inner product, sums, and the Hadamard product with a separable
+// diagonal operator followed by truncation (the fun/precond + trunc lines of
+// Algorithm 1).
+//
+// Inside the solver a rank-truncated vector is kept in Tucker form
+// (orthonormal Q_l, small dense core): the canonical form returned by
+// Tucker-to-canonical has rank up to r^2, which would multiply the cost of
+// the next Hadamard product; the Tucker form carries the same truncated
+// tensor. Canonical tensors are converted at the API boundary.
+//
+// The Hadamard product D .* X of a rank-R separable diagonal D and a Tucker
+// X has per-mode span inside span{e_k .* q_a}; its dominant mode-l subspace
+// is found by a randomized range finder on the mode-l unfolding with
+// Khatri-Rao-structured Gaussian probes (w_m x w_n per sample), which never
+// forms the R*r columns; the core of D .* X in the new bases is then
+// sum_k w_k core x_1 M_1k x_2 M_2k x_3 M_3k with M_lk = Q'_l^T diag(e_lk) Q_l,
+// and the HOSVD of that core performs the eps truncation exactly (the bases
+// are orthonormal, so Frobenius norms of the core are norms of the tensor).
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "tctl_internal.cuh"
+
+namespace tctl {
+
+namespace {
+
+constexpr int kMaxRank = 64;
+
+__global__ void permute3_kernel(int r0, int r1, int r2, const double *__restrict__ in, int p0,
+                                int p1, int p2, double *__restrict__ out) {
+  // out dims (r[p0], r[p1], r[p2]); out[i_p0, i_p1, i_p2] = in[i0, i1, i2]
+  const long long total = (long long)r0 * r1 * r2;
+  const int r[3] = {r0, r1, r2};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    idx[0] = (int)(t % r0);
+    idx[1] = (int)((t / r0) % r1);
+    idx[2] = (int)(t / ((long long)r0 * r1));
+    const long long o = idx[p0] + (long long)r[p0] * (idx[p1] + (long long)r[p1] * idx[p2]);
+    out[o] = in[t];
+  }
+}
+
+void permute3(Ctx &c, const int r[3], const double *in, int p0, int p1, int p2, double *out) {
+  const long long total = (long long)r[0] * r[1] * r[2];
+  if (!total) return;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 2048);
+  LAUNCH(c, permute3_kernel, blocks, 256, 0, r[0], r[1], r[2], in, p0, p1, p2, out);
+}
+
+// out[a + ra*(s + ls*k)] = w[k] * sum_b F[(a + ra*b) + ra*rb*(s + ls*k)] * P[(b + rb*s) + rb*ls*k]
+__global__ void contract_b_kernel(int ra, int rb, int ls, int K, const double *__restrict__ F,
+                                  const double *__restrict__ P, const double *__restrict__ w,
+                                  double *__restrict__ out) {
+  const long long total = (long long)ra * ls * K;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(t % ra);
+    const long long sk = t / ra;  // s + ls*k
+    const int k = (int)(sk / ls);
+    const int s = (int)(sk % ls);
+    const double *Fc = F + (long long)ra * rb * sk + a;
+    const double *Pc = P + (long long)rb * ls * k + (long long)rb * s;
+    double acc = 0.0;
+    for (int b = 0; b < rb; ++b) acc = fma(Fc[(long long)ra * b], Pc[b], acc);
+    out[t] = w[k] * acc;
+  }
+}
+
+// u[a + ra*(p + rp*s)] = v[(a + ra*s) + ra*ls*p]   ((a,s,p) -> (a,p,s))
+__global__ void perm_asp_kernel(int ra, int ls, int rp, const double *__restrict__ v,
+                                double *__restrict__ u) {
+  const long long total = (long long)ra * ls * rp;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(t % ra);
+    const int s = (int)((t / ra) % ls);
+    const int p = (int)(t / ((long long)ra * ls));
+    u[a + (long long)ra * (p + (long long)rp * s)] = v[t];
+  }
+}
+
+__global__ void embed3_kernel(int a0, int a1, int a2, const double *__restrict__ in, int b0, int b1,
+                              int b2, double scale, double *__restrict__ out) {
+  // out (b0,b1,b2) zero-padded copy of scale*in (a0,a1,a2)
+  const long long total = (long long)b0 * b1 * b2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % b0), j = (int)((t / b0) % b1), k = (int)(t / ((long long)b0 * b1));
+    out[t] = (i < a0 && j < a1 && k < a2) ? scale * in[i + (long long)a0 * (j + (long long)a1 * k)]
+                                          : 0.0;
+  }
+}
+
+__global__ void dot_kernel(long long n, const double *__restrict__ x, const double *__restrict__ y,
+                           double *out) {
+  double s = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    s = fma(x[t], y[t], s);
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+  }
+}
+
+double dot_host(Ctx &c, long long n, const double *x, const double *y) {
+  if (n <= 0) return 0.0;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 64);
+  size_t mk = c.ws.mark();
+  double *part = c.ws.dbl(blocks);
+  LAUNCH(c, dot_kernel, blocks, 256, 0, n, x, y, part);
+  std::vector<double> h(blocks);
+  to_host(c, h.data(), part, blocks);
+  c.ws.reset(mk);
+  double s = 0.0;
+  for (double v : h) s += v;
+  if (!std::isfinite(s)) fail(TCTL_E_NAN, "non-finite inner product");
+  return s;
+}
+
+__global__ void side_scale_kernel(int m, const double *__restrict__ w, const double *__restrict__ n0,
+                                  const double *__restrict__ n1, const double *__restrict__ n2,
+                                  int l, double *__restrict__ s) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const double nn[3] = {n0[k], n1[k], n2[k]};
+    double v = fabs(w[k]);
+    for (int q = 0; q < 3; ++q) {
+      if (q != l) v *= nn[q];
+    }
+    s[k] = v;
+  }
+}
+
+__global__ void gather_cols_kernel(int rows, const double *__restrict__ src, int lds,
+                                   const int *__restrict__ idx, int count, double *__restrict__ dst,
+                                   int ldd) {
+  const long long total = (long long)rows * count;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % rows), j = (int)(t / rows);
+    dst[i + (long long)j * ldd] = src[i + (long long)idx[j] * lds];
+  }
+}
+
+void gather_cols(Ctx &c, int rows, const double *src, int lds, const int *idx_dev, int count,
+                 double *dst, int ldd) {
+  const long long total = (long long)rows * count;
+  if (!total) return;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  LAUNCH(c, gather_cols_kernel, blocks, 256, 0, rows, src, lds, idx_dev, count, dst, ldd);
+}
+
+// ttm along `mode`: out = core x_mode op(M), op(M) is p x r[mode]. If mt, M is stored as
+// r[mode] x p (leading dim ldm) and op(M) = M^T; otherwise M is p x r[mode] (leading dim ldm).
+void ttm(Ctx &c, const int r[3], const double *core, const double *M, int ldm, bool mt, int p,
+         int mode, double *out) {
+  if (mode == 0) {
+    gemm(c, mt, false, p, r[1] * r[2], r[0], 1.0, M, ldm, 0, core, r[0], 0, 0.0, out, p, 0);
+  } else if (mode == 1) {
+    gemm(c, false, !mt, r[0], p, r[1], 1.0, core, r[0], (long long)r[0] * r[1], M, ldm, 0, 0.0,
+         out, r[0], (long long)r[0] * p, r[2]);
+  } else {
+    gemm(c, false, !mt, r[0] * r[1], p, r[2], 1.0, core, r[0] * r[1], 0, M, ldm, 0, 0.0, out,
+         r[0] * r[1], 0);
+  }
+}
+
+int rank_from_tail(const std::vector<double> &lam_desc, double thr2) {
+  // smallest r such that sum_{i >= r} max(lam_i, 0) <= thr2
+  const int m = (int)lam_desc.size();
+  double tail = 0.0;
+  int r = m;
+  for (int i = m - 1; i >= 0; --i) {
+    const double v = std::max(lam_desc[i], 0.0);
+    if (tail + v > thr2) break;
+    tail += v;
+    r = i;
+  }
+  return std::max(r, 1);
+}
+
+}  // namespace
+
+void tucker_alloc(Ctx &c, Tucker &t, int cap) {
+  t.cap = cap;
+  for (int l = 0; l < 3; ++l) {
+    t.Q[l] = c.ws.dbl((size_t)c.n * cap);
+    t.r[l] = 0;
+  }
+  t.core = c.ws.dbl((size_t)cap * cap * cap);
+}
+
+void tucker_copy(Ctx &c, const Tucker &src, Tucker &dst) {
+  for (int l = 0; l < 3; ++l) {
+    dst.r[l] = src.r[l];
+    copy_d(c, dst.Q[l], src.Q[l], (size_t)c.n * src.r[l]);
+  }
+  copy_d(c, dst.core, src.core, (size_t)src.r[0] * src.r[1] * src.r[2]);
+}
+
+static bool tucker_empty(const Tucker &x) { return x.r[0] == 0 || x.r[1] == 0 || x.r[2] == 0; }
+
+void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
+  if (tucker_empty(x)) return;
+  const int n = c.n;
+  size_t mk = c.ws.mark();
+  const int r[3] = {x.r[0], x.r[1], x.r[2]};
+  const long long sz = (long long)r[0] * r[1] * r[2];
+  double *perm = c.ws.dbl(sz);
+  double *G[3], *lam[3], *U[3];
+  std::vector<double> lh[3];
+  for (int l = 0; l < 3; ++l) {
+    G[l] = c.ws.dbl((size_t)r[l] * r[l]);
+    lam[l] = c.ws.dbl(r[l]);
+    U[l] = c.ws.dbl((size_t)r[l] * r[l]);
+    const double *src = x.core;
+    if (l == 1) { permute3(c, r, x.core, 1, 0, 2, perm); src = perm; }
+    if (l == 2) { permute3(c, r, x.core, 2, 0, 1, perm); src = perm; }
+    // mode-l unfolding (r_l x rest), column-major with ld r_l
+    gemm(c, false, true, r[l], r[l], (int)(sz / r[l]), 1.0, src, r[l], 0, src, r[l], 0, 0.0, G[l],
+         r[l], 0);
+    sym_eig(c, r[l], 1, G[l], lam[l], U[l]);
+  }
+  double tot = 0.0;
+  for (int l = 0; l < 3; ++l) {
+    lh[l].resize(r[l]);
+    to_host(c, lh[l].data(), lam[l], r[l]);
+  }
+  for (double v : lh[0]) tot += std::max(v, 0.0);
+  if (!std::isfinite(tot)) fail(TCTL_E_NAN, "non-finite core in truncation");
+  if (tot == 0.0) {
+    x.r[0] = x.r[1] = x.r[2] = 0;
+    c.ws.reset(mk);
+    return;
+  }
+  int rn[3];
+  for (int l = 0; l < 3; ++l) rn[l] = rank_from_tail(lh[l], eps * eps * tot / 3.0);
+  // new core = core x_l U_l[:, :rn]^T
+  double *t1 = c.ws.dbl(sz), *t2 = c.ws.dbl(sz);
+  int rc[3] = {r[0], r[1], r[2]};
+  ttm(c, rc, x.core, U[0], r[0], true, rn[0], 0, t1);
+  rc[0] = rn[0];
+  ttm(c, rc, t1, U[1], r[1], true, rn[1], 1, t2);
+  rc[1] = rn[1];
+  ttm(c, rc, t2, U[2], r[2], true, rn[2], 2, x.core);
+  // new factors Q_l U_l[:, :rn]
+  double *Qt = c.ws.dbl((size_t)n * kMaxRank);
+  for (int l = 0; l < 3; ++l) {
+    gemm(c, false, false, n, rn[l], r[l], 1.0, x.Q[l], n, 0, U[l], r[l], 0, 0.0, Qt, n, 0);
+    copy_d(c, x.Q[l], Qt, (size_t)n * rn[l]);
+    x.r[l] = rn[l];
+  }
+  c.ws.reset(mk);
+}
+
+double tucker_inner(Ctx &c, const Tucker &x, const Tucker &y) {
+  if (tucker_empty(x) || tucker_empty(y)) return 0.0;
+  const int n = c.n;
+  size_t mk = c.ws.mark();
+  double *M[3];
+  for (int l = 0; l < 3; ++l) {
+    M[l] = c.ws.dbl((size_t)x.r[l] * y.r[l]);
+    gemm(c, true, false, x.r[l], y.r[l], n, 1.0, x.Q[l], n, 0, y.Q[l], n, 0, 0.0, M[l], x.r[l], 0);
+  }
+  const long long big = (long long)std::max(x.r[0], y.r[0]) * std::max(x.r[1], y.r[1]) *
+                        std::max(x.r[2], y.r[2]);
+  double *t1 = c.ws.dbl(big), *t2 = c.ws.dbl(big), *t3 = c.ws.dbl(big);
+  int rc[3] = {y.r[0], y.r[1], y.r[2]};
+  ttm(c, rc, y.core, M[0], x.r[0], false, x.r[0], 0, t1);
+  rc[0] = x.r[0];
+  ttm(c, rc, t1, M[1], x.r[1], false, x.r[1], 1, t2);
+  rc[1] = x.r[1];
+  ttm(c, rc, t2, M[2], x.r[2], false, x.r[2], 2, t3);
+  const double v = dot_host(c, (long long)x.r[0] * x.r[1] * x.r[2], x.core, t3);
+  c.ws.reset(mk);
+  return v;
+}
+
+void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucker &y, Tucker &z,
+                        double eps) {
+  const int n = c.n;
+  if (tucker_empty(x) || a == 0.0) {
+    tucker_copy(c, y, z);
+    axpby(c, (size_t)y.r[0] * y.r[1] * y.r[2], b, y.core, 0.0, z.core);
+    tucker_hosvd_trunc(c, z, eps);
+    return;
+  }
+  if (tucker_empty(y) || b == 0.0) {
+    tucker_copy(c, x, z);
+    axpby(c, (size_t)x.r[0] * x.r[1] * x.r[2], a, x.core, 0.0, z.core);
+    tucker_hosvd_trunc(c, z, eps);
+    return;
+  }
+  size_t mk = c.ws.mark();
+  double *My[3];
+  int rz[3];
+  double *Qz[3];
+  for (int l = 0; l < 3; ++l) {
+    const int rx = x.r[l], ry = y.r[l];
+    double *C1 = c.ws.dbl((size_t)rx * ry);
+    double *W = c.ws.dbl((size_t)n * ry);
+    // W = Q_y - Q_x (Q_x^T Q_y), twice (block classical Gram-Schmidt with reorthogonalisation)
+    gemm(c, true, false, rx, ry, n, 1.0, x.Q[l], n, 0, y.Q[l], n, 0, 0.0, C1, rx, 0);
+    copy_d(c, W, y.Q[l], (size_t)n * ry);
+    gemm(c, false, false, n, ry, rx, -1.0, x.Q[l], n, 0, C1, rx, 0, 1.0, W, n, 0);
+    double *C2 = c.ws.dbl((size_t)rx * ry);
+    gemm(c, true, false, rx, ry, n, 1.0, x.Q[l], n, 0, W, n, 0, 0.0, C2, rx, 0);
+    gemm(c, false, false, n, ry, rx, -1.0, x.Q[l], n, 0, C2, rx, 0, 1.0, W, n, 0);
+    Qz[l] = c.ws.dbl((size_t)n * kMaxRank);
+    copy_d(c, Qz[l], x.Q[l], (size_t)n * rx);
+    const int rw = orth(c, n, ry, W, n, 1e-8, false, std::max(0, kMaxRank - rx), Qz[l] + (size_t)n * rx);
+    rz[l] = rx + rw;
+    // coordinates of Q_y in [Q_x | Q_w]: [C1 + C2 ; Q_w^T Q_y]
+    My[l] = c.ws.dbl((size_t)rz[l] * ry);
+    gemm(c, true, false, rz[l], ry, n, 1.0, Qz[l], n, 0, y.Q[l], n, 0, 0.0, My[l], rz[l], 0);
+  }
+  const long long szz = (long long)rz[0] * rz[1] * rz[2];
+  double *core = c.ws.dbl(szz);
+  {
+    const int blocks = (int)std::min<long long>((szz + 255) / 256, 2048);
+    LAUNCH(c, embed3_kernel, blocks, 256, 0, x.r[0], x.r[1], x.r[2], x.core, rz[0], rz[1], rz[2], a,
+           core);
+  }
+  double *t1 = c.ws.dbl(szz), *t2 = c.ws.dbl(szz), *t3 = c.ws.dbl(szz);
+  int rc[3] = {y.r[0], y.r[1], y.r[2]};
+  ttm(c, rc, y.core, My[0], rz[0], false, rz[0], 0, t1);
+  rc[0] = rz[0];
+  ttm(c, rc, t1, My[1], rz[1], false, rz[1], 1, t2);
+  rc[1] = rz[1];
+  ttm(c, rc, t2, My[2], rz[2], false, rz[2], 2, t3);
+  axpby(c, (size_t)szz, b, t3, 1.0, core);
+  for (int l = 0; l < 3; ++l) {
+    z.r[l] = rz[l];
+    copy_d(c, z.Q[l], Qz[l], (size_t)n * rz[l]);
+  }
+  copy_d(c, z.core, core, (size_t)szz);
+  c.ws.reset(mk);
+  tucker_hosvd_trunc(c, z, eps);
+}
+
+void tucker_basis_change(Ctx &c, Tucker &x, bool to_eig) {
+  const int n = c.n;
+  size_t mk = c.ws.mark();
+  double *t = c.ws.dbl((size_t)n * kMaxRank);
+  for (int l = 0; l < 3; ++l) {
+    if (!x.r[l]) continue;
+    gemm(c, to_eig, false, n, x.r[l], n, 1.0, c.V[l], n, 0, x.Q[l], n, 0, 0.0, t, n, 0);
+    copy_d(c, x.Q[l], t, (size_t)n * x.r[l]);
+  }
+  c.ws.reset(mk);
+}
+
+void cp_to_tucker(Ctx &c, int m, const double *w, double *const U[3], bool to_eig, Tucker &out,
+                  double eps_core) {
+  const int n = c.n;
+  if (m == 0) {
+    out.r[0] = out.r[1] = out.r[2] = 0;
+    return;
+  }
+  size_t mk = c.ws.mark();
+  double *X[3], *nu[3];
+  for (int l = 0; l < 3; ++l) {
+    X[l] = c.ws.dbl((size_t)n * m);
+    if (to_eig)
+      gemm(c, true, false, n, m, n, 1.0, c.V[l], n, 0, U[l], n, 0, 0.0, X[l], n, 0);
+    else
+      copy_d(c, X[l], U[l], (size_t)n * m);
+    nu[l] = c.ws.dbl(m);
+    col_norms(c, n, m, X[l], n, nu[l]);
+  }
+  double *s = c.ws.dbl(m);
+  double *Y = c.ws.dbl((size_t)n * std::max(m, kMaxRank));
+  double *Ct[3];
+  for (int l = 0; l < 3; ++l) {
+    LAUNCH(c, side_scale_kernel, (m + 255) / 256, 256, 0, m, w, nu[0], nu[1], nu[2], l, s);
+    // weighted side matrix: column k of X_l times |w_k| prod_{q != l} ||x_qk||
+    copy_d(c, Y, X[l], (size_t)n * m);
+    scale_cols(c, n, m, Y, n, s, false);
+    int r;
+    if (m <= kMaxRank) {
+      r = orth(c, n, m, Y, n, 1e-8, true, kMaxRank, out.Q[l]);
+    } else {
+      double *Om = c.ws.dbl((size_t)m * kMaxRank);
+      double *Ys = c.ws.dbl((size_t)n * kMaxRank);
+      fill_gaussian(c, Om, (size_t)m * kMaxRank, c.o.seed * 0x9E3779B97F4A7C15ull + (c.rng_counter++));
+      gemm(c, false, false, n, kMaxRank, m, 1.0, Y, n, 0, Om, m, 0, 0.0, Ys, n, 0);
+      r = orth(c, n, kMaxRank, Ys, n, 1e-8, true, kMaxRank, out.Q[l]);
+    }
+    out.r[l] = r;
+    // C_l^T = X_l^T Q_l (m x r)
+    Ct[l] = c.ws.dbl((size_t)m * r);
+    gemm(c, true, false, m, r, n, 1.0, X[l], n, 0, out.Q[l], n, 0, 0.0, Ct[l], m, 0);
+  }
+  // core_(1) = (diag(w) C_1^T)^T KR(C_2^T, C_3^T) : (r0 x m) (m x r1 r2)
+  double *KR = c.ws.dbl((size_t)m * out.r[1] * out.r[2]);
+  khatri_rao(c, m, Ct[1], m, out.r[1], Ct[2], m, out.r[2], KR, m);
+  double *WC = c.ws.dbl((size_t)m * out.r[0]);
+  copy_d(c, WC, Ct[0], (size_t)m * out.r[0]);
+  // scale rows of WC by w: use scale_cols on the transpose view is not possible; do a gemm with
+  // diag via khatri_rao of (w as n=m x 1) and WC
+  khatri_rao(c, m, WC, m, out.r[0], w, m, 1, WC, m);
+  gemm(c, true, false, out.r[0], out.r[1] * out.r[2], m, 1.0, WC, m, 0, KR, m, 0, 0.0, out.core,
+       out.r[0], 0);
+  c.ws.reset(mk);
+  if (eps_core > 0) tucker_hosvd_trunc(c, out, eps_core);
+}
+
+// Y (n x ls) = mode-l unfolding of D .* X times ls Khatri-Rao Gaussian probes
+// (one Gaussian vector per other mode per probe). Cl: core permuted so mode l is first.
+static void sketch_mode(Ctx &c, const Sep &D, const Tucker &x, const double *Cl, int l, int ls,
+                        double *Y) {
+  const int n = c.n, R = D.R;
+  const int r[3] = {x.r[0], x.r[1], x.r[2]};
+  const int oth[3][2] = {{1, 2}, {0, 2}, {0, 1}};
+  const int m1 = oth[l][0], m2 = oth[l][1];
+  size_t mk = c.ws.mark();
+  double *P[3] = {nullptr, nullptr, nullptr};
+  for (int q = 0; q < 2; ++q) {
+    const int m = oth[l][q];
+    double *Om = c.ws.dbl((size_t)n * ls);
+    fill_gaussian(c, Om, (size_t)n * ls, c.o.seed * 0x9E3779B97F4A7C15ull + (c.rng_counter++));
+    // P_m[(a,s),k] = sum_i Q_m[i,a] Om[i,s] E_m[i,k] = (KR(Q_m, Om)^T B_m) Z_m
+    double *KRm = c.ws.dbl((size_t)n * r[m] * ls);
+    khatri_rao(c, n, x.Q[m], n, r[m], Om, n, ls, KRm, n);
+    double *T = c.ws.dbl((size_t)r[m] * ls * D.rD[m]);
+    gemm(c, true, false, r[m] * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, T, r[m] * ls, 0);
+    if (D.Z[m]) {
+      P[m] = c.ws.dbl((size_t)r[m] * ls * R);
+      gemm(c, false, false, r[m] * ls, R, D.rD[m], 1.0, T, r[m] * ls, 0, D.Z[m], D.rD[m], 0, 0.0,
+           P[m], r[m] * ls, 0);
+    } else {
+      P[m] = T;
+    }
+  }
+  // v[a,(s,k)] = w_k sum_{b,c} Cl[a,b,c] P_m1[(b,s),k] P_m2[(c,s),k], in chunks of k;
+  // uT[(a,s),p] = sum_k v[(a,s),k] Z_l[p,k]
+  double *uT = c.ws.dbl((size_t)r[l] * ls * D.rD[l]);
+  const long long per_k = (long long)r[l] * r[m1] * ls;
+  const int kc = (int)std::max<long long>(1, std::min<long long>(R, (32ll << 20) / std::max(per_k, 1ll)));
+  double *F = c.ws.dbl((size_t)per_k * kc);
+  double *v = c.ws.dbl((size_t)r[l] * ls * kc);
+  for (int k0 = 0; k0 < R; k0 += kc) {
+    const int nk = std::min(kc, R - k0);
+    gemm(c, false, false, r[l] * r[m1], ls * nk, r[m2], 1.0, Cl, r[l] * r[m1], 0,
+         P[m2] + (size_t)r[m2] * ls * k0, r[m2], 0, 0.0, F, r[l] * r[m1], 0);
+    const long long tot = (long long)r[l] * ls * nk;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+    LAUNCH(c, contract_b_kernel, blocks, 256, 0, r[l], r[m1], ls, nk, F,
+           P[m1] + (size_t)r[m1] * ls * k0, D.w + k0, v);
+    if (D.Z[l]) {
+      gemm(c, false, true, r[l] * ls, D.rD[l], nk, 1.0, v, r[l] * ls, 0,
+           D.Z[l] + (size_t)D.rD[l] * k0, D.rD[l], 0, k0 == 0 ? 0.0 : 1.0, uT, r[l] * ls, 0);
+    } else {
+      copy_d(c, uT + (size_t)r[l] * ls * k0, v, (size_t)r[l] * ls * nk);
+    }
+  }
+  // Y = KR(Q_l, B_l) (n x r_l rD) U2 (r_l rD x ls), U2[(a,p),s] = uT[(a,s),p]
+  double *U2 = c.ws.dbl((size_t)r[l] * D.rD[l] * ls);
+  {
+    const long long tot = (long long)r[l] * ls * D.rD[l];
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+    LAUNCH(c, perm_asp_kernel, blocks, 256, 0, r[l], ls, D.rD[l], uT, U2);
+  }
+  const int pc = std::max(1, std::min(D.rD[l], (int)((64ll << 20) / ((long long)n * r[l]))));
+  double *KRl = c.ws.dbl((size_t)n * r[l] * pc);
+  for (int p0 = 0; p0 < D.rD[l]; p0 += pc) {
+    const int np_ = std::min(pc, D.rD[l] - p0);
+    khatri_rao(c, n, x.Q[l], n, r[l], D.B[l] + (size_t)n * p0, n, np_, KRl, n);
+    gemm(c, false, false, n, ls, r[l] * np_, 1.0, KRl, n, 0, U2 + (size_t)r[l] * p0, r[l] * D.rD[l],
+         0, p0 == 0 ? 0.0 : 1.0, Y, n, 0);
+  }
+  c.ws.reset(mk);
+}
+
+void sep_apply_trunc(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, double eps) {
+  const int n = c.n;
+  if (tucker_empty(x)) {
+    y.r[0] = y.r[1] = y.r[2] = 0;
+    return;
+  }
+  const int R = D.R;
+  size_t mk = c.ws.mark();
+  const int r[3] = {x.r[0], x.r[1], x.r[2]};
+  int rmax = std::max(r[0], std::max(r[1], r[2]));
+  double *Qn[3];
+  int rn[3];
+  // permuted cores with mode l first: Cl[l] dims (r_l, r_m1, r_m2), m1 < m2 the other modes
+  double *Cl[3];
+  for (int l = 0; l < 3; ++l) {
+    Cl[l] = c.ws.dbl((size_t)r[0] * r[1] * r[2]);
+    if (l == 0) copy_d(c, Cl[0], x.core, (size_t)r[0] * r[1] * r[2]);
+    else if (l == 1) permute3(c, r, x.core, 1, 0, 2, Cl[1]);
+    else permute3(c, r, x.core, 2, 0, 1, Cl[2]);
+  }
+  // ---------------- range finding per mode
+  int ls = std::min(kMaxRank, rmax + 24);
+  for (int l = 0; l < 3; ++l) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      double *Y = c.ws.dbl((size_t)n * ls);
+      sketch_mode(c, D, x, Cl[l], l, ls, Y);
+      Qn[l] = c.ws.dbl((size_t)n * kMaxRank);
+      rn[l] = orth(c, n, ls, Y, n, 1e-8, true, kMaxRank, Qn[l]);
+      if (rn[l] < ls || ls >= kMaxRank) break;
+      ls = kMaxRank;  // saturated sketch: enlarge and redo this mode
+    }
+  }
+  // ---------------- core of D .* X in the new bases
+  double *M[3];
+  for (int l = 0; l < 3; ++l) {
+    // N_l[(a',b), p] = sum_i Qn[i,a'] Q[i,b] B[i,p];  M_l = N_l Z_l : (rn r) x R
+    double *KR = c.ws.dbl((size_t)n * rn[l] * r[l]);
+    khatri_rao(c, n, Qn[l], n, rn[l], x.Q[l], n, r[l], KR, n);
+    double *N = c.ws.dbl((size_t)rn[l] * r[l] * D.rD[l]);
+    gemm(c, true, false, rn[l] * r[l], D.rD[l], n, 1.0, KR, n, 0, D.B[l], n, 0, 0.0, N,
+         rn[l] * r[l], 0);
+    if (D.Z[l]) {
+      M[l] = c.ws.dbl((size_t)rn[l] * r[l] * R);
+      gemm(c, false, false, rn[l] * r[l], R, D.rD[l], 1.0, N, rn[l] * r[l], 0, D.Z[l], D.rD[l], 0,
+           0.0, M[l], rn[l] * r[l], 0);
+    } else {
+      M[l] = N;
+    }
+  }
+  const long long szo = (long long)rn[0] * rn[1] * rn[2];
+  double *nc = c.ws.dbl(szo);
+  {
+    const long long s1 = (long long)rn[0] * r[1] * r[2];
+    const long long s2 = (long long)rn[0] * r[1] * rn[2];
+    const long long s3 = szo;
+    const long long per = s1 + s2 + s3;
+    const int kc = (int)std::max<long long>(1, std::min<long long>(R, (48ll << 20) / per));
+    double *T1 = c.ws.dbl((size_t)s1 * kc), *T2 = c.ws.dbl((size_t)s2 * kc),
+           *T3 = c.ws.dbl((size_t)s3 * kc);
+    for (int k0 = 0; k0 < R; k0 += kc) {
+      const int nk = std::min(kc, R - k0);
+      // T1[k] = M_0k (rn0 x r0) * core (r0 x r1 r2)
+      gemm(c, false, false, rn[0], r[1] * r[2], r[0], 1.0, M[0] + (size_t)rn[0] * r[0] * k0, rn[0],
+           (long long)rn[0] * r[0], x.core, r[0], 0, 0.0, T1, rn[0], s1, nk);
+      // T2[k] = T1[k] (rn0 r1 x r2) * M_2k^T (r2 x rn2)
+      gemm(c, false, true, rn[0] * r[1], rn[2], r[2], 1.0, T1, rn[0] * r[1], s1,
+           M[2] + (size_t)rn[2] * r[2] * k0, rn[2], (long long)rn[2] * r[2], 0.0, T2, rn[0] * r[1],
+           s2, nk);
+      // T3[k][:,:,c] = T2[k][:,:,c] (rn0 x r1) * M_1k^T (r1 x rn1), batch over (k, c)
+      gemm(c, false, true, rn[0], rn[1], r[1], 1.0, T2, rn[0], (long long)rn[0] * r[1],
+           M[1] + (size_t)rn[1] * r[1] * k0, rn[1], (long long)rn[1] * r[1], 0.0, T3, rn[0],
+           (long long)rn[0] * rn[1], nk * rn[2], 1, rn[2]);
+      // nc += T3 w
+      gemm(c, false, false, (int)szo, 1, nk, 1.0, T3, (int)szo, 0, D.w + k0, nk, 0,
+           k0 == 0 ? 0.0 : 1.0, nc, (int)szo, 0);
+    }
+  }
+  for (int l = 0; l < 3; ++l) {
+    y.r[l] = rn[l];
+    copy_d(c, y.Q[l], Qn[l], (size_t)n * rn[l]);
+  }
+  copy_d(c, y.core, nc, (size_t)szo);
+  c.ws.reset(mk);
+  tucker_hosvd_trunc(c, y, eps);
+}
+
+int tucker_to_cp(Ctx &c, const Tucker &x, bool from_eig, double eps, tctl_cp *y) {
+  const int n = c.n;
+  if (tucker_empty(x)) {
+    y->rank = 0;
+    return TCTL_OK;
+  }
+  size_t mk = c.ws.mark();
+  const int r0 = x.r[0], r1 = x.r[1], r2 = x.r[2];
+  double *Qp[3];
+  for (int l = 0; l < 3; ++l) {
+    Qp[l] = c.ws.dbl((size_t)n * x.r[l]);
+    if (from_eig)
+      gemm(c, false, false, n, x.r[l], n, 1.0, c.V[l], n, 0, x.Q[l], n, 0, 0.0, Qp[l], n, 0);
+    else
+      copy_d(c, Qp[l], x.Q[l], (size_t)n * x.r[l]);
+  }
+  // slice Grams S_c^T S_c (r1 x r1), batch r2
+  double *G = c.ws.dbl((size_t)r1 * r1 * r2);
+  gemm(c, true, false, r1, r1, r0, 1.0, x.core, r0, (long long)r0 * r1, x.core, r0,
+       (long long)r0 * r1, 0.0, G, r1, (long long)r1 * r1, r2, 1, 1);
+  double *lam = c.ws.dbl((size_t)r1 * r2), *Bv = c.ws.dbl((size_t)r1 * r1 * r2);
+  sym_eig(c, r1, r2, G, lam, Bv);
+  // A_c = S_c Bv_c (r0 x r1); columns later divided by sigma
+  double *Av = c.ws.dbl((size_t)r0 * r1 * r2);
+  gemm(c, false, false, r0, r1, r1, 1.0, x.core, r0, (long long)r0 * r1, Bv, r1, (long long)r1 * r1,
+       0.0, Av, r0, (long long)r0 * r1, r2, 1, 1);
+  std::vector<double> lh((size_t)r1 * r2);
+  to_host(c, lh.data(), lam, lh.size());
+  double tot = 0.0;
+  for (double v : lh) tot += std::max(v, 0.0);
+  struct Trip {
+    double s2;
+    int c, i;
+  };
+  std::vector<Trip> trips;
+  for (int cc = 0; cc < r2; ++cc)
+    for (int i = 0; i < std::min(r0, r1); ++i) trips.push_back({std::max(lh[i + (size_t)cc * r1], 0.0), cc, i});
+  std::vector<int> order(trips.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return trips[a].s2 < trips[b].s2; });
+  std::vector<char> drop(trips.size(), 0);
+  double acc = 0.0;
+  for (int j : order) {
+    if (acc + trips[j].s2 > eps * eps * tot) break;
+    acc += trips[j].s2;
+    drop[j] = 1;
+  }
+  std::vector<int> ia, ib, ic;
+  std::vector<double> wv, inv;
+  for (size_t j = 0; j < trips.size(); ++j) {
+    if (drop[j] || trips[j].s2 <= 0.0) continue;
+    const double sg = std::sqrt(trips[j].s2);
+    ia.push_back(trips[j].i + trips[j].c * r1);  // column of Av / Bv (slice-major)
+    ic.push_back(trips[j].c);
+    wv.push_back(sg);
+    inv.push_back(1.0 / sg);
+  }
+  const int rank = (int)wv.size();
+  int status = TCTL_OK;
+  int keep = rank;
+  if (rank > y->cap) {
+    status = TCTL_E_RANK_CAP;
+    keep = y->cap;
+  }
+  if (keep > 0) {
+    int *idx = c.ws.i32(keep), *idc = c.ws.i32(keep);
+    TCTL_CUDA(cudaMemcpyAsync(idx, ia.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.st));
+    TCTL_CUDA(cudaMemcpyAsync(idc, ic.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.st));
+    double *Asel = c.ws.dbl((size_t)r0 * keep), *Bsel = c.ws.dbl((size_t)r1 * keep);
+    double *invd = c.ws.dbl(keep);
+    to_dev(c, invd, inv.data(), keep);
+    gather_cols(c, r0, Av, r0, idx, keep, Asel, r0);
+    scale_cols(c, r0, keep, Asel, r0, invd, false);
+    gather_cols(c, r1, Bv, r1, idx, keep, Bsel, r1);
+    gemm(c, false, false, n, keep, r0, 1.0, Qp[0], n, 0, Asel, r0, 0, 0.0, y->U[0], n, 0);
+    gemm(c, false, false, n, keep, r1, 1.0, Qp[1], n, 0, Bsel, r1, 0, 0.0, y->U[1], n, 0);
+    gather_cols(c, n, Qp[2], n, idc, keep, y->U[2], n);
+    to_dev(c, y->w, wv.data(), keep);
+    TCTL_CUDA(cudaStreamSynchronize(c.st));
+  }
+  y->rank = keep;
+  c.ws.reset(mk);
+  return status;
+}
+
+}  // namespace tctl

