@@ -159,6 +159,36 @@ int tctl_get_stats(tctl_ctx *ctx, tctl_stats *st);
  * kept by the library's own launch wrappers). */
 long long tctl_launch_count(const tctl_ctx *ctx);
 
+/* Allocation-free 1D eigendecompositions, for callers that cannot allocate
+ * device memory: code running where cudaMalloc is not allowed or not wanted,
+ * e.g. inside another library's memory pool, a stream-ordered pipeline whose
+ * owner controls every allocation, or an embedded runtime with a fixed memory
+ * budget. The paper has no counterpart of this entry point; it computes the
+ * same eigenpairs as tctl_setup (the three A_(l) of Section 3.2 and their
+ * eigendecompositions), so its outputs match tctl_get_eigs for the same
+ * coefficients, without creating a context.
+ *   coeffs: DEVICE, 3 x (n+1) doubles (row l = a_l(x_{i-1/2}), i = 1..n+1).
+ *   lam:    DEVICE, 3 x n doubles, ascending per mode (output).
+ *   V:      DEVICE, 3 x n x n doubles; mode l at V + l*n*n, column-major,
+ *           eigenvectors as columns, signs as in tctl_get_eigs (output).
+ *   cuda_stream: cudaStream_t (NULL = default stream); the call synchronizes
+ *           the stream once (coefficient check) and leaves the eigensolver
+ *           kernels queued on it.
+ * Scratch comes from a file-scope device array sized for n <=
+ * TCTL_EIG_NOALLOC_MAX_N (about 3.2 MB, held by every device that loads the
+ * library until the process exits); no cudaMalloc, cudaFree or allocating
+ * library routine is called. The first call on a device looks up the array's
+ * device address (one-time set-up); make that first call before any stream
+ * capture. All calls on a device share the array: calls whose GPU work
+ * overlaps (different streams, or host threads without ordering) race and
+ * corrupt each other's results; serialize them.
+ * Errors: TCTL_E_ARG (NULL pointer, n < 2 or n > TCTL_EIG_NOALLOC_MAX_N),
+ * TCTL_E_COEFF (a coefficient <= 0 or not finite), TCTL_E_CUDA.
+ * tctl_last_error(NULL) describes the failure. */
+#define TCTL_EIG_NOALLOC_MAX_N 256
+int tctl_eig1d_noalloc(const double *coeffs, int n, int paper_end_rows, double *lam,
+                       double *V, void *cuda_stream);
+
 /* Per-kernel timing (tracing): when enabled, the context records a pair of
  * CUDA events on its stream around every kernel it launches. The report is a
  * JSON object {kernel: {"launches", "ms", "flops"}} aggregated over the

@@ -73,6 +73,8 @@ void apply_sep(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, Tucker &tmp, do
 
 namespace tctl {
 
+void set_noalloc_error(const std::string &msg) { g_last_error = msg; }
+
 int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
   Timer timer(c.st);
   const double eps = c.eps;

@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "tctl_internal.cuh"
 
@@ -217,3 +219,117 @@ void setup_eigs(Ctx &c) {
 }
 
 }  // namespace tctl
+
+// ------------------------------------------------------------------ allocation-free entry point
+// tctl_eig1d_noalloc runs the same assembly, bisection and twisted-factorization
+// kernels as tctl_setup, but takes its scratch (tridiagonal entries, Gershgorin
+// bounds, the per-eigenvector D+ and backward-multiplier arrays, an error flag)
+// from the file-scope device array below instead of cudaMalloc. The array is
+// sized for n <= TCTL_EIG_NOALLOC_MAX_N and is resident on every device that
+// loads the library until the process exits.
+namespace tctl {
+namespace {
+
+constexpr int kNoAllocMaxN = TCTL_EIG_NOALLOC_MAX_N;
+constexpr size_t kNoAllocDoubles =
+    (size_t)6 * kNoAllocMaxN * kNoAllocMaxN + (size_t)6 * kNoAllocMaxN + 16;
+
+}  // namespace
+}  // namespace tctl
+
+static __device__ __align__(256) double g_eig_noalloc_scratch[tctl::kNoAllocDoubles];
+
+namespace tctl {
+namespace {
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[256] = {};  // device address of the scratch, per device ordinal
+
+__global__ void coeff_check_kernel(int count, const double *__restrict__ coef, int *flag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const double v = coef[i];
+    if (!(v > 0.0) || !isfinite(v)) atomicExch(flag, 1);
+  }
+}
+
+}  // namespace
+}  // namespace tctl
+
+extern "C" int tctl_eig1d_noalloc(const double *coeffs, int n, int paper_end_rows, double *lam,
+                                  double *V, void *cuda_stream) {
+  using namespace tctl;
+  if (!coeffs || !lam || !V) {
+    set_noalloc_error("tctl_eig1d_noalloc: NULL pointer argument");
+    return TCTL_E_ARG;
+  }
+  if (n < 2 || n > kNoAllocMaxN) {
+    set_noalloc_error("tctl_eig1d_noalloc: n = " + std::to_string(n) +
+                      " is outside [2, TCTL_EIG_NOALLOC_MAX_N = " + std::to_string(kNoAllocMaxN) +
+                      "]; use tctl_setup for larger grids");
+    return TCTL_E_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    set_noalloc_error("tctl_eig1d_noalloc: cudaGetDevice failed");
+    return TCTL_E_CUDA;
+  }
+  double *base = nullptr;
+  {
+    // one-time set-up per device: the host-side name of the array is not a
+    // device address, so its address is looked up with the device current.
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void *p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_eig_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        set_noalloc_error(std::string("tctl_eig1d_noalloc: cudaGetSymbolAddress failed: ") +
+                          cudaGetErrorString(e));
+        return TCTL_E_CUDA;
+      }
+      g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  const size_t nn = (size_t)n * n;
+  double *d = base;                  // 3 n
+  double *e = d + 3 * (size_t)n;     // 3 n (n-1 used per mode)
+  double *bounds = e + 3 * (size_t)n;  // 12
+  int *flag = reinterpret_cast<int *>(bounds + 12);  // 1 int (in a 4-double slot)
+  double *Dp = bounds + 16;          // 3 n^2
+  double *Um = Dp + 3 * nn;          // 3 n^2
+  auto fail_cuda = [&](const char *what) {
+    set_noalloc_error(std::string("tctl_eig1d_noalloc: ") + what + ": " +
+                      cudaGetErrorString(cudaGetLastError()));
+    return TCTL_E_CUDA;
+  };
+  // the coefficient flag must start at zero on every call
+  if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return fail_cuda("memset");
+  coeff_check_kernel<<<(3 * (n + 1) + 255) / 256, 256, 0, st>>>(3 * (n + 1), coeffs, flag);
+  int hflag = 0;
+  if (cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail_cuda("coefficient check");
+  if (hflag) {
+    set_noalloc_error("tctl_eig1d_noalloc: coefficient a_l(x) must be positive and finite");
+    return TCTL_E_COEFF;
+  }
+  double *dm[3], *em[3], *lm[3], *Vm[3];
+  for (int l = 0; l < 3; ++l) {
+    dm[l] = d + (size_t)l * n;
+    em[l] = e + (size_t)l * n;
+    lm[l] = lam + (size_t)l * n;
+    Vm[l] = V + (size_t)l * nn;
+  }
+  dim3 ga((n + 255) / 256, 3);
+  assemble_kernel<<<ga, 256, 0, st>>>(n, coeffs, paper_end_rows, dm[0], dm[1], dm[2], em[0], em[1],
+                                      em[2]);
+  gersh_kernel<<<3, 256, 0, st>>>(n, dm[0], dm[1], dm[2], em[0], em[1], em[2], bounds);
+  dim3 gb((n + 63) / 64, 3);
+  bisect_kernel<<<gb, 64, 0, st>>>(n, dm[0], dm[1], dm[2], em[0], em[1], em[2], bounds, lm[0], lm[1],
+                                   lm[2]);
+  twisted_kernel<<<gb, 64, 0, st>>>(n, dm[0], dm[1], dm[2], em[0], em[1], em[2], bounds, lm[0],
+                                    lm[1], lm[2], Vm[0], Vm[1], Vm[2], Dp, Um);
+  if (cudaGetLastError() != cudaSuccess) return fail_cuda("kernel launch");
+  return TCTL_OK;
+}

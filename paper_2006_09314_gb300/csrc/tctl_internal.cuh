@@ -176,6 +176,9 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps);
 // Apply V_l (from_eig) or V_l^T (to_eig) to the Tucker factors in place.
 void tucker_basis_change(Ctx &c, Tucker &x, bool to_eig);
 
+// Records the message returned by tctl_last_error(NULL) (entry points without a context).
+void set_noalloc_error(const std::string &msg);
+
 // ------------------------------------------------------------ pcg.cu
 int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st);
 

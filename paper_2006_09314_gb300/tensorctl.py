@@ -34,7 +34,7 @@ EXPORTED = [
     "tctl_truncate", "tctl_pcg_solve", "tctl_fullgrid_solve", "tctl_fullgrid_state",
     "tctl_solve_host", "tctl_cp_alloc", "tctl_cp_free", "tctl_get_eigs",
     "tctl_get_stats", "tctl_launch_count", "tctl_destroy", "tctl_last_error",
-    "tctl_profile_enable", "tctl_profile_report",
+    "tctl_profile_enable", "tctl_profile_report", "tctl_eig1d_noalloc",
 ]
 
 ERRORS = {0: "OK", -1: "E_ARG", -2: "E_COEFF", -3: "E_CUDA", -4: "E_NOMEM",
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
         "tctl_destroy": (None, [P]),
         "tctl_profile_enable": (I, [P, I]),
         "tctl_profile_report": (I, [P, ctypes.c_char_p, I]),
+        "tctl_eig1d_noalloc": (I, [P, I, I, P, P, P]),
         "tctl_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -297,6 +298,19 @@ def tctl_profile_report(ctx):
     buf = ctypes.create_string_buffer(1 << 16)
     _check(load().tctl_profile_report(ctx, buf, len(buf)), ctx)
     return json.loads(buf.value.decode())
+
+
+def tctl_eig1d_noalloc(coeffs_dev, n, lam_dev, V_dev, paper_end_rows=0, stream=None):
+    """Allocation-free eigendecompositions into caller-provided device tensors.
+
+    coeffs_dev: (3, n+1) float64 CUDA tensor; lam_dev: (3, n); V_dev: (3, n, n)
+    (V_dev[l].T is the column-major eigenvector matrix of mode l).
+    """
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().tctl_eig1d_noalloc(coeffs_dev.data_ptr(), int(n), int(paper_end_rows),
+                                     lam_dev.data_ptr(), V_dev.data_ptr(), ctypes.c_void_p(stream)))
 
 
 def tctl_destroy(ctx):
