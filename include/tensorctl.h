@@ -100,7 +100,9 @@ int tctl_default_opts(tctl_opts *o);
  * FP64, the spectral interval, the sinc exp-sum of F2 (Section 3.4) and the
  * preconditioner exp-sum (Section 3.5, case (B)), and their factor matrices.
  * n >= 2, 0 < alpha <= 1, beta > 0, eps_trunc in (0, 1). opts may be NULL.
- * cuda_stream: a cudaStream_t (NULL = default stream). Synchronizes once.
+ * cuda_stream: a cudaStream_t (NULL = the calling host thread's default
+ * stream: the library is built with per-thread default streams; pass
+ * cudaStreamLegacy for the legacy default stream). Synchronizes once.
  * Errors: TCTL_E_ARG, TCTL_E_COEFF, TCTL_E_NOMEM, TCTL_E_CUDA, TCTL_E_NUMERIC. */
 int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha,
                double beta, double eps_trunc, const tctl_opts *opts,
@@ -171,7 +173,8 @@ long long tctl_launch_count(const tctl_ctx *ctx);
  *   lam:    DEVICE, 3 x n doubles, ascending per mode (output).
  *   V:      DEVICE, 3 x n x n doubles; mode l at V + l*n*n, column-major,
  *           eigenvectors as columns, signs as in tctl_get_eigs (output).
- *   cuda_stream: cudaStream_t (NULL = default stream); the call synchronizes
+ *   cuda_stream: cudaStream_t (NULL = the calling thread's default stream);
+ *           the call synchronizes
  *           the stream once (coefficient check) and leaves the eigensolver
  *           kernels queued on it.
  * Scratch comes from a file-scope device array sized for n <=

@@ -180,9 +180,12 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
   const long long tiles = (long long)gx * gy * batch;
   int splits = 1;
   const int target = 2 * 152;
-  if (tiles < target && k >= 512) {
-    splits = (int)std::min<long long>((target + tiles - 1) / tiles, (k + 255) / 256);
-    splits = std::max(1, std::min(splits, 64));
+  if (tiles < target && k >= 4 * GEMM_BK) {
+    // tall-skinny products (Gram matrices, projections with K = n): split K so that
+    // about two CTAs per SM run; chunks down to one 16-deep tile.
+    splits = (int)std::min<long long>((target + tiles - 1) / tiles, (k + GEMM_BK - 1) / GEMM_BK);
+    const long long cap = std::max<long long>(1, (16ll << 20) / ((long long)m * n * batch));
+    splits = (int)std::max<long long>(1, std::min<long long>({(long long)splits, 256ll, cap}));
   }
   int kchunk = (k + splits - 1) / splits;
   kchunk = ((kchunk + GEMM_BK - 1) / GEMM_BK) * GEMM_BK;
@@ -357,12 +360,21 @@ void to_dev(Ctx &c, double *dst, const double *src, size_t count) {
 // ------------------------------------------------------------------ Jacobi
 // Parallel cyclic Jacobi (round-robin pairing) for symmetric m x m, m <= 64.
 // One CTA per matrix; A and V in shared memory (padded to even size mp).
+// Matrix b of the launch has size ms[b] and lives at As[b] (ld ms[b]); its
+// eigenvalues (descending) go to lams[b], eigenvectors (columns) to Vs[b].
 constexpr int JMAX = 64;
 
-__global__ void __launch_bounds__(256) jacobi_kernel(int m, const double *__restrict__ Ain,
-                                                     double *__restrict__ lam,
-                                                     double *__restrict__ Vout) {
+struct EigDesc {
+  const double *A;
+  double *lam;
+  double *V;
+  int m;
+};
+
+__global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__ desc) {
   extern __shared__ double sm[];
+  const EigDesc dsc = desc[blockIdx.x];
+  const int m = dsc.m;
   const int mp = (m + 1) & ~1;
   const int ld = mp + 1;
   double *A = sm;               // mp x ld
@@ -371,8 +383,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int m, const double *__rest
   int *pq = reinterpret_cast<int *>(cs + mp);  // 2 * (mp/2)
   __shared__ double red[8];
   __shared__ int done;
-  const int b = blockIdx.x;
-  const double *Ab = Ain + (long long)b * m * m;
+  const double *Ab = dsc.A;
   for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
     const int i = t % mp, j = t / mp;
     A[i + j * ld] = (i < m && j < m) ? Ab[i + j * m] : 0.0;
@@ -380,7 +391,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int m, const double *__rest
   }
   __syncthreads();
   const int half = mp / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  for (int sweep = 0; sweep < 40 && mp > 1; ++sweep) {
     // convergence test: off-diagonal vs total Frobenius mass
     double off = 0.0, tot = 0.0;
     for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
@@ -393,9 +404,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int m, const double *__rest
       off += __shfl_down_sync(0xffffffffu, off, o);
       tot += __shfl_down_sync(0xffffffffu, tot, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-      red[threadIdx.x >> 5] = off;
-    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
@@ -467,15 +476,20 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int m, const double *__rest
       const double dj = A[j + j * ld];
       rank += (dj > di) || (dj == di && j < i);
     }
-    lam[(long long)b * m + rank] = di;
-    for (int r = 0; r < m; ++r) Vout[(long long)b * m * m + r + (long long)rank * m] = V[r + i * ld];
+    dsc.lam[rank] = di;
+    for (int r = 0; r < m; ++r) dsc.V[r + (long long)rank * m] = V[r + i * ld];
   }
 }
 
-void sym_eig(Ctx &c, int m, int batch, const double *A, double *lam, double *Vout) {
-  if (m <= 0 || batch <= 0) return;
-  if (m > JMAX) fail(TCTL_E_ARG, "sym_eig: m > 64");
-  const int mp = (m + 1) & ~1;
+static void jacobi_launch(Ctx &c, const std::vector<EigDesc> &d) {
+  if (d.empty()) return;
+  int mmax = 0;
+  for (const EigDesc &e : d) {
+    if (e.m > JMAX) fail(TCTL_E_ARG, "sym_eig: m > 64");
+    mmax = std::max(mmax, e.m);
+  }
+  if (mmax <= 0) return;
+  const int mp = (mmax + 1) & ~1;
   const size_t smem = sizeof(double) * (2 * mp * (mp + 1) + mp) + sizeof(int) * mp;
   static bool attr = false;
   if (!attr) {
@@ -483,7 +497,29 @@ void sym_eig(Ctx &c, int m, int batch, const double *A, double *lam, double *Vou
                                    100 * 1024));
     attr = true;
   }
-  LAUNCH(c, jacobi_kernel, batch, 256, smem, m, A, lam, Vout);
+  size_t mk = c.ws.mark();
+  EigDesc *dd = static_cast<EigDesc *>(c.ws.alloc(sizeof(EigDesc) * d.size()));
+  TCTL_CUDA(cudaMemcpyAsync(dd, d.data(), sizeof(EigDesc) * d.size(), cudaMemcpyHostToDevice, c.st));
+  LAUNCH(c, jacobi_kernel, (int)d.size(), 256, smem, dd);
+  // the descriptor buffer must outlive the (asynchronous) launch
+  TCTL_CUDA(cudaStreamSynchronize(c.st));
+  c.ws.reset(mk);
+}
+
+void sym_eig(Ctx &c, int m, int batch, const double *A, double *lam, double *Vout) {
+  if (m <= 0 || batch <= 0) return;
+  std::vector<EigDesc> d(batch);
+  for (int b = 0; b < batch; ++b)
+    d[b] = EigDesc{A + (size_t)b * m * m, lam + (size_t)b * m, Vout + (size_t)b * m * m, m};
+  jacobi_launch(c, d);
+}
+
+void sym_eig_multi(Ctx &c, int count, const int *m, const double *const *A, double *const *lam,
+                   double *const *Vout) {
+  std::vector<EigDesc> d;
+  for (int b = 0; b < count; ++b)
+    if (m[b] > 0) d.push_back(EigDesc{A[b], lam[b], Vout[b], m[b]});
+  jacobi_launch(c, d);
 }
 
 // ------------------------------------------------------------------ orth

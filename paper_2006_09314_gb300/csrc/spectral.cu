@@ -211,6 +211,84 @@ void build_sep(Ctx &c, Sep &D, const std::vector<double> &w, const std::vector<T
   c.ws.reset(mk);
 }
 
+__global__ void term_scale_kernel(int R, const double *__restrict__ w, const double *__restrict__ n0,
+                                  const double *__restrict__ n1, const double *__restrict__ n2,
+                                  int l, double *__restrict__ s) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < R; k += gridDim.x * blockDim.x) {
+    double v = fabs(w[k]);
+    if (l != 0) v *= n0[k];
+    if (l != 1) v *= n1[k];
+    if (l != 2) v *= n2[k];
+    s[k] = v;
+  }
+}
+
+double frob2(Ctx &c, int n, int m, const double *A, double *tmp) {
+  col_norms(c, n, m, A, n, tmp);
+  std::vector<double> h(m);
+  to_host(c, h.data(), tmp, m);
+  double s = 0;
+  for (double v : h) s += v * v;
+  return s;
+}
+
+// Per-mode orthonormal basis B_l (n x rD_l) of the factor columns of D, weighted by the
+// term weight and the other modes' column norms, found by randomized range finding with
+// deflation (each round resolves ~1e-7 of what is left), until the weighted residual is
+// below tol in relative Frobenius norm; then Z_l = B_l^T E_l. Falls back to the plain
+// factors (Z = identity) if the basis would not be smaller than R/2.
+void compress_sep(Ctx &c, Sep &D, double tol) {
+  const int n = c.n, R = D.R;
+  const int capD = std::min(R / 2, 192);
+  if (capD < 8) return;
+  size_t mk = c.ws.mark();
+  double *nrm[3];
+  for (int l = 0; l < 3; ++l) {
+    nrm[l] = c.ws.dbl(R);
+    col_norms(c, n, R, D.E[l], n, nrm[l]);
+  }
+  double *sc = c.ws.dbl(R), *tmp = c.ws.dbl(R);
+  double *W = c.ws.dbl((size_t)n * R);
+  double *Om = c.ws.dbl((size_t)R * 64), *Y = c.ws.dbl((size_t)n * 64), *Qr = c.ws.dbl((size_t)n * 64);
+  double *C = c.ws.dbl((size_t)64 * R), *C2 = c.ws.dbl((size_t)capD * 64);
+  for (int l = 0; l < 3; ++l) {
+    LAUNCH(c, term_scale_kernel, (R + 255) / 256, 256, 0, R, D.w, nrm[0], nrm[1], nrm[2], l, sc);
+    copy_d(c, W, D.E[l], (size_t)n * R);
+    scale_cols(c, n, R, W, n, sc, false);
+    const double total2 = frob2(c, n, R, W, tmp);
+    double *Bq = c.dmalloc((size_t)n * capD);
+    int rD = 0;
+    bool ok = false;
+    for (int round = 0; round < 8 && rD < capD; ++round) {
+      fill_gaussian(c, Om, (size_t)R * 64, 0xC0FFEEull * (l + 1) + round);
+      gemm(c, false, false, n, 64, R, 1.0, W, n, 0, Om, R, 0, 0.0, Y, n, 0);
+      for (int pass = 0; pass < 2 && rD > 0; ++pass) {
+        gemm(c, true, false, rD, 64, n, 1.0, Bq, n, 0, Y, n, 0, 0.0, C2, rD, 0);
+        gemm(c, false, false, n, 64, rD, -1.0, Bq, n, 0, C2, rD, 0, 1.0, Y, n, 0);
+      }
+      const int q = orth(c, n, 64, Y, n, 1e-7, true, std::min(64, capD - rD), Qr);
+      if (q == 0) break;
+      copy_d(c, Bq + (size_t)n * rD, Qr, (size_t)n * q);
+      rD += q;
+      // deflate: W -= Qr (Qr^T W)
+      gemm(c, true, false, q, R, n, 1.0, Qr, n, 0, W, n, 0, 0.0, C, q, 0);
+      gemm(c, false, false, n, R, q, -1.0, Qr, n, 0, C, q, 0, 1.0, W, n, 0);
+      const double res2 = frob2(c, n, R, W, tmp);
+      if (res2 <= tol * tol * total2) {
+        ok = true;
+        break;
+      }
+    }
+    if (!ok) continue;  // keep the plain factors for this mode
+    D.B[l] = Bq;
+    D.rD[l] = rD;
+    D.Z[l] = c.dmalloc((size_t)rD * R);
+    gemm(c, true, false, rD, R, n, 1.0, Bq, n, 0, D.E[l], n, 0, 0.0, D.Z[l], rD, 0);
+  }
+  TCTL_CUDA(cudaStreamSynchronize(c.st));
+  c.ws.reset(mk);
+}
+
 }  // namespace
 
 void setup_spectral(Ctx &c) {
@@ -270,6 +348,7 @@ void setup_spectral(Ctx &c) {
     c.op_rel_err = emax;
   }
   build_sep(c, c.op, w, td);
+  compress_sep(c, c.op, 1e-13);
 
   // ---- preconditioner P(s) = s sum_k p_k exp(-theta_k s), NNLS weights
   const int K = std::max(1, c.o.r_pre);
@@ -303,6 +382,7 @@ void setup_spectral(Ctx &c) {
   }
   if (pw.empty()) fail(TCTL_E_NUMERIC, "preconditioner fit produced no positive weight");
   build_sep(c, c.pre, pw, ptd);
+  compress_sep(c, c.pre, 1e-13);
 }
 
 // ------------------------------------------------------------------ full grid

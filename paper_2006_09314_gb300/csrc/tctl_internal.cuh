@@ -130,6 +130,9 @@ void khatri_rao(Ctx &c, int n, const double *A, int lda, int ra, const double *B
 // `batch` m x m matrices (ld m, contiguous); eigenvalues descending in lam
 // (batch x m), eigenvectors as columns in Vout (batch x m x m). m <= 64.
 void sym_eig(Ctx &c, int m, int batch, const double *A, double *lam, double *Vout);
+// Several symmetric eigenproblems of different sizes (<= 64) in one launch.
+void sym_eig_multi(Ctx &c, int count, const int *m, const double *const *A, double *const *lam,
+                   double *const *Vout);
 // Orthonormal basis of span(Y) (n x m, m <= 64) by pivoted Cholesky of Y^T Y:
 // columns whose residual norm falls below tol * (reference) are dropped, where
 // reference = max column norm (relative=true) or 1 (relative=false). Writes Q

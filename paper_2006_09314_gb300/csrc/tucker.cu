@@ -231,8 +231,8 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
     // mode-l unfolding (r_l x rest), column-major with ld r_l
     gemm(c, false, true, r[l], r[l], (int)(sz / r[l]), 1.0, src, r[l], 0, src, r[l], 0, 0.0, G[l],
          r[l], 0);
-    sym_eig(c, r[l], 1, G[l], lam[l], U[l]);
   }
+  sym_eig_multi(c, 3, r, G, lam, U);
   double tot = 0.0;
   for (int l = 0; l < 3; ++l) {
     lh[l].resize(r[l]);

@@ -194,6 +194,10 @@ def tctl_setup(coeffs, n, alpha, beta, eps_trunc, opts=None, stream=None):
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
+    if stream == 0:
+        # torch's default stream is the legacy default stream; the library is built
+        # with per-thread default streams, so name the legacy stream explicitly
+        stream = 1  # cudaStreamLegacy
     _check(lib.tctl_setup(ctypes.byref(ctx), coeffs.ctypes.data, int(n), float(alpha),
                           float(beta), float(eps_trunc),
                           ctypes.byref(opts) if opts is not None else None,
@@ -309,6 +313,8 @@ def tctl_eig1d_noalloc(coeffs_dev, n, lam_dev, V_dev, paper_end_rows=0, stream=N
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
+    if stream == 0:
+        stream = 1  # cudaStreamLegacy (see tctl_setup)
     _check(load().tctl_eig1d_noalloc(coeffs_dev.data_ptr(), int(n), int(paper_end_rows),
                                      lam_dev.data_ptr(), V_dev.data_ptr(), ctypes.c_void_p(stream)))
 

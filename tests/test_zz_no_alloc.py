@@ -30,8 +30,9 @@ from paper_2006_09314_gb300 import tensorctl as T  # noqa: E402
 def _noalloc(lib, coef, n, stream):
     lam = torch.full((3, n), float("nan"), dtype=torch.float64, device="cuda")
     V = torch.full((3, n, n), float("nan"), dtype=torch.float64, device="cuda")
+    handle = stream.cuda_stream or 1  # torch's default stream is the legacy stream (handle 1)
     rc = lib.tctl_eig1d_noalloc(coef.data_ptr(), n, 0, lam.data_ptr(), V.data_ptr(),
-                                ctypes.c_void_p(stream.cuda_stream))
+                                ctypes.c_void_p(handle))
     return rc, lam, V
 
 
