@@ -68,7 +68,11 @@ typedef struct {
   int r_pre;          /* nodes of the preconditioner exp-sum (default 24)             */
   int rank_cap;       /* maximal Tucker rank per mode inside the solver (default and
                          maximum 64)                                                  */
-  int precision;      /* 0 = FP64 (only value implemented)                            */
+  int precision;      /* full-grid mode products: 0 = FP64 FMA (default); 1 = tensor
+                         cores, BF16 digit split (4 x 7-bit digits, shared row/column
+                         exponents, 10 products, FP32 accumulate; ~1e-7 relative per
+                         product; needs n % 128 == 0, n <= 1024). The rank-structured
+                         solver always runs in FP64.                                   */
   int basis;          /* 1 = PCG vectors kept in eigenbasis coordinates (default);
                          0 = paper form, mode products with V_l in every apply         */
   int expsum_src;     /* 0 = sinc quadrature (only value implemented)                 */
@@ -129,7 +133,9 @@ int tctl_pcg_solve(tctl_ctx *ctx, const tctl_cp *b, tctl_cp *x, tctl_stats *st);
 /* Exact full-grid solve u = (xV)[((xV^T) y) ./ F2(lambda_i+lambda_j+lambda_k)]
  * (Sections 3.3-3.4, "DiagFGen2D"), six dense mode products and the
  * pointwise spectral divide. y, u: DEVICE n^3 arrays (x1 fastest), must not
- * alias. Uses 2 n^3 doubles of context workspace (allocated on first use). */
+ * alias. opts.precision selects FP64 FMA GEMMs (one n^3 double temporary) or
+ * the tensor-core digit-split GEMMs (two n^3 float temporaries, digit planes
+ * of the six eigenvector matrices); workspace is allocated on first use. */
 int tctl_fullgrid_solve(tctl_ctx *ctx, const double *y, double *u);
 
 /* State equation ("State"): y = A^-alpha u on the full grid (DEVICE n^3). */

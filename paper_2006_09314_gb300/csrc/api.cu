@@ -178,7 +178,10 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
     if (!c) fail(TCTL_E_NOMEM, "host allocation failed");
     tctl_default_opts(&c->o);
     if (opts) c->o = *opts;
-    if (c->o.precision != 0) fail(TCTL_E_ARG, "only precision 0 (FP64) is implemented");
+    if (c->o.precision != 0 && c->o.precision != 1)
+      fail(TCTL_E_ARG, "precision must be 0 (FP64) or 1 (tensor-core digit split)");
+    if (c->o.precision == 1 && !tc_fullgrid_supported(n))
+      fail(TCTL_E_ARG, "precision 1 needs n a multiple of 128 and n <= 1024");
     if (c->o.expsum_src != 0) fail(TCTL_E_ARG, "only expsum_src 0 (sinc) is implemented");
     if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
     if (!(c->o.op_tol > 0 && c->o.op_tol < 1e-2)) fail(TCTL_E_ARG, "op_tol must be in (0, 1e-2)");
@@ -282,7 +285,8 @@ int tctl_fullgrid_solve(tctl_ctx *ctx, const double *y, double *u) {
   if (!c) return TCTL_E_ARG;
   try {
     if (!y || !u || y == u) fail(TCTL_E_ARG, "y and u must be distinct device arrays");
-    fullgrid_apply(*c, y, u, 0);
+    if (c->o.precision == 1) fullgrid_apply_tc(*c, y, u, 0);
+    else fullgrid_apply(*c, y, u, 0);
     return TCTL_OK;
   } catch (const Error &e) {
     return handle(c, e);
@@ -294,7 +298,8 @@ int tctl_fullgrid_state(tctl_ctx *ctx, const double *u, double *y) {
   if (!c) return TCTL_E_ARG;
   try {
     if (!y || !u || y == u) fail(TCTL_E_ARG, "u and y must be distinct device arrays");
-    fullgrid_apply(*c, u, y, 1);
+    if (c->o.precision == 1) fullgrid_apply_tc(*c, u, y, 1);
+    else fullgrid_apply(*c, u, y, 1);
     return TCTL_OK;
   } catch (const Error &e) {
     return handle(c, e);

@@ -1,6 +1,7 @@
 // Internal declarations of the tensorctl library (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -80,7 +81,14 @@ struct Ctx {
   Sep op, pre;
   double op_rel_err = 0;
   Arena ws;
-  double *full_tmp = nullptr;        // 2 n^3 for the full-grid solve
+  double *full_tmp = nullptr;        // n^3 temporary of the FP64 full-grid solve
+  // tensor-core full grid: digit planes of V_l^T / V_l, row exponents, two FP32
+  // n^3 buffers, column exponents, error flag (allocated on first use)
+  __nv_bfloat16 *tc_w[6] = {};
+  int *tc_e[6] = {};
+  float *tc_x[2] = {};
+  int *tc_f = nullptr;
+  int *tc_err = nullptr;
   tctl_stats stats{};
   std::string err;
   long long launches = 0;
@@ -157,6 +165,10 @@ void setup_eigs(Ctx &c);
 // ------------------------------------------------------------ spectral.cu
 void setup_spectral(Ctx &c);
 void fullgrid_apply(Ctx &c, const double *y, double *u, int which);
+
+// ------------------------------------------------------------ tc_modeprod.cu
+bool tc_fullgrid_supported(int n);
+void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which);
 
 // ------------------------------------------------------------ tucker.cu
 struct TuckerOps;

@@ -264,3 +264,30 @@ def test_minimum_size_n2():
     with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6) as ctx:
         x, st, code = ctx.pcg_solve(T.CP.from_numpy(pr.yw, pr.yU))
     assert np.linalg.norm(_full_from_gpu(x) - ustar) <= 1e-5 * np.linalg.norm(ustar)
+
+
+# ------------------------------------------------------------------ tensor-core full grid
+@pytest.mark.parametrize("n,alpha,beta", [(128, 0.5, 1e-2), (256, 0.25, 1e-4), (256, 0.75, 1.0)])
+def test_fullgrid_tensor_core_digit_split(n, alpha, beta):
+    """Mode products on tcgen05 with the BF16 digit split: within 1e-6 of the exact solve."""
+    pr = make_problem(n, alpha, beta, 5, 900 + n)
+    lams, Vs = _oracle_eigs(pr)
+    Y = F.cp_full(pr.yw, pr.yU)
+    ustar = fg.solve_exact(Y, lams, Vs, alpha, beta)
+    o = T.tctl_default_opts(precision=1)
+    with T.Context(pr.coeffs, n, alpha, beta, 1e-6, opts=o) as ctx:
+        yd = torch.from_numpy(np.asfortranarray(Y).reshape(-1, order="F")).cuda()
+        u = ctx.fullgrid_solve(yd).cpu().numpy().reshape((n, n, n), order="F")
+        err = np.linalg.norm(u - ustar) / np.linalg.norm(ustar)
+        assert err <= 1e-6, err
+        st = ctx.fullgrid_state(torch.from_numpy(np.asfortranarray(ustar).reshape(-1, order="F")).cuda())
+        st = st.cpu().numpy().reshape((n, n, n), order="F")
+        ref = fg.state_exact(ustar, lams, Vs, alpha)
+        assert np.linalg.norm(st - ref) / np.linalg.norm(ref) <= 1e-6
+
+
+def test_tensor_core_precision_rejects_unsupported_n():
+    pr = make_problem(100, 0.5, 1e-2, 1, 3)
+    with pytest.raises(T.TctlError) as ei:
+        T.tctl_setup(pr.coeffs, 100, 0.5, 1e-2, 1e-6, opts=T.tctl_default_opts(precision=1))
+    assert ei.value.code == -1
