@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=9, help="concurrent solves per step (<= 9)")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--fullgrid-n", type=int, default=512,
+                    help="grid of the full-grid mode-product measurement (0: skip)")
+    ap.add_argument("--fullgrid-only", action="store_true",
+                    help="run only the full-grid mode-product measurement")
     return ap.parse_args()
 
 
@@ -323,6 +327,7 @@ def ours_arm(args, rank, world):
 
     if rank != 0:
         return
+    fgsec = fullgrid_section(args, check=not args.no_check) if args.fullgrid_n > 0 else None
     errs = []
     if not args.no_check:
         for p, x in zip(probs, sols):
@@ -378,6 +383,7 @@ def ours_arm(args, rank, world):
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "note": f"tctl_solve_host x{B} concurrently: setup + H2D (pinned) + PCG + D2H"},
+        "mode_products": fgsec,
         "gpu_launches": launches,
         "clocks": clk,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
@@ -386,6 +392,82 @@ def ours_arm(args, rank, world):
     print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
+
+
+def fullgrid_section(args, check=True):
+    """Full-grid spectral solve (six mode products + divide) on the tensor cores.
+
+    The n^3 design function (expanded from the canonical y_Omega of the
+    precision configuration: n = 512, alpha = 0.5, beta = 1e-2) is solved with
+    the BF16 digit-split tcgen05 GEMMs (precision 1) and, once, with the FP64
+    FMA GEMMs (precision 0); the tensor-core result is compared with the
+    oracle's exact full-grid solve.
+    """
+    import torch
+    from oracle import fullgrid as fg
+    from oracle import operator as op
+    from paper_2006_09314_gb300 import tensorctl as T
+    from paper_2006_09314_gb300.inputs import make_problem, problem_seed
+
+    n = args.fullgrid_n
+    pr = make_problem(n, 0.5, 1e-2, RANK, problem_seed(2, 0))
+    Y = np.einsum("j,ij,kj,lj->ikl", pr.yw, pr.yU[0], pr.yU[1], pr.yU[2], optimize=True)
+    yd = torch.from_numpy(np.asfortranarray(Y).reshape(-1, order="F")).cuda()
+    out = {"workload": (f"full-grid spectral solve n={n} (6 mode products n x n by n x n^2 and the "
+                        "spectral divide), alpha=0.5, beta=1e-2, design rank 5")}
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, EPS, opts=T.tctl_default_opts(precision=1)) as ctx:
+        for _ in range(max(2, args.warmup)):
+            u = ctx.fullgrid_solve(yd)
+        times = []
+        for _ in range(max(3, args.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            u = ctx.fullgrid_solve(yd)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ctx.profile(True)
+        ctx.fullgrid_solve(yd)
+        prof = ctx.profile_report()
+        ctx.profile(False)
+    tc = prof.get("tc_modeprod_kernel", {"ms": float("nan"), "launches": 0})
+    ms = statistics.median(times)
+    bf16_flops = 15 * 2.0 * n ** 4 * 6  # 15 digit products per mode product, 6 products
+    out.update({"precision": "BF16 digit split (5 x 7-bit digits, 15 products, exact low levels) "
+                             "on tcgen05, FP32 storage",
+                "ms_per_solve": ms, "solves_per_s": 1000.0 / ms,
+                "mode_product_ms": tc["ms"] / max(tc["launches"], 1),
+                "bf16_tflops_effective": bf16_flops / (tc["ms"] / 1000.0) / 1e12,
+                "bf16_peak_tflops": _peak("bf16_tflops", 1957.2),
+                "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
+                            for k, v in prof.items()}})
+    out["frac_of_bf16_peak"] = out["bf16_tflops_effective"] / out["bf16_peak_tflops"]
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, EPS, opts=T.tctl_default_opts(precision=0)) as ctx:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.fullgrid_solve(yd)
+        e0.record()
+        ctx.fullgrid_solve(yd)
+        e1.record()
+        torch.cuda.synchronize()
+        out["fp64_ms_per_solve"] = e0.elapsed_time(e1)
+    if check:
+        lams, Vs = [], []
+        for l in range(3):
+            lam, V = op.eig(*op.assemble(pr.coeffs[l]))
+            lams.append(lam)
+            Vs.append(V)
+        ustar = fg.solve_exact(Y, lams, Vs, 0.5, 1e-2)
+        ug = u.cpu().numpy().reshape((n, n, n), order="F")
+        out["rel_err_vs_oracle"] = float(np.linalg.norm(ug - ustar) / np.linalg.norm(ustar))
+    return out
+
+
+def _peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except Exception:
+        return fallback
 
 
 def main():
@@ -401,6 +483,13 @@ def main():
         else:
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
             dist.init_process_group("nccl")
+    if args.fullgrid_only:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        if rank == 0:
+            print(json.dumps({"mode_products": fullgrid_section(args, check=not args.no_check)}),
+                  flush=True)
+        return
     if args.impl == "reference":
         reference_arm(args, rank)
     else:

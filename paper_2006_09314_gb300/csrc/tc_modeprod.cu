@@ -48,13 +48,12 @@ namespace {
 constexpr int TM = 128, TN = 128, BK = 32, NSTAGE = 2;
 constexpr int NPLANE = 5;                                    // digits of W
 constexpr int XPLANE = 5;                                    // digits of X
-constexpr int NTHREADS = 256;
+constexpr int NTHREADS = 256;  // 8 warps: producer, MMA issuer, all in the epilogue
 constexpr int PLANE_ELEMS = TM * BK;                         // 4096 bf16 = 8 KB
 constexpr int W_BYTES = NPLANE * PLANE_ELEMS * 2;            // 40 KB per stage
 constexpr int X_BYTES = XPLANE * PLANE_ELEMS * 2;            // 40 KB per stage
 constexpr int STAGE_BYTES = W_BYTES + X_BYTES;               // 80 KB
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 2048;      // + barriers, alignment
-constexpr int XPT = BK * TN / NTHREADS;                      // X elements per thread per stage
 constexpr uint32_t LBO = 128, SBO = (BK / 8) * 128;          // bytes
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -186,7 +185,7 @@ struct TcArgs {
   int n;
   const __nv_bfloat16 *wplanes;
   const int *e_row;
-  const float *X;
+  const __nv_bfloat16 *xplanes;  // X digit blocks (x_digits_kernel)
   long long sk, sj0, sj1;  // input strides
   long long sm;            // output stride of m (j strides as the input)
   const int *f_col;
@@ -199,25 +198,81 @@ struct TcArgs {
   int *err;
 };
 
-__device__ __forceinline__ void x_coords(int e, long long sk, int &k, int &jl) {
-  // thread-to-element map of the X stage tile (k < BK, jl < TN): coalesced along
-  // the contiguous index (k for the mode-1 product, j0 otherwise)
-  if (sk == 1) { k = e % BK; jl = e / BK; } else { jl = e % TN; k = e / TN; }
+// ---------------------------------------------------------------- X digits
+// Cuts the five digit planes of X once per mode product, in the tile layout
+// of the GEMM: block (jt, ks) holds, for the 128 columns j of tile jt and the
+// 32 contracted indices of slice ks, five 128 x 32 BF16 planes in the K-major
+// core-matrix layout (40 KB, contiguous). One CTA per (jt, ks) block; the
+// column exponents f_j come from col_exp_kernel. Each thread owns one column j
+// and 8 consecutive k (one 16-byte core-matrix row per plane), so the shared
+// staging stores are 16-byte and conflict-free; the block is then copied out
+// with coalesced 16-byte stores.
+__global__ void __launch_bounds__(512) x_digits_kernel(int n, const float *__restrict__ X,
+                                                       long long sk, long long sj0, long long sj1,
+                                                       const int *__restrict__ f_col,
+                                                       __nv_bfloat16 *__restrict__ planes) {
+  __shared__ __align__(16) uint8_t st[XPLANE * PLANE_ELEMS * 2];
+  const int ks = blockIdx.x, jt = blockIdx.y;
+  const long long jbase = (long long)jt * TN;
+  const int j1 = (int)(jbase / n), j0s = (int)(jbase % n);
+  // work item: (jl, kg) with kg the group of 8 consecutive k; 128 x 4 items
+  const int t = threadIdx.x;
+  int jl, kg;
+  if (sk == 1) { kg = t & 3; jl = t >> 2; } else { jl = t & 127; kg = t >> 7; }
+  const int f = f_col[jbase + jl];
+  uint32_t w[XPLANE][4];
+#pragma unroll
+  for (int q = 0; q < XPLANE; ++q)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) w[q][h] = 0;
+  const long long base = (long long)(j0s + jl) * sj0 + (long long)j1 * sj1;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int k = ks * BK + kg * 8 + e;
+    const float x = X[base + (long long)k * sk];
+    int d[XPLANE];
+    float sg;
+    digits_f32(__float_as_uint(x), f, d, sg);
+#pragma unroll
+    for (int q = 0; q < XPLANE; ++q) {
+      const __nv_bfloat16 b = __float2bfloat16_rn(sg * (float)d[q] * pow2i(-7 * q));
+      const uint32_t bits = (uint32_t)__bfloat16_as_ushort(b);
+      w[q][e >> 1] |= bits << (16 * (e & 1));
+    }
+  }
+  const uint32_t off = core_off(jl, kg * 8);
+#pragma unroll
+  for (int q = 0; q < XPLANE; ++q)
+    *reinterpret_cast<uint4 *>(st + q * PLANE_ELEMS * 2 + off) =
+        make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  __syncthreads();
+  const int nks = n / BK;
+  uint4 *dst = reinterpret_cast<uint4 *>(planes + ((long long)jt * nks + ks) * XPLANE * PLANE_ELEMS);
+  const uint4 *src = reinterpret_cast<const uint4 *>(st);
+  for (int e = threadIdx.x; e < XPLANE * PLANE_ELEMS * 2 / 16; e += blockDim.x) dst[e] = src[e];
 }
 
+// ---------------------------------------------------------------- the GEMM
+// Pure tensor-core stage loop: every stage's W and X digit blocks (40 KB each,
+// contiguous in global memory) are brought into shared memory by the
+// bulk-copy engine (thread 0 of warp 0, completion counted on full[b]); one
+// thread of warp 1 waits for them, issues the 30 tcgen05.mma of the stage and
+// commits them to empty[b], which gates the next copy into the buffer.
 __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
-  uint64_t *mma_done = reinterpret_cast<uint64_t *>(smem + NSTAGE * STAGE_BYTES);
-  uint64_t *w_full = mma_done + NSTAGE;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(w_full + NSTAGE);
+  uint64_t *empty = reinterpret_cast<uint64_t *>(smem + NSTAGE * STAGE_BYTES);
+  uint64_t *full = empty + NSTAGE;
+  uint64_t *done_bar = full + NSTAGE;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done_bar + 1);
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = a.n;
   const int mt = blockIdx.x;
-  const long long jbase = (long long)blockIdx.y * TN;
-  const int j1 = (int)(jbase / n), j0s = (int)(jbase % n);
+  const int jt = blockIdx.y;
+  const long long jbase = (long long)jt * TN;
+  const int j1 = (int)(jbase / n);
   const int nks = n / BK;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -227,9 +282,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
   }
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mma_done[s])), "r"(1));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&w_full[s])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(1));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done_bar)), "r"(1));
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -237,120 +293,80 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                         ((uint32_t)(TM >> 4) << 24);
-  const __nv_bfloat16 *wsrc = a.wplanes + (long long)mt * nks * NPLANE * PLANE_ELEMS;
-  // W digits of stage s -> buffer s % NSTAGE by the bulk-copy engine (thread 0)
-  auto issue_w = [&](int s) {
-    const uint32_t bar = smem_u32(&w_full[s % NSTAGE]);
-    const uint32_t dst = smem_u32(smem + (s % NSTAGE) * STAGE_BYTES);
-    const __nv_bfloat16 *src = wsrc + (long long)s * NPLANE * PLANE_ELEMS;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"(W_BYTES));
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(dst),
-        "l"(src), "r"(W_BYTES), "r"(bar)
-        : "memory");
-  };
-  float xr[XPT], xn[XPT];
-  auto load_x = [&](int s, float *dst) {
-#pragma unroll
-    for (int i = 0; i < XPT; ++i) {
-      int k, jl;
-      x_coords(tid + i * NTHREADS, a.sk, k, jl);
-      dst[i] = __ldg(&a.X[(long long)(s * BK + k) * a.sk + (long long)(j0s + jl) * a.sj0 +
-                         (long long)j1 * a.sj1]);
+  if (warp == 0 && lane == 0) {
+    // producer: bulk copies of the W and X digit blocks of each stage
+    const __nv_bfloat16 *wsrc = a.wplanes + (long long)mt * nks * NPLANE * PLANE_ELEMS;
+    const __nv_bfloat16 *xsrc = a.xplanes + (long long)jt * nks * XPLANE * PLANE_ELEMS;
+    for (int s = 0; s < nks; ++s) {
+      const int b = s % NSTAGE;
+      if (s >= NSTAGE) {
+        const int t = s - NSTAGE;
+        if (!mbar_wait(smem_u32(&empty[b]), (uint32_t)((t / NSTAGE) & 1))) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+      }
+      const uint32_t bar = smem_u32(&full[b]);
+      const uint32_t dst = smem_u32(smem + b * STAGE_BYTES);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                   "r"(STAGE_BYTES));
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+              "r"(dst),
+          "l"(wsrc + (long long)s * NPLANE * PLANE_ELEMS), "r"(W_BYTES), "r"(bar)
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+              "r"(dst + W_BYTES),
+          "l"(xsrc + (long long)s * XPLANE * PLANE_ELEMS), "r"(X_BYTES), "r"(bar)
+          : "memory");
     }
-  };
-  if (tid == 0) issue_w(0);
-  load_x(0, xr);
-  int issued = 0;
-  bool ok = true;
-  for (int s = 0; s < nks; ++s) {
-    const int b = s % NSTAGE;
-    // 1. X values of the next stage: registers, no buffer needed
-    if (s + 1 < nks) load_x(s + 1, xn);
-    // 2. X digits of stage s into buffer b (its previous MMAs, stage s - NSTAGE, were
-    //    waited for at the end of iteration s - 1)
-    uint8_t *sX = smem + b * STAGE_BYTES + W_BYTES;
-#pragma unroll
-    for (int i = 0; i < XPT; ++i) {
-      int k, jl;
-      x_coords(tid + i * NTHREADS, a.sk, k, jl);
-      const int f = a.f_col[jbase + jl];
-      int d[XPLANE];
-      float sg;
-      digits_f32(__float_as_uint(xr[i]), f, d, sg);
-      const uint32_t off = core_off(jl, k);
-#pragma unroll
-      for (int q = 0; q < XPLANE; ++q)
-        *reinterpret_cast<__nv_bfloat16 *>(sX + q * PLANE_ELEMS * 2 + off) =
-            __float2bfloat16_rn(sg * (float)d[q] * pow2i(-7 * q));
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // 3. one thread issues the MMAs of stage s (asynchronous)
-    if (tid == 0) {
-      const bool w = mbar_wait(smem_u32(&w_full[b]), (uint32_t)((s / NSTAGE) & 1));
-      if (!w) {
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+    int s = 0;
+    for (; s < nks; ++s) {
+      const int b = s % NSTAGE;
+      if (!mbar_wait(smem_u32(&full[b]), (uint32_t)((s / NSTAGE) & 1))) {
         atomicExch(abort_flag, 1);
-      } else {
-        const uint32_t wb = smem_u32(smem + b * STAGE_BYTES), xb = smem_u32(sX);
-        for (int t = 0; t < BK / 16; ++t) {
-          for (int p = 0; p < NPLANE; ++p) {
-            for (int q = 0; q < XPLANE; ++q) {
-              if (p + q > 4) continue;  // digit pairs with p + q <= 4 (0-based): 15 products
-              const uint64_t ad = smem_desc(wb + p * PLANE_ELEMS * 2 + t * 2 * LBO);
-              const uint64_t bd = smem_desc(xb + q * PLANE_ELEMS * 2 + t * 2 * LBO);
-              // accumulator by digit level: 0 (exact integers), 1 (exact multiples of
-              // 2^-7 below 2^17), >= 2 (FP32 rounding 2^-14 below the result)
-              const int lvl = p + q < 2 ? p + q : 2;
-              const uint32_t dst = tmem + 128u * (uint32_t)lvl;
-              // the first product into each accumulator overwrites it
-              const bool first = (s == 0 && t == 0) &&
-                                 ((p == 0 && q == 0) || (p == 0 && q == 1) || (p == 0 && q == 2));
-              const uint32_t acc = first ? 0u : 1u;
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t wb = smem_u32(smem + b * STAGE_BYTES), xb = wb + W_BYTES;
+      for (int t = 0; t < BK / 16; ++t) {
+        for (int p = 0; p < NPLANE; ++p) {
+          for (int q = 0; q < XPLANE; ++q) {
+            if (p + q > 4) continue;  // digit pairs with p + q <= 4 (0-based): 15 products
+            const uint64_t ad = smem_desc(wb + p * PLANE_ELEMS * 2 + t * 2 * LBO);
+            const uint64_t bd = smem_desc(xb + q * PLANE_ELEMS * 2 + t * 2 * LBO);
+            // accumulator by digit level: 0 (exact integers), 1 (exact multiples of
+            // 2^-7 below 2^17), >= 2 (FP32 rounding 2^-14 below the result)
+            const int lvl = p + q < 2 ? p + q : 2;
+            const uint32_t dst = tmem + 128u * (uint32_t)lvl;
+            // the first product into each accumulator overwrites it
+            const bool first = (s == 0 && t == 0) &&
+                               ((p == 0 && q == 0) || (p == 0 && q == 1) || (p == 0 && q == 2));
+            const uint32_t acc = first ? 0u : 1u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
           }
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mma_done[b])));
       }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&empty[b])));
     }
-    issued = s + 1;
-    // 4. buffer of stage s + 1 is free once the MMAs of stage s + 1 - NSTAGE are done;
-    //    then its W digits are requested (they arrive while stage s + 1 is split)
-    if (s + 1 < nks) {
-      if (s + 1 >= NSTAGE) {
-        const int t = s + 1 - NSTAGE;
-        const bool w = mbar_wait(smem_u32(&mma_done[t % NSTAGE]), (uint32_t)((t / NSTAGE) & 1));
-        if (!w) atomicExch(abort_flag, 1);
-      }
-      __syncthreads();
-      if (*abort_flag) { ok = false; break; }
-      if (tid == 0) issue_w(s + 1);
-    }
-#pragma unroll
-    for (int i = 0; i < XPT; ++i) xr[i] = xn[i];
+    // completion of every MMA issued above (also after an abort, so that TMEM can be freed)
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(done_bar)));
   }
-  // wait for the last committed stage (covers all earlier MMAs); after an abort this
-  // bounded wait lets MMAs in flight finish before TMEM is freed
-  __syncthreads();
-  ok = ok && (*abort_flag == 0) && issued == nks;
-  {
-    const int t = issued - 1;
-    bool fin = true;
-    if (t >= 0) fin = mbar_wait(smem_u32(&mma_done[t % NSTAGE]), (uint32_t)((t / NSTAGE) & 1));
-    ok = (__syncthreads_and(fin ? 1 : 0) != 0) && ok;
-  }
+  // everyone waits for the final commit (bounded)
+  const bool fin = mbar_wait(smem_u32(done_bar), 0u);
+  const bool ok = (__syncthreads_and(fin ? 1 : 0) != 0) && (*abort_flag == 0);
   if (!ok && tid == 0) atomicExch(a.err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
@@ -436,6 +452,7 @@ void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
     c.tc_x[0] = reinterpret_cast<float *>(c.dmalloc((size_t)(n3 + 1) / 2));
     c.tc_x[1] = reinterpret_cast<float *>(c.dmalloc((size_t)(n3 + 1) / 2));
     c.tc_f = reinterpret_cast<int *>(c.dmalloc((size_t)(n2 + 1) / 2));
+    c.tc_xd = reinterpret_cast<__nv_bfloat16 *>(c.dmalloc((size_t)(n3 * XPLANE + 3) / 4));
     c.tc_err = reinterpret_cast<int *>(c.dmalloc(1));
     TCTL_CUDA(cudaFuncSetAttribute(tc_modeprod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    SMEM_BYTES));
@@ -455,11 +472,15 @@ void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
     const int cblocks = (sk[l] == 1) ? (int)std::min<long long>(n2 * 32 / 256, 152 * 64)
                                      : (int)std::min<long long>((n2 + 255) / 256, 152 * 64);
     LAUNCH(c, col_exp_kernel, cblocks, 256, 0, n, X, sk[l], sj0[l], sj1[l], c.tc_f);
+    {
+      dim3 g(n / BK, (unsigned)(n2 / TN));
+      LAUNCH(c, x_digits_kernel, g, 512, 0, n, X, sk[l], sj0[l], sj1[l], c.tc_f, c.tc_xd);
+    }
     TcArgs ar;
     ar.n = n;
     ar.wplanes = c.tc_w[idx];
     ar.e_row = c.tc_e[idx];
-    ar.X = X;
+    ar.xplanes = c.tc_xd;
     ar.sk = sk[l];
     ar.sj0 = sj0[l];
     ar.sj1 = sj1[l];

@@ -88,6 +88,7 @@ struct Ctx {
   int *tc_e[6] = {};
   float *tc_x[2] = {};
   int *tc_f = nullptr;
+  __nv_bfloat16 *tc_xd = nullptr;    // X digit blocks of one mode product
   int *tc_err = nullptr;
   tctl_stats stats{};
   std::string err;

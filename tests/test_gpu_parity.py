@@ -291,3 +291,16 @@ def test_tensor_core_precision_rejects_unsupported_n():
     with pytest.raises(T.TctlError) as ei:
         T.tctl_setup(pr.coeffs, 100, 0.5, 1e-2, 1e-6, opts=T.tctl_default_opts(precision=1))
     assert ei.value.code == -1
+
+
+def test_fullgrid_tensor_core_full_size_n512():
+    """The precision configuration's full grid (n = 512, 1.3e8 points), as bench.py runs it."""
+    n, alpha, beta = 512, 0.5, 1e-2
+    pr = make_problem(n, alpha, beta, 5, 2000)
+    lams, Vs = _oracle_eigs(pr)
+    Y = np.einsum("j,ij,kj,lj->ikl", pr.yw, pr.yU[0], pr.yU[1], pr.yU[2], optimize=True)
+    ustar = fg.solve_exact(Y, lams, Vs, alpha, beta)
+    with T.Context(pr.coeffs, n, alpha, beta, 1e-6, opts=T.tctl_default_opts(precision=1)) as ctx:
+        u = ctx.fullgrid_solve(torch.from_numpy(np.asfortranarray(Y).reshape(-1, order="F")).cuda())
+    u = u.cpu().numpy().reshape((n, n, n), order="F")
+    assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) <= 1e-6
