@@ -45,15 +45,18 @@ namespace tctl {
 
 namespace {
 
-constexpr int TM = 128, TN = 128, BK = 32, NSTAGE = 2;
+constexpr int TM = 128, TN = 64, BK = 16, NSTAGE = 3;
 constexpr int NPLANE = 5;                                    // digits of W
 constexpr int XPLANE = 5;                                    // digits of X
 constexpr int NTHREADS = 256;  // 8 warps: producer, MMA issuer, all in the epilogue
-constexpr int PLANE_ELEMS = TM * BK;                         // 4096 bf16 = 8 KB
-constexpr int W_BYTES = NPLANE * PLANE_ELEMS * 2;            // 40 KB per stage
-constexpr int X_BYTES = XPLANE * PLANE_ELEMS * 2;            // 40 KB per stage
-constexpr int STAGE_BYTES = W_BYTES + X_BYTES;               // 80 KB
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 2048;      // + barriers, alignment
+constexpr int PLANE_ELEMS = TM * BK;                         // W plane: 2048 bf16 = 4 KB
+constexpr int XPLANE_ELEMS = TN * BK;                        // X plane: 1024 bf16 = 2 KB
+constexpr int W_BYTES = NPLANE * PLANE_ELEMS * 2;            // 20 KB per stage
+constexpr int X_BYTES = XPLANE * XPLANE_ELEMS * 2;           // 10 KB per stage
+constexpr int STAGE_BYTES = W_BYTES + X_BYTES;               // 30 KB
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 2048;      // 92 KB: two CTAs per SM
+constexpr int TMEM_COLS = 256;                               // 3 accumulators of TN columns
+constexpr int XD_KS = 4;                                     // K slices per x_digits block
 constexpr uint32_t LBO = 128, SBO = (BK / 8) * 128;          // bytes
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -200,25 +203,26 @@ struct TcArgs {
 
 // ---------------------------------------------------------------- X digits
 // Cuts the five digit planes of X once per mode product, in the tile layout
-// of the GEMM: block (jt, ks) holds, for the 128 columns j of tile jt and the
-// 32 contracted indices of slice ks, five 128 x 32 BF16 planes in the K-major
-// core-matrix layout (40 KB, contiguous). One CTA per (jt, ks) block; the
-// column exponents f_j come from col_exp_kernel. Each thread owns one column j
-// and 8 consecutive k (one 16-byte core-matrix row per plane), so the shared
-// staging stores are 16-byte and conflict-free; the block is then copied out
-// with coalesced 16-byte stores.
+// of the GEMM: block (jt, ks) holds, for the TN columns j of tile jt and the
+// BK contracted indices of slice ks, five TN x BK BF16 planes in the K-major
+// core-matrix layout (10 KB, contiguous). One CTA handles XD_KS consecutive
+// slices of one tile; the column exponents f_j come from col_exp_kernel. Each
+// thread owns one column j and 8 consecutive k (one 16-byte core-matrix row per
+// plane), so the shared staging stores are 16-byte and conflict-free; the
+// blocks are then copied out with coalesced 16-byte stores.
 __global__ void __launch_bounds__(512) x_digits_kernel(int n, const float *__restrict__ X,
                                                        long long sk, long long sj0, long long sj1,
                                                        const int *__restrict__ f_col,
                                                        __nv_bfloat16 *__restrict__ planes) {
-  __shared__ __align__(16) uint8_t st[XPLANE * PLANE_ELEMS * 2];
-  const int ks = blockIdx.x, jt = blockIdx.y;
+  __shared__ __align__(16) uint8_t st[XD_KS * X_BYTES];
+  const int ksg = blockIdx.x, jt = blockIdx.y;
   const long long jbase = (long long)jt * TN;
   const int j1 = (int)(jbase / n), j0s = (int)(jbase % n);
-  // work item: (jl, kg) with kg the group of 8 consecutive k; 128 x 4 items
+  // work item: (jl, kg) with kg the group of 8 consecutive k within XD_KS slices
+  constexpr int KG = XD_KS * BK / 8;  // 8
   const int t = threadIdx.x;
   int jl, kg;
-  if (sk == 1) { kg = t & 3; jl = t >> 2; } else { jl = t & 127; kg = t >> 7; }
+  if (sk == 1) { kg = t % KG; jl = t / KG; } else { jl = t % TN; kg = t / TN; }
   const int f = f_col[jbase + jl];
   uint32_t w[XPLANE][4];
 #pragma unroll
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(512) x_digits_kernel(int n, const float *__res
   const long long base = (long long)(j0s + jl) * sj0 + (long long)j1 * sj1;
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
-    const int k = ks * BK + kg * 8 + e;
+    const int k = ksg * XD_KS * BK + kg * 8 + e;
     const float x = X[base + (long long)k * sk];
     int d[XPLANE];
     float sg;
@@ -240,16 +244,18 @@ __global__ void __launch_bounds__(512) x_digits_kernel(int n, const float *__res
       w[q][e >> 1] |= bits << (16 * (e & 1));
     }
   }
-  const uint32_t off = core_off(jl, kg * 8);
+  const int ksl = kg / (BK / 8), kin = (kg % (BK / 8)) * 8;
+  const uint32_t off = core_off(jl, kin);
 #pragma unroll
   for (int q = 0; q < XPLANE; ++q)
-    *reinterpret_cast<uint4 *>(st + q * PLANE_ELEMS * 2 + off) =
+    *reinterpret_cast<uint4 *>(st + ksl * X_BYTES + q * XPLANE_ELEMS * 2 + off) =
         make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
   __syncthreads();
   const int nks = n / BK;
-  uint4 *dst = reinterpret_cast<uint4 *>(planes + ((long long)jt * nks + ks) * XPLANE * PLANE_ELEMS);
+  uint4 *dst = reinterpret_cast<uint4 *>(
+      planes + ((long long)jt * nks + (long long)ksg * XD_KS) * XPLANE * XPLANE_ELEMS);
   const uint4 *src = reinterpret_cast<const uint4 *>(st);
-  for (int e = threadIdx.x; e < XPLANE * PLANE_ELEMS * 2 / 16; e += blockDim.x) dst[e] = src[e];
+  for (int e = threadIdx.x; e < XD_KS * X_BYTES / 16; e += blockDim.x) dst[e] = src[e];
 }
 
 // ---------------------------------------------------------------- the GEMM
@@ -258,7 +264,7 @@ __global__ void __launch_bounds__(512) x_digits_kernel(int n, const float *__res
 // bulk-copy engine (thread 0 of warp 0, completion counted on full[b]); one
 // thread of warp 1 waits for them, issues the 30 tcgen05.mma of the stage and
 // commits them to empty[b], which gates the next copy into the buffer.
-__global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
+__global__ void __launch_bounds__(NTHREADS, 2) tc_modeprod_kernel(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
@@ -277,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(512));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
   if (warp == 0 && lane == 0) {
     // producer: bulk copies of the W and X digit blocks of each stage
     const __nv_bfloat16 *wsrc = a.wplanes + (long long)mt * nks * NPLANE * PLANE_ELEMS;
-    const __nv_bfloat16 *xsrc = a.xplanes + (long long)jt * nks * XPLANE * PLANE_ELEMS;
+    const __nv_bfloat16 *xsrc = a.xplanes + (long long)jt * nks * XPLANE * XPLANE_ELEMS;
     for (int s = 0; s < nks; ++s) {
       const int b = s % NSTAGE;
       if (s >= NSTAGE) {
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
       asm volatile(
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
               "r"(dst + W_BYTES),
-          "l"(xsrc + (long long)s * XPLANE * PLANE_ELEMS), "r"(X_BYTES), "r"(bar)
+          "l"(xsrc + (long long)s * XPLANE * XPLANE_ELEMS), "r"(X_BYTES), "r"(bar)
           : "memory");
     }
   } else if (warp == 1 && lane == 0) {
@@ -339,11 +345,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
           for (int q = 0; q < XPLANE; ++q) {
             if (p + q > 4) continue;  // digit pairs with p + q <= 4 (0-based): 15 products
             const uint64_t ad = smem_desc(wb + p * PLANE_ELEMS * 2 + t * 2 * LBO);
-            const uint64_t bd = smem_desc(xb + q * PLANE_ELEMS * 2 + t * 2 * LBO);
+            const uint64_t bd = smem_desc(xb + q * XPLANE_ELEMS * 2 + t * 2 * LBO);
             // accumulator by digit level: 0 (exact integers), 1 (exact multiples of
             // 2^-7 below 2^17), >= 2 (FP32 rounding 2^-14 below the result)
             const int lvl = p + q < 2 ? p + q : 2;
-            const uint32_t dst = tmem + 128u * (uint32_t)lvl;
+            const uint32_t dst = tmem + (uint32_t)(TN * lvl);
             // the first product into each accumulator overwrites it
             const bool first = (s == 0 && t == 0) &&
                                ((p == 0 && q == 0) || (p == 0 && q == 1) || (p == 0 && q == 2));
@@ -370,52 +376,60 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
   if (!ok && tid == 0) atomicExch(a.err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows m), columns 64 (w / 4) .. +63
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows m), columns 32 (w / 4) .. +31,
+    // 16 at a time
     const int row = (warp & 3) * 32 + lane;
     const int m = mt * TM + row;
     const int em = a.e_row[m];
-#pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
-      const int cb = (warp >> 2) * 64 + cc * 32;
-      uint32_t hi[32], l1[32], rs[32];
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      const int cb = (warp >> 2) * 32 + half * 16;
+      uint32_t hi[16], l1[16], rs[16];
       const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb;
-#define TCTL_LD32(dst, addr)                                                                     \
+#define TCTL_LD16(dst, addr)                                                                     \
   asm volatile(                                                                                  \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"   \
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"         \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"   \
+      "%14,%15}, [%16];"                                                                         \
       : "=r"(dst[0]), "=r"(dst[1]), "=r"(dst[2]), "=r"(dst[3]), "=r"(dst[4]), "=r"(dst[5]),      \
         "=r"(dst[6]), "=r"(dst[7]), "=r"(dst[8]), "=r"(dst[9]), "=r"(dst[10]), "=r"(dst[11]),    \
-        "=r"(dst[12]), "=r"(dst[13]), "=r"(dst[14]), "=r"(dst[15]), "=r"(dst[16]),               \
-        "=r"(dst[17]), "=r"(dst[18]), "=r"(dst[19]), "=r"(dst[20]), "=r"(dst[21]),               \
-        "=r"(dst[22]), "=r"(dst[23]), "=r"(dst[24]), "=r"(dst[25]), "=r"(dst[26]),               \
-        "=r"(dst[27]), "=r"(dst[28]), "=r"(dst[29]), "=r"(dst[30]), "=r"(dst[31])                \
+        "=r"(dst[12]), "=r"(dst[13]), "=r"(dst[14]), "=r"(dst[15])                              \
       : "r"(addr))
-      TCTL_LD32(hi, t0);
-      TCTL_LD32(l1, t0 + 128);
-      TCTL_LD32(rs, t0 + 256);
-#undef TCTL_LD32
+      TCTL_LD16(hi, t0);
+      TCTL_LD16(l1, t0 + TN);
+      TCTL_LD16(rs, t0 + 2 * TN);
+#undef TCTL_LD16
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       const long long jb = jbase + cb;
       const int jj0 = (int)(jb % n);
       float *out = a.C + (long long)m * a.sm + (long long)jj0 * a.sj0 + (long long)j1 * a.sj1;
       const double lmj = a.divide ? a.lm[m] + a.l1[j1] : 0.0;
+      float v[16];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
+      for (int i = 0; i < 16; ++i) {
         const int fj = a.f_col[jb + i];
-        float v = ((__uint_as_float(hi[i]) + __uint_as_float(l1[i])) + __uint_as_float(rs[i])) *
-                  pow2i(em + fj - 14);
+        v[i] = ((__uint_as_float(hi[i]) + __uint_as_float(l1[i])) + __uint_as_float(rs[i])) *
+               pow2i(em + fj - 14);
         if (a.divide) {
           const float pw = powf((float)(lmj + a.l0[jj0 + i]), a.alpha);
-          v = (a.divide == 1) ? v / (1.0f / pw + a.beta * pw) : v / pw;
+          v[i] = (a.divide == 1) ? v[i] / (1.0f / pw + a.beta * pw) : v[i] / pw;
         }
-        out[(long long)i * a.sj0] = v;
+      }
+      if (a.sj0 == 1) {
+        // 16 contiguous floats: 16-byte stores
+#pragma unroll
+        for (int i = 0; i < 16; i += 4)
+          *reinterpret_cast<float4 *>(out + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) out[(long long)i * a.sj0] = v[i];
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
 }
 
 __global__ void f64_to_f32_kernel(long long count, const double *__restrict__ x, float *__restrict__ y) {
@@ -432,7 +446,7 @@ __global__ void f32_to_f64_kernel(long long count, const float *__restrict__ x, 
 
 }  // namespace
 
-bool tc_fullgrid_supported(int n) { return n >= 128 && n <= 1024 && n % 128 == 0; }
+bool tc_fullgrid_supported(int n) { return n >= 128 && n <= 1024 && n % 128 == 0; }  // (BK * XD_KS) | n
 
 // u = (x V) [ ((x V^T) y) ./ F2(S) ] with all six mode products on the tensor cores.
 void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
@@ -453,6 +467,8 @@ void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
     c.tc_x[1] = reinterpret_cast<float *>(c.dmalloc((size_t)(n3 + 1) / 2));
     c.tc_f = reinterpret_cast<int *>(c.dmalloc((size_t)(n2 + 1) / 2));
     c.tc_xd = reinterpret_cast<__nv_bfloat16 *>(c.dmalloc((size_t)(n3 * XPLANE + 3) / 4));
+    static_assert(XD_KS * X_BYTES <= 48 * 1024, "x_digits staging exceeds static shared memory");
+    static_assert((TN * (XD_KS * BK / 8)) == 512, "x_digits work items must match its block");
     c.tc_err = reinterpret_cast<int *>(c.dmalloc(1));
     TCTL_CUDA(cudaFuncSetAttribute(tc_modeprod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    SMEM_BYTES));
@@ -473,7 +489,7 @@ void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
                                      : (int)std::min<long long>((n2 + 255) / 256, 152 * 64);
     LAUNCH(c, col_exp_kernel, cblocks, 256, 0, n, X, sk[l], sj0[l], sj1[l], c.tc_f);
     {
-      dim3 g(n / BK, (unsigned)(n2 / TN));
+      dim3 g(n / (BK * XD_KS), (unsigned)(n2 / TN));
       LAUNCH(c, x_digits_kernel, g, 512, 0, n, X, sk[l], sj0[l], sj1[l], c.tc_f, c.tc_xd);
     }
     TcArgs ar;
