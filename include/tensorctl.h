@@ -79,6 +79,10 @@ typedef struct {
   int paper_end_rows; /* 1 = the paper's printed end rows of A_(l) (default 0)        */
   double eps_final;   /* truncation of the returned solution; <= 0 means eps/10       */
   unsigned long long seed; /* seed of the sketching random numbers (default 1)       */
+  double range_tol;   /* range finder of the truncated Hadamard products F2 .* x and
+                         P .* x: a direction of the mode-l sketch is kept while its
+                         residual exceeds max(1e-8, range_tol * eps_trunc) of the
+                         largest sketch column (default 0.1)                           */
 } tctl_opts;
 
 typedef struct {
@@ -203,6 +207,8 @@ int tctl_eig1d_noalloc(const double *coeffs, int n, int paper_end_rows, double *
  * JSON object {kernel: {"launches", "ms", "flops"}} aggregated over the
  * launches since the last report (flops: algorithmic 2mnk for GEMMs, 0 for
  * other kernels); it synchronizes the stream and clears the records.
+ * on = 2 additionally prefixes every name with the algorithm phase
+ * ("apply_op/...", "truncate/...", ...).
  * Errors: TCTL_E_ARG (NULL, or buffer too small). */
 int tctl_profile_enable(tctl_ctx *ctx, int on);
 int tctl_profile_report(tctl_ctx *ctx, char *buf, int buflen);

@@ -2,6 +2,7 @@
 // Algorithm 1). Every entry point catches the library's internal errors and
 // returns a status code; nothing throws across the ABI.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -97,19 +98,31 @@ int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
     x->rank = 0;
   } else {
     tucker_copy(c, B, R);                       // R0 = B - fun(X0), X0 = 0
-    apply_sep(c, c.pre, R, Z, T1, eps);         // Z0 = trunc(precond(R0))
+    {
+      TCTL_OUTER(c, "precond");
+      apply_sep(c, c.pre, R, Z, T1, eps);       // Z0 = trunc(precond(R0))
+    }
     tucker_copy(c, Z, P);                       // P0 = Z0
     double rz = tucker_inner(c, R, Z);
     rel = 1.0;
     while (iters < c.o.max_iter) {
-      apply_sep(c, c.op, P, S, T1, eps);        // S = trunc(fun(P))
+      {
+        TCTL_OUTER(c, "fun");
+        apply_sep(c, c.op, P, S, T1, eps);      // S = trunc(fun(P))
+      }
       track(S);
       const double pS = tucker_inner(c, P, S);
       if (!(pS > 0.0) || !std::isfinite(pS)) fail(TCTL_E_NUMERIC, "PCG breakdown: <P, S> <= 0");
       const double a = rz / pS;
-      tucker_axpby_trunc(c, 1.0, X, a, P, T2, eps_x);   // X = trunc(X + a P)
+      {
+        TCTL_OUTER(c, "update_x");
+        tucker_axpby_trunc(c, 1.0, X, a, P, T2, eps_x);  // X = trunc(X + a P)
+      }
       std::swap(X, T2);
-      tucker_axpby_trunc(c, 1.0, R, -a, S, T2, eps);    // R = trunc(R - a S)
+      {
+        TCTL_OUTER(c, "update_r");
+        tucker_axpby_trunc(c, 1.0, R, -a, S, T2, eps);   // R = trunc(R - a S)
+      }
       std::swap(R, T2);
       track(X);
       track(R);
@@ -117,15 +130,22 @@ int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
       rel = std::sqrt(std::max(tucker_inner(c, R, R), 0.0)) / bnorm;
       if (!std::isfinite(rel)) fail(TCTL_E_NAN, "non-finite residual");
       if (rel <= c.o.pcg_rtol) break;
-      apply_sep(c, c.pre, R, Z, T1, eps);       // Z = trunc(precond(R))
+      {
+        TCTL_OUTER(c, "precond");
+        apply_sep(c, c.pre, R, Z, T1, eps);     // Z = trunc(precond(R))
+      }
       const double rz_new = tucker_inner(c, R, Z);
       const double beta = rz_new / rz;
       rz = rz_new;
-      tucker_axpby_trunc(c, 1.0, Z, beta, P, T2, eps);  // P = trunc(Z + beta P)
+      {
+        TCTL_OUTER(c, "update_p");
+        tucker_axpby_trunc(c, 1.0, Z, beta, P, T2, eps);  // P = trunc(Z + beta P)
+      }
       std::swap(P, T2);
       track(P);
     }
     if (rel > c.o.pcg_rtol) status = TCTL_E_NOT_CONVERGED;
+    TCTL_OUTER(c, "to_cp");
     const int s2 = tucker_to_cp(c, X, eig, eps_x, x);
     if (status == TCTL_OK) status = s2;
   }
@@ -157,6 +177,7 @@ int tctl_default_opts(tctl_opts *o) {
   o->paper_end_rows = 0;
   o->eps_final = 0.0;
   o->seed = 1;
+  o->range_tol = 0.1;
   return TCTL_OK;
 }
 
@@ -184,10 +205,16 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
       fail(TCTL_E_ARG, "precision 1 needs n a multiple of 128 and n <= 1024");
     if (c->o.expsum_src != 0) fail(TCTL_E_ARG, "only expsum_src 0 (sinc) is implemented");
     if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
+    if (!(c->o.range_tol >= 0.0 && c->o.range_tol <= 1.0))
+      fail(TCTL_E_ARG, "range_tol must lie in [0, 1]");
     if (!(c->o.op_tol > 0 && c->o.op_tol < 1e-2)) fail(TCTL_E_ARG, "op_tol must be in (0, 1e-2)");
     if (c->o.r_pre < 1 || c->o.r_pre > 200) fail(TCTL_E_ARG, "r_pre must be in [1, 200]");
     if (c->o.max_iter < 1) fail(TCTL_E_ARG, "max_iter must be >= 1");
     if (!(c->o.pcg_rtol > 0)) fail(TCTL_E_ARG, "pcg_rtol must be positive");
+    {
+      const char *tr = std::getenv("TCTL_TRACE");
+      c->trace = tr && tr[0] == '1';
+    }
     c->n = n;
     c->alpha = alpha;
     c->beta = beta;
@@ -390,6 +417,7 @@ int tctl_profile_enable(tctl_ctx *ctx, int on) {
   Ctx *c = reinterpret_cast<Ctx *>(ctx);
   if (!c) return TCTL_E_ARG;
   c->prof = (on != 0);
+  c->prof_phases = (on == 2);
   c->prof_recs.clear();
   c->prof_used = 0;
   return TCTL_OK;
@@ -411,6 +439,8 @@ int tctl_profile_report(tctl_ctx *ctx, char *buf, int buflen) {
       nm.erase(std::remove(nm.begin(), nm.end(), '('), nm.end());
       const size_t lt = nm.find('<');
       if (lt != std::string::npos) nm = nm.substr(0, lt);
+      if (c->prof_phases && r.phase) nm = std::string(r.phase) + "/" + nm;
+      if (c->prof_phases && r.outer) nm = std::string(r.outer) + "/" + nm;
       float ms = 0;
       TCTL_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
       auto it = std::find_if(agg.begin(), agg.end(), [&](const Agg &a) { return a.name == nm; });

@@ -362,6 +362,19 @@ void to_dev(Ctx &c, double *dst, const double *src, size_t count) {
 // One CTA per matrix; A and V in shared memory (padded to even size mp).
 // Matrix b of the launch has size ms[b] and lives at As[b] (ld ms[b]); its
 // eigenvalues (descending) go to lams[b], eigenvectors (columns) to Vs[b].
+//
+// A step rotates the mp/2 disjoint pairs (p, q) of the round-robin schedule at
+// once: A <- J^T A J, V <- V J, J the product of the plane rotations
+// [[c, s], [-s, c]] on (p, q). Since the pairs are disjoint, J^T A J splits into
+// 2 x 2 blocks (rows of pair a, columns of pair b) that transform
+// independently, B <- R_a^T B R_b; the upper-triangle blocks are computed once
+// and mirrored (A stays exactly symmetric), and the rotated diagonal blocks
+// are set to their exact values (a_pp - t a_pq, a_qq + t a_pq, 0) instead of
+// being recomputed from differences of large numbers, so that the off-diagonal
+// mass goes to zero rather than to the rounding level of the diagonal. A pair
+// is left unrotated when |a_pq| <= 1e-15 sqrt(a_pp a_qq) (the relative
+// accuracy threshold of one-sided and two-sided Jacobi, Demmel and Veselic)
+// or |a_pq| <= 1e-18 ||A||_F; the sweeps stop after a sweep without rotations.
 constexpr int JMAX = 64;
 
 struct EigDesc {
@@ -377,96 +390,103 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__
   const int m = dsc.m;
   const int mp = (m + 1) & ~1;
   const int ld = mp + 1;
+  const int half = mp / 2;
   double *A = sm;               // mp x ld
   double *V = A + mp * ld;      // mp x ld
-  double *cs = V + mp * ld;     // 2 * (mp/2)
-  int *pq = reinterpret_cast<int *>(cs + mp);  // 2 * (mp/2)
+  double *rc = V + mp * ld;     // half: c
+  double *rs = rc + half;       // half: s
+  double *rt = rs + half;       // half: t (0: no rotation)
+  int *rp = reinterpret_cast<int *>(rt + half);  // half: p
+  int *rq = rp + half;                           // half: q
   __shared__ double red[8];
-  __shared__ int done;
+  __shared__ int nrot;
   const double *Ab = dsc.A;
+  double ss = 0.0;
   for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
     const int i = t % mp, j = t / mp;
-    A[i + j * ld] = (i < m && j < m) ? Ab[i + j * m] : 0.0;
+    const double v = (i < m && j < m) ? Ab[i + j * m] : 0.0;
+    A[i + j * ld] = v;
     V[i + j * ld] = (i == j) ? 1.0 : 0.0;
+    ss = fma(v, v, ss);
   }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
   __syncthreads();
-  const int half = mp / 2;
+  double tot = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+  const double abs_floor = 1e-36 * tot;  // |a_pq|^2 below this: no rotation
   for (int sweep = 0; sweep < 40 && mp > 1; ++sweep) {
-    // convergence test: off-diagonal vs total Frobenius mass
-    double off = 0.0, tot = 0.0;
-    for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
-      const int i = t % mp, j = t / mp;
-      const double v = A[i + j * ld];
-      tot = fma(v, v, tot);
-      if (i != j) off = fma(v, v, off);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_down_sync(0xffffffffu, off, o);
-      tot += __shfl_down_sync(0xffffffffu, tot, o);
-    }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
+    if (threadIdx.x == 0) nrot = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-      red[0] = s;
-    }
-    __syncthreads();
-    off = red[0];
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-      done = (off <= 1e-32 * s) || (s == 0.0);
-    }
-    __syncthreads();
-    if (done) break;
     for (int step = 0; step < mp - 1; ++step) {
-      for (int t = threadIdx.x; t < half; t += blockDim.x) {
-        // round robin: position 0 fixed, others rotate
+      if (threadIdx.x < half) {
+        // round robin: position 0 fixed, the others rotate
+        const int t = threadIdx.x;
         auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (mp - 1); };
         int p = at(t), q = at(mp - 1 - t);
         if (p > q) { const int tmp = p; p = q; q = tmp; }
-        const double apq = A[p + q * ld];
-        double cc = 1.0, ss = 0.0;
-        if (fabs(apq) > 1e-300) {
-          const double tau = (A[q + q * ld] - A[p + p * ld]) / (2.0 * apq);
-          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double app = A[p + p * ld], aqq = A[q + q * ld], apq = A[p + q * ld];
+        double cc = 1.0, sn = 0.0, tt = 0.0;
+        if (apq * apq > abs_floor && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
           cc = 1.0 / sqrt(1.0 + tt * tt);
-          ss = tt * cc;
+          sn = tt * cc;
+          nrot = 1;
         }
-        cs[2 * t] = cc;
-        cs[2 * t + 1] = ss;
-        pq[2 * t] = p;
-        pq[2 * t + 1] = q;
+        rc[t] = cc;
+        rs[t] = sn;
+        rt[t] = tt;
+        rp[t] = p;
+        rq[t] = q;
       }
       __syncthreads();
-      // rows p, q of A
-      for (int t = threadIdx.x; t < half * mp; t += blockDim.x) {
-        const int pr = t % half, j = t / half;
-        const double cc = cs[2 * pr], ss = cs[2 * pr + 1];
-        const int p = pq[2 * pr], q = pq[2 * pr + 1];
-        const double ap = A[p + j * ld], aq = A[q + j * ld];
-        A[p + j * ld] = cc * ap - ss * aq;
-        A[q + j * ld] = ss * ap + cc * aq;
+      // 2 x 2 blocks (a, b), a <= b, of J^T A J
+      for (int u = threadIdx.x; u < half * half; u += blockDim.x) {
+        const int a = u % half, b = u / half;
+        if (a > b) continue;
+        const double ta = rt[a], tb = rt[b];
+        if (ta == 0.0 && tb == 0.0) continue;
+        const int pa = rp[a], qa = rq[a];
+        if (a == b) {
+          const double apq = A[pa + qa * ld];
+          A[pa + pa * ld] -= ta * apq;
+          A[qa + qa * ld] += ta * apq;
+          A[pa + qa * ld] = 0.0;
+          A[qa + pa * ld] = 0.0;
+          continue;
+        }
+        const int pb = rp[b], qb = rq[b];
+        const double ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
+        const double b00 = A[pa + pb * ld], b01 = A[pa + qb * ld];
+        const double b10 = A[qa + pb * ld], b11 = A[qa + qb * ld];
+        const double l00 = ca * b00 - sa * b10, l01 = ca * b01 - sa * b11;
+        const double l10 = sa * b00 + ca * b10, l11 = sa * b01 + ca * b11;
+        const double n00 = l00 * cb - l01 * sb, n01 = l00 * sb + l01 * cb;
+        const double n10 = l10 * cb - l11 * sb, n11 = l10 * sb + l11 * cb;
+        A[pa + pb * ld] = n00;
+        A[pa + qb * ld] = n01;
+        A[qa + pb * ld] = n10;
+        A[qa + qb * ld] = n11;
+        A[pb + pa * ld] = n00;
+        A[qb + pa * ld] = n01;
+        A[pb + qa * ld] = n10;
+        A[qb + qa * ld] = n11;
       }
-      __syncthreads();
-      // columns p, q of A and V
-      for (int t = threadIdx.x; t < half * mp; t += blockDim.x) {
-        const int pr = t % half, i = t / half;
-        const double cc = cs[2 * pr], ss = cs[2 * pr + 1];
-        const int p = pq[2 * pr], q = pq[2 * pr + 1];
-        const double ap = A[i + p * ld], aq = A[i + q * ld];
-        A[i + p * ld] = cc * ap - ss * aq;
-        A[i + q * ld] = ss * ap + cc * aq;
+      // columns p, q of V
+      for (int u = threadIdx.x; u < half * mp; u += blockDim.x) {
+        const int a = u % half, i = u / half;
+        if (rt[a] == 0.0) continue;
+        const double cc = rc[a], sn = rs[a];
+        const int p = rp[a], q = rq[a];
         const double vp = V[i + p * ld], vq = V[i + q * ld];
-        V[i + p * ld] = cc * vp - ss * vq;
-        V[i + q * ld] = ss * vp + cc * vq;
+        V[i + p * ld] = cc * vp - sn * vq;
+        V[i + q * ld] = sn * vp + cc * vq;
       }
       __syncthreads();
     }
+    if (nrot == 0) break;
+    __syncthreads();  // nrot is reset at the top of the next sweep
   }
   // sort eigenvalues descending (selection by rank, m <= 64)
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -490,7 +510,7 @@ static void jacobi_launch(Ctx &c, const std::vector<EigDesc> &d) {
   }
   if (mmax <= 0) return;
   const int mp = (mmax + 1) & ~1;
-  const size_t smem = sizeof(double) * (2 * mp * (mp + 1) + mp) + sizeof(int) * mp;
+  const size_t smem = sizeof(double) * (2 * mp * (mp + 1) + 3 * (mp / 2)) + sizeof(int) * mp;
   static bool attr = false;
   if (!attr) {
     TCTL_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -64,6 +64,8 @@ struct Tucker {
 // One profiled launch (opt-in: events around every kernel of the context).
 struct ProfRec {
   const char *name;
+  const char *outer;
+  const char *phase;
   cudaEvent_t a, b;
   double flops;
 };
@@ -96,10 +98,15 @@ struct Ctx {
   uint64_t rng_counter = 0;
   std::vector<void *> owned;         // device allocations freed at destroy
   bool prof = false;                 // record events around every launch
+  bool trace = false;                // TCTL_TRACE=1: per-step ranks on stderr
+  bool prof_phases = false;          // report "phase/kernel" names
   std::vector<ProfRec> prof_recs;
   std::vector<cudaEvent_t> prof_pool;
   size_t prof_used = 0;
   double next_flops = 0;             // algorithmic flops of the next launch (GEMMs)
+  const char *next_tag = nullptr;    // profile name of the next launch (GEMM call site)
+  const char *phase = nullptr;       // current algorithm phase (profile grouping)
+  const char *outer = nullptr;       // current PCG step (profile grouping)
   double *dmalloc(size_t count);
   cudaEvent_t prof_event();
 };
@@ -120,10 +127,27 @@ struct Ctx {
     (ctx).launches++;                                                             \
     if ((ctx).prof) {                                                             \
       ::tctl::check_cuda(cudaEventRecord(tctl_ev_b, (ctx).st), "cudaEventRecord"); \
-      (ctx).prof_recs.push_back({#kernel, tctl_ev_a, tctl_ev_b, (ctx).next_flops}); \
+      (ctx).prof_recs.push_back({(ctx).next_tag ? (ctx).next_tag : #kernel, (ctx).outer, (ctx).phase, \
+                                 tctl_ev_a, tctl_ev_b, (ctx).next_flops});        \
     }                                                                             \
     (ctx).next_flops = 0;                                                         \
+    (ctx).next_tag = nullptr;                                                     \
   } while (0)
+
+// Scoped algorithm phase for the per-kernel trace (names must be literals).
+struct PhaseScope {
+  Ctx &c;
+  const char *Ctx::*slot;
+  const char *prev;
+  PhaseScope(Ctx &cc, const char *Ctx::*s, const char *p) : c(cc), slot(s), prev(cc.*s) { c.*s = p; }
+  ~PhaseScope() { c.*slot = prev; }
+};
+#define TCTL_CAT2(a, b) a##b
+#define TCTL_CAT(a, b) TCTL_CAT2(a, b)
+#define TCTL_PHASE(ctx, name) \
+  ::tctl::PhaseScope TCTL_CAT(tctl_phase_scope_, __LINE__)(ctx, &::tctl::Ctx::phase, name)
+#define TCTL_OUTER(ctx, name) \
+  ::tctl::PhaseScope TCTL_CAT(tctl_outer_scope_, __LINE__)(ctx, &::tctl::Ctx::outer, name)
 
 // ------------------------------------------------------------ linalg.cu
 // C = alpha op(A) op(B) + beta C, column-major, batched with element strides;

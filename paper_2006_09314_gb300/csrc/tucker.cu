@@ -21,6 +21,7 @@
 // are orthonormal, so Frobenius norms of the core are norms of the tensor).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <numeric>
 
 #include "tctl_internal.cuh"
@@ -214,6 +215,7 @@ static bool tucker_empty(const Tucker &x) { return x.r[0] == 0 || x.r[1] == 0 ||
 
 void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
   if (tucker_empty(x)) return;
+  TCTL_PHASE(c, "hosvd");
   const int n = c.n;
   size_t mk = c.ws.mark();
   const int r[3] = {x.r[0], x.r[1], x.r[2]};
@@ -247,6 +249,9 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
   }
   int rn[3];
   for (int l = 0; l < 3; ++l) rn[l] = rank_from_tail(lh[l], eps * eps * tot / 3.0);
+  if (c.trace)
+    std::fprintf(stderr, "[tctl] hosvd %s (%d,%d,%d) -> (%d,%d,%d)\n", c.outer ? c.outer : "-", r[0],
+                 r[1], r[2], rn[0], rn[1], rn[2]);
   // new core = core x_l U_l[:, :rn]^T
   double *t1 = c.ws.dbl(sz), *t2 = c.ws.dbl(sz);
   int rc[3] = {r[0], r[1], r[2]};
@@ -267,6 +272,7 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
 
 double tucker_inner(Ctx &c, const Tucker &x, const Tucker &y) {
   if (tucker_empty(x) || tucker_empty(y)) return 0.0;
+  TCTL_PHASE(c, "inner");
   const int n = c.n;
   size_t mk = c.ws.mark();
   double *M[3];
@@ -303,6 +309,7 @@ void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucke
     tucker_hosvd_trunc(c, z, eps);
     return;
   }
+  TCTL_PHASE(c, "axpy");
   size_t mk = c.ws.mark();
   double *My[3];
   int rz[3];
@@ -369,6 +376,7 @@ void cp_to_tucker(Ctx &c, int m, const double *w, double *const U[3], bool to_ei
     out.r[0] = out.r[1] = out.r[2] = 0;
     return;
   }
+  TCTL_PHASE(c, "c2t");
   size_t mk = c.ws.mark();
   double *X[3], *nu[3];
   for (int l = 0; l < 3; ++l) {
@@ -417,33 +425,43 @@ void cp_to_tucker(Ctx &c, int m, const double *w, double *const U[3], bool to_ei
   if (eps_core > 0) tucker_hosvd_trunc(c, out, eps_core);
 }
 
+// Probe factor of mode m for the Khatri-Rao sketches: with Om (n x ls) a fresh
+// Gaussian matrix, P_m[(a,s),k] = sum_i Q_m[i,a] Om[i,s] E_m[i,k]
+// = (KR(Q_m, Om)^T B_m) Z_m, an (r_m ls) x R matrix in the workspace. The same
+// P_m serves the sketches of both other modes (each sketch still draws
+// independent Gaussian vectors in each of its two probe modes).
+static double *sketch_factor(Ctx &c, const Sep &D, const Tucker &x, int m, int ls) {
+  const int n = c.n, R = D.R;
+  const int rm = x.r[m];
+  double *P = c.ws.dbl((size_t)rm * ls * R);
+  size_t mk = c.ws.mark();
+  double *Om = c.ws.dbl((size_t)n * ls);
+  fill_gaussian(c, Om, (size_t)n * ls, c.o.seed * 0x9E3779B97F4A7C15ull + (c.rng_counter++));
+  double *KRm = c.ws.dbl((size_t)n * rm * ls);
+  khatri_rao(c, n, x.Q[m], n, rm, Om, n, ls, KRm, n);
+  if (D.Z[m]) {
+    double *T = c.ws.dbl((size_t)rm * ls * D.rD[m]);
+    gemm(c, true, false, rm * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, T, rm * ls, 0);
+    gemm(c, false, false, rm * ls, R, D.rD[m], 1.0, T, rm * ls, 0, D.Z[m], D.rD[m], 0, 0.0, P,
+         rm * ls, 0);
+  } else {
+    // uncompressed operator: B_m holds the R factor columns themselves
+    gemm(c, true, false, rm * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, P, rm * ls, 0);
+  }
+  c.ws.reset(mk);
+  return P;
+}
+
 // Y (n x ls) = mode-l unfolding of D .* X times ls Khatri-Rao Gaussian probes
-// (one Gaussian vector per other mode per probe). Cl: core permuted so mode l is first.
+// (one Gaussian vector per other mode per probe, from the probe factors P).
+// Cl: core permuted so mode l is first.
 static void sketch_mode(Ctx &c, const Sep &D, const Tucker &x, const double *Cl, int l, int ls,
-                        double *Y) {
+                        double *const P[3], double *Y) {
   const int n = c.n, R = D.R;
   const int r[3] = {x.r[0], x.r[1], x.r[2]};
   const int oth[3][2] = {{1, 2}, {0, 2}, {0, 1}};
   const int m1 = oth[l][0], m2 = oth[l][1];
   size_t mk = c.ws.mark();
-  double *P[3] = {nullptr, nullptr, nullptr};
-  for (int q = 0; q < 2; ++q) {
-    const int m = oth[l][q];
-    double *Om = c.ws.dbl((size_t)n * ls);
-    fill_gaussian(c, Om, (size_t)n * ls, c.o.seed * 0x9E3779B97F4A7C15ull + (c.rng_counter++));
-    // P_m[(a,s),k] = sum_i Q_m[i,a] Om[i,s] E_m[i,k] = (KR(Q_m, Om)^T B_m) Z_m
-    double *KRm = c.ws.dbl((size_t)n * r[m] * ls);
-    khatri_rao(c, n, x.Q[m], n, r[m], Om, n, ls, KRm, n);
-    double *T = c.ws.dbl((size_t)r[m] * ls * D.rD[m]);
-    gemm(c, true, false, r[m] * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, T, r[m] * ls, 0);
-    if (D.Z[m]) {
-      P[m] = c.ws.dbl((size_t)r[m] * ls * R);
-      gemm(c, false, false, r[m] * ls, R, D.rD[m], 1.0, T, r[m] * ls, 0, D.Z[m], D.rD[m], 0, 0.0,
-           P[m], r[m] * ls, 0);
-    } else {
-      P[m] = T;
-    }
-  }
   // v[a,(s,k)] = w_k sum_{b,c} Cl[a,b,c] P_m1[(b,s),k] P_m2[(c,s),k], in chunks of k;
   // uT[(a,s),p] = sum_k v[(a,s),k] Z_l[p,k]
   double *uT = c.ws.dbl((size_t)r[l] * ls * D.rD[l]);
@@ -506,17 +524,35 @@ void sep_apply_trunc(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, double ep
   }
   // ---------------- range finding per mode
   int ls = std::min(kMaxRank, rmax + 24);
+  const double rtol = std::max(1e-8, c.o.range_tol * eps);
+  TCTL_PHASE(c, "sep_sketch");
   for (int l = 0; l < 3; ++l) {
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      double *Y = c.ws.dbl((size_t)n * ls);
-      sketch_mode(c, D, x, Cl[l], l, ls, Y);
-      Qn[l] = c.ws.dbl((size_t)n * kMaxRank);
-      rn[l] = orth(c, n, ls, Y, n, 1e-8, true, kMaxRank, Qn[l]);
-      if (rn[l] < ls || ls >= kMaxRank) break;
-      ls = kMaxRank;  // saturated sketch: enlarge and redo this mode
+    Qn[l] = c.ws.dbl((size_t)n * kMaxRank);
+    rn[l] = 0;
+  }
+  {
+    size_t mks = c.ws.mark();
+    double *P[3] = {nullptr, nullptr, nullptr};
+    int ls_p = 0;  // width the probe factors were drawn with
+    double *Y = c.ws.dbl((size_t)n * kMaxRank);
+    for (int l = 0; l < 3; ++l) {
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        if (ls_p != ls) {
+          c.ws.reset(mks);
+          Y = c.ws.dbl((size_t)n * kMaxRank);
+          for (int m = 0; m < 3; ++m) P[m] = sketch_factor(c, D, x, m, ls);
+          ls_p = ls;
+        }
+        sketch_mode(c, D, x, Cl[l], l, ls, P, Y);
+        rn[l] = orth(c, n, ls, Y, n, rtol, true, kMaxRank, Qn[l]);
+        if (rn[l] < ls || ls >= kMaxRank) break;
+        ls = kMaxRank;  // saturated sketch: enlarge and redo this mode
+      }
     }
+    c.ws.reset(mks);
   }
   // ---------------- core of D .* X in the new bases
+  TCTL_PHASE(c, "sep_core");
   double *M[3];
   for (int l = 0; l < 3; ++l) {
     // N_l[(a',b), p] = sum_i Qn[i,a'] Q[i,b] B[i,p];  M_l = N_l Z_l : (rn r) x R
@@ -568,6 +604,10 @@ void sep_apply_trunc(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, double ep
   copy_d(c, y.core, nc, (size_t)szo);
   c.ws.reset(mk);
   tucker_hosvd_trunc(c, y, eps);
+  if (c.trace)
+    std::fprintf(stderr, "[tctl] %s R=%d x=(%d,%d,%d) ls=%d range=(%d,%d,%d) out=(%d,%d,%d)\n",
+                 c.outer ? c.outer : "apply", R, r[0], r[1], r[2], ls, rn[0], rn[1], rn[2], y.r[0],
+                 y.r[1], y.r[2]);
 }
 
 int tucker_to_cp(Ctx &c, const Tucker &x, bool from_eig, double eps, tctl_cp *y) {
@@ -576,6 +616,7 @@ int tucker_to_cp(Ctx &c, const Tucker &x, bool from_eig, double eps, tctl_cp *y)
     y->rank = 0;
     return TCTL_OK;
   }
+  TCTL_PHASE(c, "t2c");
   size_t mk = c.ws.mark();
   const int r0 = x.r[0], r1 = x.r[1], r2 = x.r[2];
   double *Qp[3];

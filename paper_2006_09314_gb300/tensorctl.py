@@ -58,7 +58,7 @@ class Opts(ctypes.Structure):
                 ("rank_cap", ctypes.c_int), ("precision", ctypes.c_int),
                 ("basis", ctypes.c_int), ("expsum_src", ctypes.c_int),
                 ("paper_end_rows", ctypes.c_int), ("eps_final", ctypes.c_double),
-                ("seed", ctypes.c_ulonglong)]
+                ("seed", ctypes.c_ulonglong), ("range_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -294,12 +294,13 @@ def tctl_launch_count(ctx):
 
 
 def tctl_profile_enable(ctx, on=True):
-    _check(load().tctl_profile_enable(ctx, 1 if on else 0), ctx)
+    """on: False/0 off, True/1 per kernel, 2 per (PCG step, phase, kernel)."""
+    _check(load().tctl_profile_enable(ctx, int(on)), ctx)
 
 
 def tctl_profile_report(ctx):
     import json
-    buf = ctypes.create_string_buffer(1 << 16)
+    buf = ctypes.create_string_buffer(1 << 18)
     _check(load().tctl_profile_report(ctx, buf, len(buf)), ctx)
     return json.loads(buf.value.decode())
 

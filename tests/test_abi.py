@@ -32,6 +32,7 @@ def test_default_opts_and_error_paths_without_gpu():
     from paper_2006_09314_gb300 import tensorctl as T
     o = T.tctl_default_opts()
     assert o.pcg_rtol == 1e-7 and o.max_iter == 100 and o.basis == 1 and o.r_pre == 24
+    assert o.range_tol == 0.1 and o.seed == 1
     lib = T.load()
     # argument validation happens before any device work
     import ctypes
@@ -43,6 +44,11 @@ def test_default_opts_and_error_paths_without_gpu():
     coeffs[2, 4] = 0.0
     assert lib.tctl_setup(ctypes.byref(ctx), coeffs.ctypes.data, 8, 0.5, 1e-2, 1e-6, None, None) == -2
     assert "positive" in T.tctl_last_error(None)
+    coeffs[2, 4] = 1.0
+    bad = T.tctl_default_opts(range_tol=2.0)
+    assert lib.tctl_setup(ctypes.byref(ctx), coeffs.ctypes.data, 8, 0.5, 1e-2, 1e-6,
+                          ctypes.byref(bad), None) == -1
+    assert "range_tol" in T.tctl_last_error(None)
 
 
 def test_inputs_generator_is_seeded():
