@@ -75,14 +75,16 @@ typedef struct {
                          solver always runs in FP64.                                   */
   int basis;          /* 1 = PCG vectors kept in eigenbasis coordinates (default);
                          0 = paper form, mode products with V_l in every apply         */
-  int expsum_src;     /* 0 = sinc quadrature (only value implemented)                 */
+  int expsum_src;     /* separable F2: 0 = sinc quadrature (Section 3.4); 1 = fitted
+                         exponential sum of F2(s)/s (default; falls back to sinc
+                         when the fit misses op_tol)                                   */
   int paper_end_rows; /* 1 = the paper's printed end rows of A_(l) (default 0)        */
   double eps_final;   /* truncation of the returned solution; <= 0 means eps/10       */
   unsigned long long seed; /* seed of the sketching random numbers (default 1)       */
   double range_tol;   /* range finder of the truncated Hadamard products F2 .* x and
                          P .* x: a direction of the mode-l sketch is kept while its
                          residual exceeds max(1e-8, range_tol * eps_trunc) of the
-                         largest sketch column (default 0.1)                           */
+                         largest sketch column (default 0.03)                          */
 } tctl_opts;
 
 typedef struct {
@@ -97,6 +99,7 @@ typedef struct {
   double s_min, s_max;   /* spectral interval of A                                    */
   double t_setup_ms;     /* time of tctl_setup                                       */
   double t_solve_ms;     /* time of the last tctl_pcg_solve                          */
+  int expsum_used;       /* representation of F2 in use: 0 sinc, 1 fitted             */
 } tctl_stats;
 
 /* Fills *o with the defaults listed above. */
@@ -166,6 +169,28 @@ int tctl_get_eigs(tctl_ctx *ctx, int mode, double *lam, double *V);
 
 /* Copies the statistics of the context (setup data and last solve) to *st. */
 int tctl_get_stats(tctl_ctx *ctx, tctl_stats *st);
+
+/* The fitted exponential sum behind expsum_src = 1 (host only, no device
+ * work, no context): g(s) ~ sum_k w_k exp(-t_k s) on [s_min, s_max], t_k >= 0
+ * (t_0 = 0 is a constant term), w_k > 0, where g = F2(s)/s = s^(-1-alpha) +
+ * beta s^(alpha-1) for alpha < 1 (F2 ~ s g) and g = 1/s for alpha = 1
+ * (F2 ~ g + beta s, exact positive power). The node count is the smallest
+ * (to within a few) for which the max relative error of F2, measured on 2000
+ * log-spaced points of [s_min, s_max], is <= tol; *err receives it and *r
+ * the number of terms. t, w: HOST buffers of cap entries. Errors: TCTL_E_ARG,
+ * TCTL_E_RANK_CAP (r > cap, first cap copied), TCTL_E_NUMERIC (tol not met;
+ * the buffers hold the best fit found). */
+int tctl_expsum_fit(double alpha, double beta, double s_min, double s_max, double tol, double *t,
+                    double *w, int cap, int *r, double *err);
+
+/* Copies the separable representation in use (Sections 3.4, 3.5): which = 0
+ * the operator F2 (R terms), 1 the preconditioner. Term k is the Kronecker
+ * product over the modes l of diag(f_lk(lambda^(l))) with f_lk(x) =
+ * (m[k] == l ? x : 1) exp(-t[k] x), weighted by w[k]; on the eigenbasis grid
+ * the sum is the approximation of F2(lambda_i + lambda_j + lambda_k) (resp.
+ * of its inverse). t, w, m: HOST buffers of cap entries; *R receives the
+ * number of terms. TCTL_E_RANK_CAP if R > cap (the first cap are copied). */
+int tctl_get_expsum(tctl_ctx *ctx, int which, double *t, double *w, int *m, int cap, int *R);
 
 /* Number of GPU kernel launches issued by the context since setup (counter
  * kept by the library's own launch wrappers). */

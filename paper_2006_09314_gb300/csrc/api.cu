@@ -119,15 +119,18 @@ int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
         tucker_axpby_trunc(c, 1.0, X, a, P, T2, eps_x);  // X = trunc(X + a P)
       }
       std::swap(X, T2);
+      // R = trunc(R - a S); the stopping test uses ||R - a S|| before the
+      // truncation, and a converged residual is not truncated (not used again)
+      double rnorm = 0.0;
       {
         TCTL_OUTER(c, "update_r");
-        tucker_axpby_trunc(c, 1.0, R, -a, S, T2, eps);   // R = trunc(R - a S)
+        tucker_axpby_trunc(c, 1.0, R, -a, S, T2, eps, &rnorm, c.o.pcg_rtol * bnorm);
       }
       std::swap(R, T2);
       track(X);
       track(R);
       ++iters;
-      rel = std::sqrt(std::max(tucker_inner(c, R, R), 0.0)) / bnorm;
+      rel = rnorm / bnorm;
       if (!std::isfinite(rel)) fail(TCTL_E_NAN, "non-finite residual");
       if (rel <= c.o.pcg_rtol) break;
       {
@@ -173,11 +176,11 @@ int tctl_default_opts(tctl_opts *o) {
   o->rank_cap = kCap;
   o->precision = 0;
   o->basis = 1;
-  o->expsum_src = 0;
+  o->expsum_src = 1;
   o->paper_end_rows = 0;
   o->eps_final = 0.0;
   o->seed = 1;
-  o->range_tol = 0.1;
+  o->range_tol = 0.03;
   return TCTL_OK;
 }
 
@@ -203,7 +206,8 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
       fail(TCTL_E_ARG, "precision must be 0 (FP64) or 1 (tensor-core digit split)");
     if (c->o.precision == 1 && !tc_fullgrid_supported(n))
       fail(TCTL_E_ARG, "precision 1 needs n a multiple of 128 and n <= 1024");
-    if (c->o.expsum_src != 0) fail(TCTL_E_ARG, "only expsum_src 0 (sinc) is implemented");
+    if (c->o.expsum_src != 0 && c->o.expsum_src != 1)
+      fail(TCTL_E_ARG, "expsum_src must be 0 (sinc) or 1 (fitted)");
     if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
     if (!(c->o.range_tol >= 0.0 && c->o.range_tol <= 1.0))
       fail(TCTL_E_ARG, "range_tol must lie in [0, 1]");
@@ -238,6 +242,7 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
     c->stats.pre_rank = c->pre.R;
     for (int l = 0; l < 3; ++l) c->stats.op_basis[l] = c->op.rD[l];
     c->stats.op_rel_err = c->op_rel_err;
+    c->stats.expsum_used = c->expsum_used;
     c->stats.s_min = c->s_min;
     c->stats.s_max = c->s_max;
     *ctx = reinterpret_cast<tctl_ctx *>(c);
@@ -411,6 +416,48 @@ int tctl_solve_host(const double *coeffs, int n, double alpha, double beta, doub
   tctl_cp_free(ctx, &x);
   tctl_destroy(ctx);
   return s;
+}
+
+int tctl_expsum_fit(double alpha, double beta, double s_min, double s_max, double tol, double *t,
+                    double *w, int cap, int *r, double *err) {
+  try {
+    if (!(alpha > 0.0 && alpha <= 1.0)) fail(TCTL_E_ARG, "alpha must be in (0, 1]");
+    if (!(beta > 0.0) || !std::isfinite(beta)) fail(TCTL_E_ARG, "beta must be positive");
+    if (!(s_min > 0.0 && s_max > s_min && std::isfinite(s_max)))
+      fail(TCTL_E_ARG, "need 0 < s_min < s_max < inf");
+    if (!(tol > 0.0 && tol < 1.0)) fail(TCTL_E_ARG, "tol must be in (0, 1)");
+    if (cap < 0 || (cap > 0 && (!t || !w))) fail(TCTL_E_ARG, "NULL output buffer");
+    const int s = expsum_fit_host(alpha, beta, s_min, s_max, tol, t, w, cap, r, err);
+    if (s == TCTL_E_RANK_CAP) fail(s, "more terms than cap");
+    if (s == TCTL_E_NUMERIC) fail(s, "fitted exponential sum misses the tolerance");
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(nullptr, e);
+  }
+}
+
+int tctl_get_expsum(tctl_ctx *ctx, int which, double *t, double *w, int *m, int cap, int *R) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return TCTL_E_ARG;
+  try {
+    if (which != 0 && which != 1) fail(TCTL_E_ARG, "which must be 0 (operator) or 1 (preconditioner)");
+    if (cap < 0 || (cap > 0 && (!t || !w || !m))) fail(TCTL_E_ARG, "NULL output buffer");
+    const std::vector<double> &tw = which == 0 ? c->op_terms_w : c->pre_terms_w;
+    const std::vector<double> &tt = which == 0 ? c->op_terms_t : c->pre_terms_t;
+    const std::vector<int> &tm = which == 0 ? c->op_terms_m : c->pre_terms_m;
+    const int n = (int)tw.size();
+    if (R) *R = n;
+    const int k = std::min(n, cap);
+    for (int i = 0; i < k; ++i) {
+      t[i] = tt[i];
+      w[i] = tw[i];
+      m[i] = tm[i];
+    }
+    if (n > cap) fail(TCTL_E_RANK_CAP, "more terms than cap");
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
 }
 
 int tctl_profile_enable(tctl_ctx *ctx, int on) {

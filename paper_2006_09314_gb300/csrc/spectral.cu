@@ -16,6 +16,20 @@
 // P(s) F2(s) = 1 on 256 geometric sample points of [s_min, s_max]; the K
 // nodes theta_k are geometric in [0.05/s_max, 20/s_min].
 //
+// Fitted exponential sum (expsum_src = 1, the default; the paper gives only
+// the sinc construction, with rank bounds). For alpha < 1, g(s) = F2(s)/s =
+// s^(-1-alpha) + beta s^(alpha-1) is completely monotone (a sum of negative
+// powers), so it has exponential sums with positive weights:
+// g(s) ~ w_0 + sum_k w_k exp(-t_k s), t_k geometric in [lo/s_max, hi/s_min],
+// w_0 a constant term. Then F2(s) = s g(s) needs 3 Kronecker terms per
+// exponential (s = lambda_i + lambda_j + lambda_k): one function instead of
+// the sinc form's two. For alpha = 1, beta s is exact (3 terms) and g = 1/s. The weights minimise the relative
+// error of g on 400 log-spaced samples under w >= 0 (Lawson-Hanson NNLS,
+// which adds one node at a time and so stays stable although the full
+// exponential basis is nearly collinear). The number of nodes grows until the
+// measured max relative error of F2 on [s_min, s_max] is <= op_tol; if no fit
+// reaches it the sinc sum is used.
+//
 // Every exponential factorises over the modes, so each term is a Kronecker
 // product of three diagonal matrices in the eigenbasis; the factor matrices
 // E_l[i, k] = (lambda_i^(l) or 1) * exp(-t_k lambda_i^(l)) are built on the GPU.
@@ -120,10 +134,10 @@ std::vector<double> ls_solve(const std::vector<double> &A, int M, int K, const s
 
 std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::vector<double> &b) {
   std::vector<double> x(K, 0.0);
-  std::vector<char> passive(K, 0);
-  const double tol = 10.0 * 2.2e-16 * 1.0 * std::max(M, K);
-  for (int outer = 0; outer < 30 * K; ++outer) {
-    // w = A^T (b - A x)
+  std::vector<char> passive(K, 0), blocked(K, 0);
+  const double tol = 1e-15;  // the duals of this ill-conditioned basis are tiny
+  for (int outer = 0; outer < 3 * K; ++outer) {
+    // dual w = A^T (b - A x); the most positive free, unblocked coordinate enters
     std::vector<double> res(b);
     for (int k = 0; k < K; ++k)
       if (x[k] != 0)
@@ -131,7 +145,7 @@ std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::
     int jmax = -1;
     double wmax = tol;
     for (int k = 0; k < K; ++k) {
-      if (passive[k]) continue;
+      if (passive[k] || blocked[k]) continue;
       double w = 0;
       for (int i = 0; i < M; ++i) w += A[i + (size_t)k * M] * res[i];
       if (w > wmax) { wmax = w; jmax = k; }
@@ -142,23 +156,108 @@ std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::
       std::vector<int> cols;
       for (int k = 0; k < K; ++k)
         if (passive[k]) cols.push_back(k);
-      std::vector<double> z = ls_solve(A, M, K, cols, b);
+      const std::vector<double> z = ls_solve(A, M, K, cols, b);
       bool allpos = true;
       for (double v : z) allpos = allpos && (v > 0);
       if (allpos) {
         std::fill(x.begin(), x.end(), 0.0);
         for (size_t j = 0; j < cols.size(); ++j) x[cols[j]] = z[j];
+        std::fill(blocked.begin(), blocked.end(), 0);
         break;
       }
+      // step from x toward z until the first passive coordinate reaches zero
       double amin = 1e300;
+      int imin = -1;
       for (size_t j = 0; j < cols.size(); ++j)
-        if (z[j] <= 0) amin = std::min(amin, x[cols[j]] / (x[cols[j]] - z[j]));
+        if (z[j] <= 0) {
+          const double al = x[cols[j]] / (x[cols[j]] - z[j]);
+          if (al < amin) { amin = al; imin = cols[j]; }
+        }
       for (size_t j = 0; j < cols.size(); ++j) x[cols[j]] += amin * (z[j] - x[cols[j]]);
+      x[imin] = 0.0;
       for (size_t j = 0; j < cols.size(); ++j)
-        if (x[cols[j]] <= 1e-300) { passive[cols[j]] = 0; x[cols[j]] = 0; }
+        if (x[cols[j]] <= 0.0) { passive[cols[j]] = 0; x[cols[j]] = 0.0; }
+      // the entering coordinate left at once: it cannot improve the fit now
+      if (imin == jmax && amin == 0.0) { blocked[jmax] = 1; break; }
     }
   }
   return x;
+}
+
+// The fitted function: g = F2/s for alpha < 1 (F2 ~ s g); for alpha = 1 the
+// positive power is exactly beta s and g = 1/s (F2 ~ g + beta s).
+double g_of_s(double s, double a, double b) {
+  return a >= 1.0 ? 1.0 / s : std::pow(s, -1.0 - a) + b * std::pow(s, a - 1.0);
+}
+
+struct ExpFit {
+  std::vector<double> t, w;  // g(s) ~ sum_k w_k exp(-t_k s) (t_0 = 0: the constant)
+  double err = 1e300;        // measured max relative error of F2 = s g
+};
+
+double measure_F2_fit(const ExpFit &f, double a, double b, double smin, double smax) {
+  double emax = 0;
+  const int M = 2000;
+  for (int j = 0; j < M; ++j) {
+    const double s = std::exp(std::log(smin) + (std::log(smax) - std::log(smin)) * j / (M - 1));
+    double v = 0;
+    for (size_t k = 0; k < f.t.size(); ++k) v += f.w[k] * std::exp(-f.t[k] * s);
+    const double ex = F2h(s, a, b);
+    const double ap = a >= 1.0 ? v + b * s : s * v;
+    emax = std::max(emax, std::fabs(ap - ex) / ex);
+  }
+  return emax;
+}
+
+ExpFit fit_g(double a, double b, double smin, double smax, int r, double lo, double hi) {
+  constexpr int M = 400;
+  const double rho = smax / smin, g0 = g_of_s(smin, a, b);
+  std::vector<double> x(M), G(M), tau(r);
+  for (int j = 0; j < M; ++j) {
+    x[j] = std::exp(std::log(rho) * j / (M - 1));
+    G[j] = g_of_s(smin * x[j], a, b) / g0;
+  }
+  tau[0] = 0.0;
+  for (int k = 1; k < r; ++k)
+    tau[k] = std::exp(std::log(lo / rho) + (std::log(hi) - std::log(lo / rho)) * (k - 1) / std::max(1, r - 2));
+  // relative residual sum_k c_k exp(-tau_k x_j) / G_j - 1, columns scaled to unit norm
+  std::vector<double> A((size_t)M * r), cs(r), rhs(M, 1.0);
+  for (int k = 0; k < r; ++k) {
+    double nrm = 0;
+    for (int j = 0; j < M; ++j) {
+      const double v = std::exp(-tau[k] * x[j]) / G[j];
+      A[j + (size_t)k * M] = v;
+      nrm += v * v;
+    }
+    cs[k] = std::sqrt(nrm);
+    for (int j = 0; j < M; ++j) A[j + (size_t)k * M] /= cs[k];
+  }
+  const std::vector<double> c = nnls(A, M, r, rhs);
+  ExpFit out;
+  for (int k = 0; k < r; ++k) {
+    if (!(c[k] > 0)) continue;
+    out.t.push_back(tau[k] / smin);
+    out.w.push_back(c[k] / cs[k] * g0);
+  }
+  out.err = out.t.empty() ? 1e300 : measure_F2_fit(out, a, b, smin, smax);
+  return out;
+}
+
+// Smallest fitted sum (to a few nodes) with measured error <= tol: nodes in
+// [0.1/s_max, 20/s_min]; r starts at 40 and is then set from the observed
+// rate of about a decade per 5 nodes, raised by 3 until the fit passes.
+ExpFit fit_F2(double a, double b, double smin, double smax, double tol) {
+  constexpr int r0 = 40, rmax = 96;
+  constexpr double lo = 0.1, hi = 20.0;
+  ExpFit best = fit_g(a, b, smin, smax, r0, lo, hi);
+  if (best.err <= tol) return best;
+  int r = r0 + (int)std::ceil(5.0 * std::log10(best.err / tol));
+  for (int attempt = 0; attempt < 8 && r <= rmax; ++attempt, r += 3) {
+    ExpFit f = fit_g(a, b, smin, smax, r, lo, hi);
+    if (f.err <= tol) return f;
+    if (f.err < best.err) best = f;
+  }
+  return best;
 }
 
 // Term descriptor of one canonical column: factor in mode l is
@@ -291,45 +390,83 @@ void compress_sep(Ctx &c, Sep &D, double tol) {
 
 }  // namespace
 
+int expsum_fit_host(double a, double b, double smin, double smax, double tol, double *t, double *w,
+                    int cap, int *r, double *err) {
+  const ExpFit f = fit_F2(a, b, smin, smax, tol);
+  const int n = (int)f.t.size();
+  if (r) *r = n;
+  if (err) *err = f.err;
+  for (int k = 0; k < std::min(n, cap); ++k) {
+    t[k] = f.t[k];
+    w[k] = f.w[k];
+  }
+  if (n > cap) return TCTL_E_RANK_CAP;
+  return f.err <= tol ? TCTL_OK : TCTL_E_NUMERIC;
+}
+
 void setup_spectral(Ctx &c) {
   const double a = c.alpha, b = c.beta, smin = c.s_min, smax = c.s_max;
   const double delta = c.o.op_tol;
   // ---- operator F2 (term order as in the canonical factor layout)
-  const double F2min = min_F2(a, b, smin, smax), F2lo = F2h(smin, a, b), F2hi = F2h(smax, a, b);
-  std::vector<double> t1, w1, t2, w2;
-  {
-    const SincRule s = sinc_rule(a, 0.5 * delta, smin, 1.0 / F2min,
-                                 0.25 * 0.5 * delta * std::tgamma(a) * F2lo * std::pow(smin, a));
-    sinc_nodes(a, s, t1, w1);
-  }
-  const bool exact_linear = (a >= 1.0);
-  if (!exact_linear) {
-    const double g = 1.0 - a;
-    const SincRule s = sinc_rule(g, 0.5 * delta, smin, b * smax / F2hi,
-                                 0.25 * 0.5 * delta * std::tgamma(g) * F2lo * std::pow(smin, g) /
-                                     (b * smin));
-    sinc_nodes(g, s, t2, w2);
-  }
   std::vector<double> w;
   std::vector<TermDesc> td;
-  for (size_t k = 0; k < t1.size(); ++k) {
-    w.push_back(w1[k]);
-    td.push_back({t1[k], -1});
-  }
-  if (exact_linear) {
-    for (int m = 0; m < 3; ++m) {
-      w.push_back(b);
-      td.push_back({0.0, m});
-    }
-  } else {
-    for (size_t k = 0; k < t2.size(); ++k)
-      for (int m = 0; m < 3; ++m) {
-        w.push_back(b * w2[k]);
-        td.push_back({t2[k], m});
+  c.expsum_used = 0;
+  if (c.o.expsum_src == 1) {
+    const ExpFit f = fit_F2(a, b, smin, smax, delta);
+    if (f.err <= delta) {
+      if (a >= 1.0) {
+        for (size_t k = 0; k < f.t.size(); ++k) {
+          w.push_back(f.w[k]);
+          td.push_back({f.t[k], -1});
+        }
+        for (int m = 0; m < 3; ++m) {
+          w.push_back(b);
+          td.push_back({0.0, m});
+        }
+      } else {
+        for (size_t k = 0; k < f.t.size(); ++k)
+          for (int m = 0; m < 3; ++m) {
+            w.push_back(f.w[k]);
+            td.push_back({f.t[k], m});
+          }
       }
+      c.op_rel_err = f.err;
+      c.expsum_used = 1;
+    }
   }
-  // measured relative error of the representation on a sample of [s_min, s_max]
-  {
+  if (c.expsum_used == 0) {
+    const double F2min = min_F2(a, b, smin, smax), F2lo = F2h(smin, a, b), F2hi = F2h(smax, a, b);
+    std::vector<double> t1, w1, t2, w2;
+    {
+      const SincRule s = sinc_rule(a, 0.5 * delta, smin, 1.0 / F2min,
+                                   0.25 * 0.5 * delta * std::tgamma(a) * F2lo * std::pow(smin, a));
+      sinc_nodes(a, s, t1, w1);
+    }
+    const bool exact_linear = (a >= 1.0);
+    if (!exact_linear) {
+      const double g = 1.0 - a;
+      const SincRule s = sinc_rule(g, 0.5 * delta, smin, b * smax / F2hi,
+                                   0.25 * 0.5 * delta * std::tgamma(g) * F2lo * std::pow(smin, g) /
+                                       (b * smin));
+      sinc_nodes(g, s, t2, w2);
+    }
+    for (size_t k = 0; k < t1.size(); ++k) {
+      w.push_back(w1[k]);
+      td.push_back({t1[k], -1});
+    }
+    if (exact_linear) {
+      for (int m = 0; m < 3; ++m) {
+        w.push_back(b);
+        td.push_back({0.0, m});
+      }
+    } else {
+      for (size_t k = 0; k < t2.size(); ++k)
+        for (int m = 0; m < 3; ++m) {
+          w.push_back(b * w2[k]);
+          td.push_back({t2[k], m});
+        }
+    }
+    // measured relative error of the representation on a sample of [s_min, s_max]
     double emax = 0;
     const int M = 2000;
     for (int j = 0; j < M; ++j) {
@@ -346,6 +483,13 @@ void setup_spectral(Ctx &c) {
       emax = std::max(emax, std::fabs(v - ex) / ex);
     }
     c.op_rel_err = emax;
+  }
+  c.op_terms_w = w;
+  c.op_terms_t.clear();
+  c.op_terms_m.clear();
+  for (const TermDesc &d : td) {
+    c.op_terms_t.push_back(d.t);
+    c.op_terms_m.push_back(d.lam_mode);
   }
   build_sep(c, c.op, w, td);
   compress_sep(c, c.op, 1e-13);
@@ -381,6 +525,13 @@ void setup_spectral(Ctx &c) {
     }
   }
   if (pw.empty()) fail(TCTL_E_NUMERIC, "preconditioner fit produced no positive weight");
+  c.pre_terms_w = pw;
+  c.pre_terms_t.clear();
+  c.pre_terms_m.clear();
+  for (const TermDesc &d : ptd) {
+    c.pre_terms_t.push_back(d.t);
+    c.pre_terms_m.push_back(d.lam_mode);
+  }
   build_sep(c, c.pre, pw, ptd);
   compress_sep(c, c.pre, 1e-13);
 }

@@ -82,6 +82,9 @@ struct Ctx {
   double s_min = 0, s_max = 0;
   Sep op, pre;
   double op_rel_err = 0;
+  int expsum_used = 0;                     // 0 sinc, 1 fitted
+  std::vector<double> op_terms_w, op_terms_t, pre_terms_w, pre_terms_t;  // host copies
+  std::vector<int> op_terms_m, pre_terms_m;
   Arena ws;
   double *full_tmp = nullptr;        // n^3 temporary of the FP64 full-grid solve
   // tensor-core full grid: digit planes of V_l^T / V_l, row exponents, two FP32
@@ -188,6 +191,8 @@ void to_dev(Ctx &c, double *dst, const double *src, size_t count);
 void setup_eigs(Ctx &c);
 
 // ------------------------------------------------------------ spectral.cu
+int expsum_fit_host(double a, double b, double smin, double smax, double tol, double *t, double *w,
+                    int cap, int *r, double *err);
 void setup_spectral(Ctx &c);
 void fullgrid_apply(Ctx &c, const double *y, double *u, int which);
 
@@ -207,9 +212,11 @@ void tucker_alloc(Ctx &c, Tucker &t, int cap);
 void tucker_copy(Ctx &c, const Tucker &src, Tucker &dst);
 // y = trunc(D .* x) with D separable (eigenbasis), eps relative.
 void sep_apply_trunc(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, double eps);
-// z = trunc(a x + b y)
+// z = trunc(a x + b y). With norm_out, ||a x + b y|| (before truncation) is
+// returned there, and the truncation is skipped when it is <= keep_below.
 void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucker &y,
-                        Tucker &z, double eps);
+                        Tucker &z, double eps, double *norm_out = nullptr,
+                        double keep_below = -1.0);
 double tucker_inner(Ctx &c, const Tucker &x, const Tucker &y);
 // Truncate a Tucker tensor in place by HOSVD of its core (eps relative).
 void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps);

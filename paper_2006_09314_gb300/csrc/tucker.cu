@@ -295,18 +295,27 @@ double tucker_inner(Ctx &c, const Tucker &x, const Tucker &y) {
 }
 
 void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucker &y, Tucker &z,
-                        double eps) {
+                        double eps, double *norm_out, double keep_below) {
+  // orthonormal bases throughout: the norm of the sum is the norm of its core
+  auto finish = [&]() {
+    if (norm_out) {
+      const long long sz = (long long)z.r[0] * z.r[1] * z.r[2];
+      *norm_out = std::sqrt(std::max(dot_host(c, sz, z.core, z.core), 0.0));
+      if (*norm_out <= keep_below) return;
+    }
+    tucker_hosvd_trunc(c, z, eps);
+  };
   const int n = c.n;
   if (tucker_empty(x) || a == 0.0) {
     tucker_copy(c, y, z);
     axpby(c, (size_t)y.r[0] * y.r[1] * y.r[2], b, y.core, 0.0, z.core);
-    tucker_hosvd_trunc(c, z, eps);
+    finish();
     return;
   }
   if (tucker_empty(y) || b == 0.0) {
     tucker_copy(c, x, z);
     axpby(c, (size_t)x.r[0] * x.r[1] * x.r[2], a, x.core, 0.0, z.core);
-    tucker_hosvd_trunc(c, z, eps);
+    finish();
     return;
   }
   TCTL_PHASE(c, "axpy");
@@ -354,7 +363,7 @@ void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucke
   }
   copy_d(c, z.core, core, (size_t)szz);
   c.ws.reset(mk);
-  tucker_hosvd_trunc(c, z, eps);
+  finish();
 }
 
 void tucker_basis_change(Ctx &c, Tucker &x, bool to_eig) {

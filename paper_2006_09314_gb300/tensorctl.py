@@ -34,7 +34,8 @@ EXPORTED = [
     "tctl_truncate", "tctl_pcg_solve", "tctl_fullgrid_solve", "tctl_fullgrid_state",
     "tctl_solve_host", "tctl_cp_alloc", "tctl_cp_free", "tctl_get_eigs",
     "tctl_get_stats", "tctl_launch_count", "tctl_destroy", "tctl_last_error",
-    "tctl_profile_enable", "tctl_profile_report", "tctl_eig1d_noalloc",
+    "tctl_profile_enable", "tctl_profile_report", "tctl_eig1d_noalloc", "tctl_get_expsum",
+    "tctl_expsum_fit",
 ]
 
 ERRORS = {0: "OK", -1: "E_ARG", -2: "E_COEFF", -3: "E_CUDA", -4: "E_NOMEM",
@@ -67,7 +68,8 @@ class Stats(ctypes.Structure):
                 ("op_rank", ctypes.c_int), ("op_basis", ctypes.c_int * 3),
                 ("pre_rank", ctypes.c_int), ("op_rel_err", ctypes.c_double),
                 ("s_min", ctypes.c_double), ("s_max", ctypes.c_double),
-                ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double)]
+                ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
+                ("expsum_used", ctypes.c_int)]
 
     def as_dict(self):
         out = {}
@@ -116,6 +118,8 @@ def load(build_if_missing: bool = True):
         "tctl_profile_enable": (I, [P, I]),
         "tctl_profile_report": (I, [P, ctypes.c_char_p, I]),
         "tctl_eig1d_noalloc": (I, [P, I, I, P, P, P]),
+        "tctl_get_expsum": (I, [P, I, P, P, P, I, P]),
+        "tctl_expsum_fit": (I, [D, D, D, D, D, P, P, I, P, P]),
         "tctl_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -293,6 +297,32 @@ def tctl_launch_count(ctx):
     return int(load().tctl_launch_count(ctx))
 
 
+def tctl_expsum_fit(alpha, beta, s_min, s_max, tol, cap=256):
+    """Fitted exp-sum of F2(s)/s on [s_min, s_max] (host only): (t, w, err)."""
+    import numpy as np
+    t = np.zeros(cap)
+    w = np.zeros(cap)
+    r = ctypes.c_int(0)
+    err = ctypes.c_double(0)
+    _check(load().tctl_expsum_fit(alpha, beta, s_min, s_max, tol, t.ctypes.data, w.ctypes.data, cap,
+                                  ctypes.byref(r), ctypes.byref(err)))
+    return t[:r.value].copy(), w[:r.value].copy(), err.value
+
+
+def tctl_get_expsum(ctx, which=0):
+    """(t, w, m) numpy arrays of the separable operator (which=0) or preconditioner (1)."""
+    import numpy as np
+    R = ctypes.c_int(0)
+    load().tctl_get_expsum(ctx, which, None, None, None, 0, ctypes.byref(R))  # size query
+    n = R.value
+    t = np.zeros(max(n, 1))
+    w = np.zeros(max(n, 1))
+    m = np.zeros(max(n, 1), dtype=np.int32)
+    _check(load().tctl_get_expsum(ctx, which, t.ctypes.data, w.ctypes.data, m.ctypes.data, n,
+                                  ctypes.byref(R)), ctx)
+    return t[:n], w[:n], m[:n]
+
+
 def tctl_profile_enable(ctx, on=True):
     """on: False/0 off, True/1 per kernel, 2 per (PCG step, phase, kernel)."""
     _check(load().tctl_profile_enable(ctx, int(on)), ctx)
@@ -378,6 +408,9 @@ class Context:
 
     def launch_count(self):
         return tctl_launch_count(self.handle)
+
+    def expsum(self, which=0):
+        return tctl_get_expsum(self.handle, which)
 
     def profile(self, on=True):
         tctl_profile_enable(self.handle, on)

@@ -158,14 +158,48 @@ def test_apply_op_matches_oracle(n, alpha, beta):
     exact = fg.apply_spectral(fg.F2(S, alpha, beta), X, Vs)
     rep = es.F2_expsum(alpha, beta, S.min(), S.max(), 1e-8)
     sep = fg.apply_spectral(es.F2_expsum_eval(rep, S.ravel()).reshape(S.shape), X, Vs)
-    with T.Context(pr.coeffs, n, alpha, beta, 1e-6) as ctx:
+    with T.Context(pr.coeffs, n, alpha, beta, 1e-6, opts=T.tctl_default_opts(expsum_src=0)) as ctx:
         st = ctx.stats()
+        assert st["expsum_used"] == 0
         assert st["op_rank"] == len(rep["t1"]) + 3 * max(len(rep["t2"]), 1)
         y = ctx.apply_op(T.CP.from_numpy(pr.yw, pr.yU))
     Yg = _full_from_gpu(y)
     nrm = np.linalg.norm(exact)
     assert np.linalg.norm(Yg - sep) <= 1.1e-6 * nrm
     assert np.linalg.norm(Yg - exact) <= 1.2e-6 * nrm
+
+
+def _expsum_on_grid(t, w, m, lams):
+    """Value of the separable sum on every eigenvalue triple (i, j, k) of the grid."""
+    L = [np.asarray(l) for l in lams]
+    out = np.zeros((len(L[0]), len(L[1]), len(L[2])))
+    for tk, wk, mk in zip(t, w, m):
+        f = [np.exp(-tk * L[l]) * (L[l] if mk == l else 1.0) for l in range(3)]
+        out += wk * f[0][:, None, None] * f[1][None, :, None] * f[2][None, None, :]
+    return out
+
+
+@pytest.mark.parametrize("n,alpha,beta", [(32, 0.5, 1e-2), (29, 0.25, 1e-4), (40, 0.75, 1.0),
+                                          (24, 1.0, 1e-2)])
+def test_fitted_operator_on_the_spectrum(n, alpha, beta):
+    """Fitted exp-sum (default): F2 on every grid triple within 1.5 op_tol; apply parity."""
+    pr = make_problem(n, alpha, beta, 3, 500 + n)
+    lams, Vs = _oracle_eigs(pr)
+    S = fg.spectral_sum(lams)
+    X = F.cp_full(pr.yw, pr.yU)
+    exact = fg.apply_spectral(fg.F2(S, alpha, beta), X, Vs)
+    with T.Context(pr.coeffs, n, alpha, beta, 1e-6) as ctx:
+        st = ctx.stats()
+        t, w, m = ctx.expsum(0)
+        y = ctx.apply_op(T.CP.from_numpy(pr.yw, pr.yU))
+    assert st["expsum_used"] == 1 and st["op_rank"] == len(t)
+    assert st["op_rel_err"] <= 1e-8
+    rep = es.F2_expsum(alpha, beta, S.min(), S.max(), 1e-8)
+    assert len(t) < len(rep["t1"]) + 3 * max(len(rep["t2"]), 1)  # fewer terms than sinc
+    Fs = _expsum_on_grid(t, w, m, lams)
+    ex = fg.F2(S, alpha, beta)
+    assert np.max(np.abs(Fs - ex) / ex) <= 1.5e-8
+    assert np.linalg.norm(_full_from_gpu(y) - exact) <= 1.2e-6 * np.linalg.norm(exact)
 
 
 @pytest.mark.parametrize("n,alpha,beta", [(32, 0.5, 1e-2), (27, 0.75, 1.0)])
