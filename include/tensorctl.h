@@ -85,6 +85,12 @@ typedef struct {
                          P .* x: a direction of the mode-l sketch is kept while its
                          residual exceeds max(1e-8, range_tol * eps_trunc) of the
                          largest sketch column (default 0.03)                          */
+  int tc_gemm;        /* rank-structured contractions (sketches, core projection of
+                         the Hadamard products): 1 = tensor cores, BF16 digit split
+                         (4 digits for the sketches, 6 = 42 bits for the core; FP32
+                         accumulate with exact low levels, FP64 result; default);
+                         0 = FP64 FMA. Gram matrices, orthonormalisation and HOSVD
+                         always run in FP64.                                           */
 } tctl_opts;
 
 typedef struct {
@@ -169,6 +175,19 @@ int tctl_get_eigs(tctl_ctx *ctx, int mode, double *lam, double *V);
 
 /* Copies the statistics of the context (setup data and last solve) to *st. */
 int tctl_get_stats(tctl_ctx *ctx, tctl_stats *st);
+
+/* C = alpha op(A) op(B) + beta C for DEVICE FP64 column-major matrices
+ * (op(A) m x k, op(B) k x n, op = transpose when trans_* != 0), ordered on
+ * the context's stream. digits = 0: FP64 FMA kernels; digits = 4 or 6: the
+ * tensor-core digit split of the rank-structured path (each operand as 4 / 6
+ * signed 7-bit BF16 digits with one binary exponent per row of op(A) and per
+ * column of op(B); FP32 accumulation with exact leading levels, 256-deep K
+ * chunks summed in FP64). Error per entry ~2^-7d K max|A_i.| max|B_.j|.
+ * Synchronizes (checks the kernels' bounded waits) when digits > 0.
+ * Errors: TCTL_E_ARG, TCTL_E_CUDA, TCTL_E_NUMERIC (a wait timed out). */
+int tctl_gemm(tctl_ctx *ctx, int digits, int trans_a, int trans_b, int m, int n, int k,
+              double alpha, const double *A, int lda, const double *B, int ldb, double beta,
+              double *C, int ldc);
 
 /* The fitted exponential sum behind expsum_src = 1 (host only, no device
  * work, no context): g(s) ~ sum_k w_k exp(-t_k s) on [s_min, s_max], t_k >= 0

@@ -150,6 +150,7 @@ int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
     if (rel > c.o.pcg_rtol) status = TCTL_E_NOT_CONVERGED;
     TCTL_OUTER(c, "to_cp");
     const int s2 = tucker_to_cp(c, X, eig, eps_x, x);
+    tcg_check(c);
     if (status == TCTL_OK) status = s2;
   }
   c.stats.iters = iters;
@@ -181,6 +182,7 @@ int tctl_default_opts(tctl_opts *o) {
   o->eps_final = 0.0;
   o->seed = 1;
   o->range_tol = 0.03;
+  o->tc_gemm = 1;
   return TCTL_OK;
 }
 
@@ -209,6 +211,7 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
     if (c->o.expsum_src != 0 && c->o.expsum_src != 1)
       fail(TCTL_E_ARG, "expsum_src must be 0 (sinc) or 1 (fitted)");
     if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
+    if (c->o.tc_gemm != 0 && c->o.tc_gemm != 1) fail(TCTL_E_ARG, "tc_gemm must be 0 or 1");
     if (!(c->o.range_tol >= 0.0 && c->o.range_tol <= 1.0))
       fail(TCTL_E_ARG, "range_tol must lie in [0, 1]");
     if (!(c->o.op_tol > 0 && c->o.op_tol < 1e-2)) fail(TCTL_E_ARG, "op_tol must be in (0, 1e-2)");
@@ -416,6 +419,30 @@ int tctl_solve_host(const double *coeffs, int n, double alpha, double beta, doub
   tctl_cp_free(ctx, &x);
   tctl_destroy(ctx);
   return s;
+}
+
+int tctl_gemm(tctl_ctx *ctx, int digits, int trans_a, int trans_b, int m, int n, int k,
+              double alpha, const double *A, int lda, const double *B, int ldb, double beta,
+              double *C, int ldc) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return TCTL_E_ARG;
+  try {
+    if (m < 0 || n < 0 || k < 0) fail(TCTL_E_ARG, "negative dimension");
+    if (digits != 0 && digits != 4 && digits != 6) fail(TCTL_E_ARG, "digits must be 0, 4 or 6");
+    if ((m && n && k) && (!A || !B || !C)) fail(TCTL_E_ARG, "NULL matrix");
+    if (lda < std::max(1, trans_a ? k : m) || ldb < std::max(1, trans_b ? n : k) || ldc < std::max(1, m))
+      fail(TCTL_E_ARG, "leading dimension too small");
+    if (m == 0 || n == 0) return TCTL_OK;
+    if (digits == 0 || k == 0)
+      gemm(*c, trans_a != 0, trans_b != 0, m, n, k, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0);
+    else {
+      gemm_tc_cm(*c, digits, trans_a != 0, trans_b != 0, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+      tcg_check(*c);
+    }
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
 }
 
 int tctl_expsum_fit(double alpha, double beta, double s_min, double s_max, double tol, double *t,

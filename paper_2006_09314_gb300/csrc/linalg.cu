@@ -511,12 +511,10 @@ static void jacobi_launch(Ctx &c, const std::vector<EigDesc> &d) {
   if (mmax <= 0) return;
   const int mp = (mmax + 1) & ~1;
   const size_t smem = sizeof(double) * (2 * mp * (mp + 1) + 3 * (mp / 2)) + sizeof(int) * mp;
-  static bool attr = false;
-  if (!attr) {
-    TCTL_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   100 * 1024));
-    attr = true;
-  }
+  // set once per process, thread-safely (function-local static initialisation)
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  TCTL_CUDA(attr);
   size_t mk = c.ws.mark();
   EigDesc *dd = static_cast<EigDesc *>(c.ws.alloc(sizeof(EigDesc) * d.size()));
   TCTL_CUDA(cudaMemcpyAsync(dd, d.data(), sizeof(EigDesc) * d.size(), cudaMemcpyHostToDevice, c.st));

@@ -298,14 +298,31 @@ void build_sep(Ctx &c, Sep &D, const std::vector<double> &w, const std::vector<T
   int *td_m = c.ws.i32(D.R);
   to_dev(c, td_t, t.data(), D.R);
   TCTL_CUDA(cudaMemcpyAsync(td_m, lm.data(), sizeof(int) * D.R, cudaMemcpyHostToDevice, c.st));
+  // Factor columns are stored with unit 2-norm and their norms moved into the
+  // weights, w_k E_0k E_1k E_2k unchanged: every term then enters a contraction
+  // at the scale of its contribution (the tensor-core GEMMs bound their error
+  // by row / column maxima, so unbalanced factors would waste their digits).
+  std::vector<double> wn(w);
+  double *nrm = c.ws.dbl(D.R);
+  std::vector<double> nh(D.R);
   for (int l = 0; l < 3; ++l) {
     D.E[l] = c.dmalloc((size_t)n * D.R);
     const int blocks = (int)std::min<long long>(((long long)n * D.R + 255) / 256, 4096);
     LAUNCH(c, factors_kernel, blocks, 256, 0, n, D.R, c.lam[l], td_t, td_m, l, D.E[l]);
+    col_norms(c, n, D.R, D.E[l], n, nrm);
+    to_host(c, nh.data(), nrm, D.R);
+    for (int k = 0; k < D.R; ++k) {
+      if (!(nh[k] > 0.0) || !std::isfinite(nh[k])) nh[k] = 1.0;  // an underflowed column stays
+      wn[k] *= nh[k];
+    }
+    to_dev(c, nrm, nh.data(), D.R);
+    scale_cols(c, n, D.R, D.E[l], n, nrm, true);
     D.B[l] = D.E[l];
     D.rD[l] = D.R;
     D.Z[l] = nullptr;  // identity: no compression
   }
+  D.w_host = wn;
+  to_dev(c, D.w, wn.data(), D.R);
   TCTL_CUDA(cudaStreamSynchronize(c.st));
   c.ws.reset(mk);
 }

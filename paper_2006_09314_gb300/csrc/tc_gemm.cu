@@ -1,0 +1,496 @@
+// FP64-class GEMMs of the rank-structured solver on the 5th-generation tensor
+// cores (tcgen05, TMEM), by splitting both operands into D signed 7-bit digits
+// (the splitting of Ozaki et al.).
+//
+// GB300 executes FP64 at 2 FMA/clk/SM (1.26 TFLOP/s per GPU) but BF16 at
+// ~2.25 PFLOP/s. The contractions of the truncated Hadamard product (the
+// sketches of its mode unfoldings and the projection of its core onto the new
+// bases, Section 3.4 / Appendix 1 steps of Algorithm 1's fun and precond) are
+// GEMMs with K up to n; they are run here as sums of BF16 digit products:
+//   A[m, k] ~ 2^(e_m - 7) sum_p a_p[m, k],   B[k, j] ~ 2^(f_j - 7) sum_q b_q[k, j],
+// with e_m (f_j) the binary exponent bound of row m of A (column j of B),
+// a_p, b_q integers |.| <= 127 scaled by 2^-7p (exact in BF16), and
+//   C[m, j] = 2^(e_m + f_j - 14) sum_{p + q <= D - 1} (a_p b_q)[m, j].
+// The 7D-bit fixed point of each element is truncated; the neglected digit
+// products and the truncation are ~2^-7D of the row / column maxima (D = 6:
+// 42 bits, ~2e-13 relative to max|A_m| max|B_j| K; D = 4: 28 bits).
+// Products go to four TMEM accumulators by digit level L = p + q: levels 0, 1
+// and 2 separately (every partial sum is an integer multiple of 2^-7L below
+// (L + 1) 127^2 KCHUNK 2^-7L, i.e. fewer than 2^24 units for KCHUNK = 256:
+// exact in FP32 whatever the tensor core's accumulation rounding, which was
+// measured to lose low bits), and levels >= 3 together (their FP32 rounding
+// is ~2^-21 x 2^-20 below the result). Every CTA contracts at most 256 k
+// (KCHUNK), and longer K is split across CTAs whose FP64 partial sums a second
+// kernel adds. The FP64 result is formed in the epilogue from the four FP32
+// accumulators.
+//
+// Layout: the digit planes of A (B) are cut once per GEMM by split_kernel into
+// blocks of TM (TN) rows x 16 k per digit in the K-major core-matrix layout
+// (tc_common.cuh), contiguous per (row tile, k slice); the GEMM kernel's
+// producer thread moves a stage (D planes of A and of B) with two bulk copies
+// (cp.async.bulk, completion on an mbarrier), one thread issues the
+// tcgen05.mma of the stage and commits them to the stage's empty barrier, and
+// all eight warps read the accumulators back (tcgen05.ld) in the epilogue.
+// Every wait is bounded; a timeout sets an error flag the host reads.
+#include <algorithm>
+#include <cmath>
+
+#include "tc_common.cuh"
+#include "tctl_internal.cuh"
+
+namespace tctl {
+
+namespace {
+
+using namespace tc;
+
+constexpr int TM = 128, TN = 64, NTHREADS = 256;
+constexpr int KCHUNK = 256;               // contracted indices per CTA (exact levels 0..2)
+constexpr int TMEM_COLS = 256;            // 4 accumulators of TN columns
+constexpr int E_NONFINITE = 1 << 30;      // exponent code of a row / column holding Inf or NaN
+
+__device__ __forceinline__ long long row_off(const TcOpnd &o, int r) {
+  return (long long)(r % o.d) * o.s0 + (long long)(r / o.d) * o.s1;
+}
+
+// Row exponents, stored biased: e_out[item * Rpad + r] = E_BIAS + (smallest e
+// with |X(r, k)| < 2^e for all k); 0 for an all-zero row (the buffer is
+// zeroed first), E_NONFINITE if the row holds Inf/NaN. A block covers 32 rows
+// x RE_K contracted indices and folds its maximum in with atomicMax, so long
+// rows are spread over many blocks. Lanes run along whichever index is
+// contiguous in memory.
+constexpr int E_BIAS = 2000, RE_K = 256;
+
+__device__ __forceinline__ int exp_code(double v) {
+  if (!isfinite(v)) return E_NONFINITE;
+  if (v == 0.0) return 0;
+  int e;
+  frexp(v, &e);
+  return e + E_BIAS;
+}
+
+__global__ void row_exp_kernel(TcOpnd o, int R, int K, int Rpad, int *__restrict__ e_out) {
+  const int item = blockIdx.z;
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * RE_K;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 8 warps
+  const double *base = o.p + (long long)item * o.sb;
+  const int kend = min(K, k0 + RE_K);
+  if (o.sk == 1) {
+    // k contiguous: warp w takes rows r0 + w, r0 + w + 8, ...; lanes along k
+    for (int rr = w; rr < 32; rr += 8) {
+      const int r = r0 + rr;
+      int c = 0;
+      if (r < R) {
+        const double *x = base + row_off(o, r);
+        for (int k = k0 + lane; k < kend; k += 32) c = max(c, exp_code(x[k]));
+      }
+      for (int s = 16; s > 0; s >>= 1) c = max(c, __shfl_xor_sync(0xffffffffu, c, s));
+      if (lane == 0 && r < R && c > 0) atomicMax(&e_out[(long long)item * Rpad + r], c);
+    }
+  } else {
+    // rows contiguous (or strided): lane = row, warp w takes k = k0 + w, k0 + w + 8, ...
+    const int r = r0 + lane;
+    int c = 0;
+    if (r < R) {
+      const double *x = base + row_off(o, r);
+      for (int k = k0 + w; k < kend; k += 8) c = max(c, exp_code(x[(long long)k * o.sk]));
+    }
+    __shared__ int red[8][32];
+    red[w][lane] = c;
+    __syncthreads();
+    if (w == 0) {
+      for (int i = 1; i < 8; ++i) c = max(c, red[i][lane]);
+      if (r < R && c > 0) atomicMax(&e_out[(long long)item * Rpad + r], c);
+    }
+  }
+}
+
+// Digit planes of one (row tile, 16-k slice) block: 2 TR threads, each cuts the
+// D digits of 8 consecutive k of one row (one 16-byte core-matrix row per plane).
+template <int D, int TR>
+__global__ void __launch_bounds__(2 * TR) split_kernel(TcOpnd o, int R, int K, int Rpad, int nks,
+                                                       const int *__restrict__ e_in,
+                                                       __nv_bfloat16 *__restrict__ planes) {
+  const int rt = blockIdx.x, ks = blockIdx.y, item = blockIdx.z;
+  const int t = threadIdx.x;
+  int rl, kh;
+  if (o.sk == 1) {
+    rl = t >> 1;
+    kh = t & 1;
+  } else {
+    rl = t % TR;
+    kh = t / TR;
+  }
+  const int r = rt * TR + rl;
+  const int k0 = ks * BK + kh * 8;
+  const int ec = e_in[(long long)item * Rpad + r];
+  const int e = ec - E_BIAS;
+  uint32_t w[D][4];
+#pragma unroll
+  for (int p = 0; p < D; ++p)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) w[p][h] = 0;
+  if (r < R && ec != 0 && ec != E_NONFINITE) {
+    const double *x = o.p + (long long)item * o.sb + row_off(o, r);
+    const double cap = ldexp(1.0, 7 * D) - 1.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = k0 + i;
+      const double v = (k < K) ? x[(long long)k * o.sk] : 0.0;
+      if (v == 0.0) continue;
+      const uint64_t F = (uint64_t)fmin(ldexp(fabs(v), 7 * D - e), cap);  // 7D-bit fixed point
+      const float sg = v < 0.0 ? -1.0f : 1.0f;
+#pragma unroll
+      for (int p = 0; p < D; ++p) {
+        const int dg = (int)((F >> (7 * (D - 1 - p))) & 127);
+        const __nv_bfloat16 bv = __float2bfloat16_rn(sg * (float)dg * pow2f(-7 * p));
+        w[p][i >> 1] |= (uint32_t)__bfloat16_as_ushort(bv) << (16 * (i & 1));
+      }
+    }
+  }
+  const int Rt = Rpad / TR;
+  __nv_bfloat16 *blk = planes + (((long long)item * Rt + rt) * nks + ks) * D * (TR * BK);
+  const uint32_t off = core_off(rl, kh * 8) / 2;
+#pragma unroll
+  for (int p = 0; p < D; ++p)
+    *reinterpret_cast<uint4 *>(blk + p * (TR * BK) + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+}
+
+struct TcgArgs {
+  int M, N, nks, nchunk, divA, divB, Mt, Nt, Mpad, Npad;
+  const __nv_bfloat16 *pa, *pb;
+  const int *ea, *eb;
+  double alpha, beta;
+  double *C;
+  long long cm0, cm1, cj, cb;
+  int cd;
+  double *part;  // nchunk > 1: FP64 partial sums, [(b * nchunk + ch) * N + j] * M + m
+  int *err;
+};
+
+template <int D, int NST>
+__global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
+  constexpr int PA = TM * BK, PB = TN * BK;          // elements of one digit plane
+  constexpr int A_BYTES = D * PA * 2, B_BYTES = D * PB * 2, STAGE = A_BYTES + B_BYTES;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  uint64_t *empty = reinterpret_cast<uint64_t *>(smem + NST * STAGE);
+  uint64_t *full = empty + NST;
+  uint64_t *done_bar = full + NST;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done_bar + 1);
+  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = blockIdx.x, jt = blockIdx.y;
+  const int b = blockIdx.z / a.nchunk, ch = blockIdx.z % a.nchunk;
+  const int ia = b / a.divA, ib = b / a.divB;
+  const int ks0 = ch * (KCHUNK / BK);
+  const int nst = min(a.nks, ks0 + KCHUNK / BK) - ks0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(1));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done_bar)), "r"(1));
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 0 && lane == 0) {
+    // producer: one bulk copy of the A digit block and one of the B block per stage
+    const __nv_bfloat16 *asrc = a.pa + (((long long)ia * a.Mt + mt) * a.nks + ks0) * D * PA;
+    const __nv_bfloat16 *bsrc = a.pb + (((long long)ib * a.Nt + jt) * a.nks + ks0) * D * PB;
+    for (int s = 0; s < nst; ++s) {
+      const int st = s % NST;
+      if (s >= NST) {
+        if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)(((s - NST) / NST) & 1))) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+      }
+      const uint32_t bar = smem_u32(&full[st]);
+      const uint32_t dst = smem_u32(smem + st * STAGE);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGE));
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+              "r"(dst),
+          "l"(asrc + (long long)s * D * PA), "r"(A_BYTES), "r"(bar)
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+              "r"(dst + A_BYTES),
+          "l"(bsrc + (long long)s * D * PB), "r"(B_BYTES), "r"(bar)
+          : "memory");
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: kind::f16, BF16 x BF16 -> FP32, M = 128, N = 64
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+    for (int s = 0; s < nst; ++s) {
+      const int st = s % NST;
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((s / NST) & 1))) {
+        atomicExch(abort_flag, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ab = smem_u32(smem + st * STAGE), bb = ab + A_BYTES;
+#pragma unroll
+      for (int p = 0; p < D; ++p) {
+#pragma unroll
+        for (int q = 0; q < D - p; ++q) {
+          const uint64_t ad = smem_desc(ab + p * PA * 2);
+          const uint64_t bd = smem_desc(bb + q * PB * 2);
+          const int lvl = p + q < 3 ? p + q : 3;
+          const uint32_t dst = tmem + (uint32_t)(TN * lvl);
+          // the first product into each accumulator overwrites it
+          const bool first = (s == 0) && (p == 0) && (q <= 3);
+          const uint32_t acc = first ? 0u : 1u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&empty[st])));
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(done_bar)));
+  }
+  const bool fin = mbar_wait(smem_u32(done_bar), 0u);
+  const bool ok = (__syncthreads_and(fin ? 1 : 0) != 0) && (*abort_flag == 0) && nst > 0;
+  if (!ok && nst > 0 && tid == 0) atomicExch(a.err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // warp w: TMEM lanes 32 (w % 4) .. +31 (rows), columns 32 (w / 4) .. +31, 16 at a time
+    const int row = (warp & 3) * 32 + lane;
+    const int m = mt * TM + row;
+    const int ec = a.ea[(long long)ia * a.Mpad + min(m, a.Mpad - 1)];
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      const int cb = (warp >> 2) * 32 + half * 16;
+      uint32_t h0[16], h1[16], h2[16], h3[16];
+      const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb;
+#define TCTL_LD16(dst, addr)                                                                     \
+  asm volatile(                                                                                  \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"   \
+      "%14,%15}, [%16];"                                                                         \
+      : "=r"(dst[0]), "=r"(dst[1]), "=r"(dst[2]), "=r"(dst[3]), "=r"(dst[4]), "=r"(dst[5]),      \
+        "=r"(dst[6]), "=r"(dst[7]), "=r"(dst[8]), "=r"(dst[9]), "=r"(dst[10]), "=r"(dst[11]),    \
+        "=r"(dst[12]), "=r"(dst[13]), "=r"(dst[14]), "=r"(dst[15])                              \
+      : "r"(addr))
+      TCTL_LD16(h0, t0);
+      TCTL_LD16(h1, t0 + TN);
+      TCTL_LD16(h2, t0 + 2 * TN);
+      TCTL_LD16(h3, t0 + 3 * TN);
+#undef TCTL_LD16
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (m < a.M) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int j = jt * TN + cb + i;
+          if (j >= a.N) break;
+          const int fc = a.eb[(long long)ib * a.Npad + j];
+          double v;
+          if (ec == E_NONFINITE || fc == E_NONFINITE) v = __longlong_as_double(0x7FF8000000000000ll);
+          else if (ec == 0 || fc == 0) v = 0.0;
+          else
+            v = ldexp(((double)__uint_as_float(h0[i]) + (double)__uint_as_float(h1[i])) +
+                          ((double)__uint_as_float(h2[i]) + (double)__uint_as_float(h3[i])),
+                      ec + fc - 2 * E_BIAS - 14);
+          if (a.nchunk == 1) {
+            double *out = a.C + (long long)b * a.cb + (long long)(m % a.cd) * a.cm0 +
+                          (long long)(m / a.cd) * a.cm1 + (long long)j * a.cj;
+            *out = (a.beta == 0.0) ? a.alpha * v : fma(a.alpha, v, a.beta * *out);
+          } else {
+            a.part[((long long)(b * a.nchunk + ch) * a.N + j) * a.M + m] = v;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+__global__ void tcg_reduce_kernel(int M, int N, int batch, int nchunk, const double *__restrict__ part,
+                                  double alpha, double beta, double *C, long long cm0, long long cm1,
+                                  int cd, long long cj, long long cb) {
+  const long long total = (long long)M * N * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(t % M);
+    const int j = (int)((t / M) % N);
+    const int b = (int)(t / ((long long)M * N));
+    double s = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) s += part[((long long)(b * nchunk + ch) * N + j) * M + m];
+    double *out = C + (long long)b * cb + (long long)(m % cd) * cm0 + (long long)(m / cd) * cm1 +
+                  (long long)j * cj;
+    *out = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *out);
+  }
+}
+
+template <int D, int NST>
+constexpr int tcg_smem() {
+  return NST * D * (TM + TN) * BK * 2 + 2048;
+}
+
+template <int D, int TR>
+void split_operand(Ctx &c, const TcOpnd &o, int R, int K, int items, int Rpad, int nks, int *e,
+                   __nv_bfloat16 *planes) {
+  TCTL_CUDA(cudaMemsetAsync(e, 0, sizeof(int) * (size_t)items * Rpad, c.st));
+  dim3 ge((R + 31) / 32, (K + RE_K - 1) / RE_K, items);
+  LAUNCH(c, row_exp_kernel, ge, 256, 0, o, R, K, Rpad, e);
+  dim3 g(Rpad / TR, nks, items);
+  LAUNCH(c, (split_kernel<D, TR>), g, 2 * TR, 0, o, R, K, Rpad, nks, e, planes);
+}
+
+template <int D, int NST>
+void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double alpha,
+             const TcOpnd &A, const TcOpnd &B, double beta, double *C, long long cm0, long long cm1,
+             int cd, long long cj, long long cb) {
+  const int Mt = (M + TM - 1) / TM, Nt = (N + TN - 1) / TN;
+  const int Mpad = Mt * TM, Npad = Nt * TN;
+  const int nks = (K + BK - 1) / BK;
+  const int nchunk = (nks * BK + KCHUNK - 1) / KCHUNK;
+  const int itemsA = (batch - 1) / divA + 1, itemsB = (batch - 1) / divB + 1;
+  size_t mk = c.ws.mark();
+  int *ea = c.ws.i32((size_t)itemsA * Mpad);
+  int *eb = c.ws.i32((size_t)itemsB * Npad);
+  auto *pa = reinterpret_cast<__nv_bfloat16 *>(
+      c.ws.dbl(((size_t)itemsA * Mt * nks * D * TM * BK * 2 + 7) / 8));
+  auto *pb = reinterpret_cast<__nv_bfloat16 *>(
+      c.ws.dbl(((size_t)itemsB * Nt * nks * D * TN * BK * 2 + 7) / 8));
+  double *part = nchunk > 1 ? c.ws.dbl((size_t)batch * nchunk * M * N) : nullptr;
+  if (!c.tcg_err) {
+    c.tcg_err = reinterpret_cast<int *>(c.dmalloc(1));
+    TCTL_CUDA(cudaMemsetAsync(c.tcg_err, 0, sizeof(int), c.st));
+  }
+  // the attribute belongs to the function; a function-local static is set once, thread-safely
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      tcg_kernel<D, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg_smem<D, NST>());
+  TCTL_CUDA(attr);
+  split_operand<D, TM>(c, A, M, K, itemsA, Mpad, nks, ea, pa);
+  split_operand<D, TN>(c, B, N, K, itemsB, Npad, nks, eb, pb);
+  TcgArgs ar;
+  ar.M = M;
+  ar.N = N;
+  ar.nks = nks;
+  ar.nchunk = nchunk;
+  ar.divA = divA;
+  ar.divB = divB;
+  ar.Mt = Mt;
+  ar.Nt = Nt;
+  ar.Mpad = Mpad;
+  ar.Npad = Npad;
+  ar.pa = pa;
+  ar.pb = pb;
+  ar.ea = ea;
+  ar.eb = eb;
+  ar.alpha = alpha;
+  ar.beta = beta;
+  ar.C = C;
+  ar.cm0 = cm0;
+  ar.cm1 = cm1;
+  ar.cj = cj;
+  ar.cb = cb;
+  ar.cd = cd;
+  ar.part = part;
+  ar.err = c.tcg_err;
+  dim3 grid(Mt, Nt, batch * nchunk);
+  c.next_flops = 2.0 * M * (double)N * K * batch;
+  constexpr int smem_bytes = tcg_smem<D, NST>();
+  LAUNCH(c, (tcg_kernel<D, NST>), grid, NTHREADS, smem_bytes, ar);
+  if (nchunk > 1) {
+    const long long total = (long long)M * N * batch;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    LAUNCH(c, tcg_reduce_kernel, blocks, 256, 0, M, N, batch, nchunk, part, alpha, beta, C, cm0, cm1,
+           cd, cj, cb);
+  }
+  c.ws.reset(mk);
+}
+
+}  // namespace
+
+bool gemm_tc_fits(int M, int N, int K, int batch) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return false;
+  const int Mt = (M + TM - 1) / TM, Nt = (N + TN - 1) / TN, nks = (K + BK - 1) / BK;
+  const int nchunk = (nks * BK + KCHUNK - 1) / KCHUNK;
+  if (Nt > 65535 || (long long)batch * nchunk > 65535 || Mt > 65535) return false;
+  // enough work to pay for the digit split, and tiles not mostly padding
+  const double flops = 2.0 * M * (double)N * K * batch;
+  const double padded = (double)Mt * TM * Nt * TN * nks * BK;
+  return flops >= 2e7 && padded <= 4.0 * M * (double)N * K;
+}
+
+void gemm_tc(Ctx &c, int digits, int M, int N, int K, int batch, int divA, int divB, double alpha,
+             const TcOpnd &A, const TcOpnd &B, double beta, double *C, long long cm0, long long cm1,
+             int cd, long long cj, long long cb) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (K <= 0) fail(TCTL_E_ARG, "gemm_tc: K must be positive");
+  static_assert(TMEM_COLS >= 4 * TN, "four accumulators");
+  if (digits <= 4)
+    run_tcg<4, 4>(c, M, N, K, batch, divA, divB, alpha, A, B, beta, C, cm0, cm1, cd, cj, cb);
+  else
+    run_tcg<6, 3>(c, M, N, K, batch, divA, divB, alpha, A, B, beta, C, cm0, cm1, cd, cj, cb);
+}
+
+void gemm_x(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double alpha, const double *A,
+            int lda, long long sA, const double *B, int ldb, long long sB, double beta, double *C,
+            int ldc, long long sC, int batch, int divA, int divB) {
+  const bool use = digits > 0 && c.o.tc_gemm != 0;
+  // a batch that reuses one operand (stride 0) splits it once
+  if (sA == 0) divA = batch;
+  if (sB == 0) divB = batch;
+  // the larger of m, n goes to the 128-row side of the tile
+  const bool swap = n > m;
+  const int M = swap ? n : m, N = swap ? m : n;
+  if (!use || !gemm_tc_fits(M, N, k, batch)) {
+    gemm(c, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, divA, divB);
+    return;
+  }
+  // op(A)(i, kk) = ta ? A[kk + i lda] : A[i + kk lda];  op(B)(kk, j) = tb ? B[j + kk ldb] : B[kk + j ldb]
+  TcOpnd opA{A, ta ? (long long)lda : 1ll, 0ll, ta ? 1ll : (long long)lda, sA, 1 << 30};
+  TcOpnd opB{B, tb ? 1ll : (long long)ldb, 0ll, tb ? (long long)ldb : 1ll, sB, 1 << 30};
+  if (!swap)
+    gemm_tc(c, digits, m, n, k, batch, divA, divB, alpha, opA, opB, beta, C, 1, 0, 1 << 30, ldc, sC);
+  else  // C^T = op(B)^T op(A)^T: rows j of op(B) become the 128-row operand
+    gemm_tc(c, digits, n, m, k, batch, divB, divA, alpha, opB, opA, beta, C, ldc, 0, 1 << 30, 1, sC);
+}
+
+void gemm_tc_cm(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double alpha,
+                const double *A, int lda, const double *B, int ldb, double beta, double *C, int ldc) {
+  if (m <= 0 || n <= 0) return;
+  if (k <= 0) fail(TCTL_E_ARG, "k must be positive");
+  if ((m + TM - 1) / TM > 65535 || (n + TN - 1) / TN > 65535)
+    fail(TCTL_E_ARG, "matrix too large for one tensor-core GEMM launch");
+  const TcOpnd opA{A, ta ? (long long)lda : 1ll, 0ll, ta ? 1ll : (long long)lda, 0, 1 << 30};
+  const TcOpnd opB{B, tb ? 1ll : (long long)ldb, 0ll, tb ? (long long)ldb : 1ll, 0, 1 << 30};
+  gemm_tc(c, digits, m, n, k, 1, 1, 1, alpha, opA, opB, beta, C, 1, 0, 1 << 30, ldc, 0);
+}
+
+void tcg_check(Ctx &c) {
+  if (!c.tcg_err) return;
+  int herr = 0;
+  TCTL_CUDA(cudaMemcpyAsync(&herr, c.tcg_err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  TCTL_CUDA(cudaStreamSynchronize(c.st));
+  if (herr) {
+    TCTL_CUDA(cudaMemsetAsync(c.tcg_err, 0, sizeof(int), c.st));
+    fail(TCTL_E_NUMERIC, "tensor-core GEMM: bounded mbarrier wait timed out");
+  }
+}
+
+}  // namespace tctl

@@ -100,6 +100,7 @@ struct Ctx {
   long long launches = 0;
   uint64_t rng_counter = 0;
   std::vector<void *> owned;         // device allocations freed at destroy
+  int *tcg_err = nullptr;            // tensor-core GEMM wait-timeout flag (device)
   bool prof = false;                 // record events around every launch
   bool trace = false;                // TCTL_TRACE=1: per-step ranks on stderr
   bool prof_phases = false;          // report "phase/kernel" names
@@ -151,6 +152,32 @@ struct PhaseScope {
   ::tctl::PhaseScope TCTL_CAT(tctl_phase_scope_, __LINE__)(ctx, &::tctl::Ctx::phase, name)
 #define TCTL_OUTER(ctx, name) \
   ::tctl::PhaseScope TCTL_CAT(tctl_outer_scope_, __LINE__)(ctx, &::tctl::Ctx::outer, name)
+
+// ------------------------------------------------------------ tc_gemm.cu
+// Operand of the digit-split tensor-core GEMM: rows r (m of A, j of B),
+// contracted index k, batch item i; element at
+// p + i sb + (r % d) s0 + (r / d) s1 + k sk.
+struct TcOpnd {
+  const double *p;
+  long long s0, s1, sk, sb;
+  int d;
+};
+// C[b sC' + (m % cd) cm0 + (m / cd) cm1 + j cj] = alpha sum_k A(m, k) B(j, k) + beta C,
+// batch item b of A / B = b / divA, b / divB; digits 4 (28-bit) or 6 (42-bit).
+void gemm_tc(Ctx &c, int digits, int M, int N, int K, int batch, int divA, int divB,
+             double alpha, const TcOpnd &A, const TcOpnd &B, double beta, double *C,
+             long long cm0, long long cm1, int cd, long long cj, long long cb);
+bool gemm_tc_fits(int M, int N, int K, int batch);
+// gemm() semantics; the tensor cores when opts.tc_gemm and the shape pays, FP64 otherwise
+void gemm_x(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double alpha,
+            const double *A, int lda, long long sA, const double *B, int ldb, long long sB,
+            double beta, double *C, int ldc, long long sC, int batch = 1, int divA = 1,
+            int divB = 1);
+// Column-major C = alpha op(A) op(B) + beta C on the tensor cores whatever the shape.
+void gemm_tc_cm(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double alpha,
+                const double *A, int lda, const double *B, int ldb, double beta, double *C, int ldc);
+// Raises TCTL_E_NUMERIC if a tensor-core GEMM timed out on a wait (synchronizes).
+void tcg_check(Ctx &c);
 
 // ------------------------------------------------------------ linalg.cu
 // C = alpha op(A) op(B) + beta C, column-major, batched with element strides;

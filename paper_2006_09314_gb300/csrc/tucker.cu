@@ -31,6 +31,9 @@ namespace tctl {
 namespace {
 
 constexpr int kMaxRank = 64;
+// digits of the tensor-core GEMMs (42 bits: the sketches must resolve directions
+// down to the range tolerance, and the core feeds the eps truncation)
+constexpr int kDigits = 6;
 
 __global__ void permute3_kernel(int r0, int r1, int r2, const double *__restrict__ in, int p0,
                                 int p1, int p2, double *__restrict__ out) {
@@ -450,12 +453,14 @@ static double *sketch_factor(Ctx &c, const Sep &D, const Tucker &x, int m, int l
   khatri_rao(c, n, x.Q[m], n, rm, Om, n, ls, KRm, n);
   if (D.Z[m]) {
     double *T = c.ws.dbl((size_t)rm * ls * D.rD[m]);
-    gemm(c, true, false, rm * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, T, rm * ls, 0);
-    gemm(c, false, false, rm * ls, R, D.rD[m], 1.0, T, rm * ls, 0, D.Z[m], D.rD[m], 0, 0.0, P,
-         rm * ls, 0);
+    gemm_x(c, kDigits, true, false, rm * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, T,
+           rm * ls, 0);
+    gemm_x(c, kDigits, false, false, rm * ls, R, D.rD[m], 1.0, T, rm * ls, 0, D.Z[m], D.rD[m], 0,
+           0.0, P, rm * ls, 0);
   } else {
     // uncompressed operator: B_m holds the R factor columns themselves
-    gemm(c, true, false, rm * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, P, rm * ls, 0);
+    gemm_x(c, kDigits, true, false, rm * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, P,
+           rm * ls, 0);
   }
   c.ws.reset(mk);
   return P;
@@ -480,15 +485,15 @@ static void sketch_mode(Ctx &c, const Sep &D, const Tucker &x, const double *Cl,
   double *v = c.ws.dbl((size_t)r[l] * ls * kc);
   for (int k0 = 0; k0 < R; k0 += kc) {
     const int nk = std::min(kc, R - k0);
-    gemm(c, false, false, r[l] * r[m1], ls * nk, r[m2], 1.0, Cl, r[l] * r[m1], 0,
-         P[m2] + (size_t)r[m2] * ls * k0, r[m2], 0, 0.0, F, r[l] * r[m1], 0);
+    gemm_x(c, kDigits, false, false, r[l] * r[m1], ls * nk, r[m2], 1.0, Cl, r[l] * r[m1], 0,
+           P[m2] + (size_t)r[m2] * ls * k0, r[m2], 0, 0.0, F, r[l] * r[m1], 0);
     const long long tot = (long long)r[l] * ls * nk;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
     LAUNCH(c, contract_b_kernel, blocks, 256, 0, r[l], r[m1], ls, nk, F,
            P[m1] + (size_t)r[m1] * ls * k0, D.w + k0, v);
     if (D.Z[l]) {
-      gemm(c, false, true, r[l] * ls, D.rD[l], nk, 1.0, v, r[l] * ls, 0,
-           D.Z[l] + (size_t)D.rD[l] * k0, D.rD[l], 0, k0 == 0 ? 0.0 : 1.0, uT, r[l] * ls, 0);
+      gemm_x(c, kDigits, false, true, r[l] * ls, D.rD[l], nk, 1.0, v, r[l] * ls, 0,
+             D.Z[l] + (size_t)D.rD[l] * k0, D.rD[l], 0, k0 == 0 ? 0.0 : 1.0, uT, r[l] * ls, 0);
     } else {
       copy_d(c, uT + (size_t)r[l] * ls * k0, v, (size_t)r[l] * ls * nk);
     }
@@ -505,18 +510,34 @@ static void sketch_mode(Ctx &c, const Sep &D, const Tucker &x, const double *Cl,
   for (int p0 = 0; p0 < D.rD[l]; p0 += pc) {
     const int np_ = std::min(pc, D.rD[l] - p0);
     khatri_rao(c, n, x.Q[l], n, r[l], D.B[l] + (size_t)n * p0, n, np_, KRl, n);
-    gemm(c, false, false, n, ls, r[l] * np_, 1.0, KRl, n, 0, U2 + (size_t)r[l] * p0, r[l] * D.rD[l],
-         0, p0 == 0 ? 0.0 : 1.0, Y, n, 0);
+    gemm_x(c, kDigits, false, false, n, ls, r[l] * np_, 1.0, KRl, n, 0, U2 + (size_t)r[l] * p0,
+           r[l] * D.rD[l], 0, p0 == 0 ? 0.0 : 1.0, Y, n, 0);
   }
   c.ws.reset(mk);
 }
 
-void sep_apply_trunc(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, double eps) {
+void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double eps) {
   const int n = c.n;
   if (tucker_empty(x)) {
     y.r[0] = y.r[1] = y.r[2] = 0;
     return;
   }
+  // The tensor-core contractions use the factor matrices E_l themselves: their
+  // error is relative to the row / column maxima of the operands, and the
+  // compressed form E_l = B_l Z_l recombines basis coefficients with
+  // cancellation (entries of E_l span many orders of magnitude across i), which
+  // would amplify that error. FP64 uses the compressed basis (rD_l < R columns).
+  Sep Du;
+  if (c.o.tc_gemm) {
+    Du.R = Dc.R;
+    Du.w = Dc.w;
+    for (int l = 0; l < 3; ++l) {
+      Du.E[l] = Du.B[l] = Dc.E[l];
+      Du.rD[l] = Dc.R;
+      Du.Z[l] = nullptr;
+    }
+  }
+  const Sep &D = c.o.tc_gemm ? Du : Dc;
   const int R = D.R;
   size_t mk = c.ws.mark();
   const int r[3] = {x.r[0], x.r[1], x.r[2]};
@@ -568,12 +589,12 @@ void sep_apply_trunc(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, double ep
     double *KR = c.ws.dbl((size_t)n * rn[l] * r[l]);
     khatri_rao(c, n, Qn[l], n, rn[l], x.Q[l], n, r[l], KR, n);
     double *N = c.ws.dbl((size_t)rn[l] * r[l] * D.rD[l]);
-    gemm(c, true, false, rn[l] * r[l], D.rD[l], n, 1.0, KR, n, 0, D.B[l], n, 0, 0.0, N,
-         rn[l] * r[l], 0);
+    gemm_x(c, kDigits, true, false, rn[l] * r[l], D.rD[l], n, 1.0, KR, n, 0, D.B[l], n, 0, 0.0, N,
+           rn[l] * r[l], 0);
     if (D.Z[l]) {
       M[l] = c.ws.dbl((size_t)rn[l] * r[l] * R);
-      gemm(c, false, false, rn[l] * r[l], R, D.rD[l], 1.0, N, rn[l] * r[l], 0, D.Z[l], D.rD[l], 0,
-           0.0, M[l], rn[l] * r[l], 0);
+      gemm_x(c, kDigits, false, false, rn[l] * r[l], R, D.rD[l], 1.0, N, rn[l] * r[l], 0, D.Z[l],
+             D.rD[l], 0, 0.0, M[l], rn[l] * r[l], 0);
     } else {
       M[l] = N;
     }
@@ -591,16 +612,27 @@ void sep_apply_trunc(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, double ep
     for (int k0 = 0; k0 < R; k0 += kc) {
       const int nk = std::min(kc, R - k0);
       // T1[k] = M_0k (rn0 x r0) * core (r0 x r1 r2)
-      gemm(c, false, false, rn[0], r[1] * r[2], r[0], 1.0, M[0] + (size_t)rn[0] * r[0] * k0, rn[0],
-           (long long)rn[0] * r[0], x.core, r[0], 0, 0.0, T1, rn[0], s1, nk);
+      gemm_x(c, kDigits, false, false, rn[0], r[1] * r[2], r[0], 1.0,
+             M[0] + (size_t)rn[0] * r[0] * k0, rn[0], (long long)rn[0] * r[0], x.core, r[0], 0, 0.0,
+             T1, rn[0], s1, nk);
       // T2[k] = T1[k] (rn0 r1 x r2) * M_2k^T (r2 x rn2)
-      gemm(c, false, true, rn[0] * r[1], rn[2], r[2], 1.0, T1, rn[0] * r[1], s1,
-           M[2] + (size_t)rn[2] * r[2] * k0, rn[2], (long long)rn[2] * r[2], 0.0, T2, rn[0] * r[1],
-           s2, nk);
-      // T3[k][:,:,c] = T2[k][:,:,c] (rn0 x r1) * M_1k^T (r1 x rn1), batch over (k, c)
-      gemm(c, false, true, rn[0], rn[1], r[1], 1.0, T2, rn[0], (long long)rn[0] * r[1],
-           M[1] + (size_t)rn[1] * r[1] * k0, rn[1], (long long)rn[1] * r[1], 0.0, T3, rn[0],
-           (long long)rn[0] * rn[1], nk * rn[2], 1, rn[2]);
+      gemm_x(c, kDigits, false, true, rn[0] * r[1], rn[2], r[2], 1.0, T1, rn[0] * r[1], s1,
+             M[2] + (size_t)rn[2] * r[2] * k0, rn[2], (long long)rn[2] * r[2], 0.0, T2, rn[0] * r[1],
+             s2, nk);
+      // T3[k](a, b', c') = sum_b T2[k](a, b, c') M_1k(b', b)
+      if (c.o.tc_gemm && gemm_tc_fits(rn[0] * rn[2], rn[1], r[1], nk)) {
+        // one GEMM per k with rows (a, c'): T2[k] (rn0 rn2 x r1) * M_1k^T
+        const TcOpnd A{T2, 1, (long long)rn[0] * r[1], (long long)rn[0], s2, rn[0]};
+        const TcOpnd B{M[1] + (size_t)rn[1] * r[1] * k0, 1, 0, (long long)rn[1],
+                       (long long)rn[1] * r[1], 1 << 30};
+        gemm_tc(c, kDigits, rn[0] * rn[2], rn[1], r[1], nk, 1, 1, 1.0, A, B, 0.0, T3, 1,
+                (long long)rn[0] * rn[1], rn[0], rn[0], s3);
+      } else {
+        // batch over (k, c'): T2[k][:,:,c'] (rn0 x r1) * M_1k^T (r1 x rn1)
+        gemm(c, false, true, rn[0], rn[1], r[1], 1.0, T2, rn[0], (long long)rn[0] * r[1],
+             M[1] + (size_t)rn[1] * r[1] * k0, rn[1], (long long)rn[1] * r[1], 0.0, T3, rn[0],
+             (long long)rn[0] * rn[1], nk * rn[2], 1, rn[2]);
+      }
       // nc += T3 w
       gemm(c, false, false, (int)szo, 1, nk, 1.0, T3, (int)szo, 0, D.w + k0, nk, 0,
            k0 == 0 ? 0.0 : 1.0, nc, (int)szo, 0);

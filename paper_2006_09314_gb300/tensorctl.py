@@ -35,7 +35,7 @@ EXPORTED = [
     "tctl_solve_host", "tctl_cp_alloc", "tctl_cp_free", "tctl_get_eigs",
     "tctl_get_stats", "tctl_launch_count", "tctl_destroy", "tctl_last_error",
     "tctl_profile_enable", "tctl_profile_report", "tctl_eig1d_noalloc", "tctl_get_expsum",
-    "tctl_expsum_fit",
+    "tctl_expsum_fit", "tctl_gemm",
 ]
 
 ERRORS = {0: "OK", -1: "E_ARG", -2: "E_COEFF", -3: "E_CUDA", -4: "E_NOMEM",
@@ -59,7 +59,8 @@ class Opts(ctypes.Structure):
                 ("rank_cap", ctypes.c_int), ("precision", ctypes.c_int),
                 ("basis", ctypes.c_int), ("expsum_src", ctypes.c_int),
                 ("paper_end_rows", ctypes.c_int), ("eps_final", ctypes.c_double),
-                ("seed", ctypes.c_ulonglong), ("range_tol", ctypes.c_double)]
+                ("seed", ctypes.c_ulonglong), ("range_tol", ctypes.c_double),
+                ("tc_gemm", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -120,6 +121,7 @@ def load(build_if_missing: bool = True):
         "tctl_eig1d_noalloc": (I, [P, I, I, P, P, P]),
         "tctl_get_expsum": (I, [P, I, P, P, P, I, P]),
         "tctl_expsum_fit": (I, [D, D, D, D, D, P, P, I, P, P]),
+        "tctl_gemm": (I, [P, I, I, I, I, I, I, D, P, I, P, I, D, P, I]),
         "tctl_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -297,6 +299,28 @@ def tctl_launch_count(ctx):
     return int(load().tctl_launch_count(ctx))
 
 
+def tctl_gemm(ctx, digits, A, B, C=None, trans_a=False, trans_b=False, alpha=1.0, beta=0.0):
+    """C = alpha op(A) op(B) + beta C on CUDA float64 tensors (row-major torch views).
+
+    torch tensors are row-major, the library column-major: a row-major X is the
+    column-major X^T, so C^T = op(B)^T op(A)^T is computed with swapped roles.
+    """
+    import torch
+    for t in (A, B):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("A, B must be contiguous CUDA float64 tensors")
+    m = A.shape[1] if trans_a else A.shape[0]
+    k = A.shape[0] if trans_a else A.shape[1]
+    n = B.shape[0] if trans_b else B.shape[1]
+    if C is None:
+        C = torch.zeros(m, n, dtype=torch.float64, device=A.device)
+    # column-major view: C^T (n x m, ld n) = op(B)^T (n x k) op(A)^T (k x m)
+    _check(load().tctl_gemm(ctx, digits, 1 if trans_b else 0, 1 if trans_a else 0, n, m, k, alpha,
+                            B.data_ptr(), B.shape[1], A.data_ptr(), A.shape[1], beta,
+                            C.data_ptr(), n), ctx)
+    return C
+
+
 def tctl_expsum_fit(alpha, beta, s_min, s_max, tol, cap=256):
     """Fitted exp-sum of F2(s)/s on [s_min, s_max] (host only): (t, w, err)."""
     import numpy as np
@@ -408,6 +432,9 @@ class Context:
 
     def launch_count(self):
         return tctl_launch_count(self.handle)
+
+    def gemm(self, digits, A, B, C=None, trans_a=False, trans_b=False, alpha=1.0, beta=0.0):
+        return tctl_gemm(self.handle, digits, A, B, C, trans_a, trans_b, alpha, beta)
 
     def expsum(self, which=0):
         return tctl_get_expsum(self.handle, which)

@@ -246,6 +246,23 @@ def test_pcg_matches_exact(n, alpha, beta):
     assert err <= 1e-5, (err, st)
 
 
+def test_pcg_fp64_and_tensor_core_contractions_agree():
+    """tc_gemm = 1 (digit-split tensor-core contractions, default) vs 0 (FP64 FMA)."""
+    n, alpha, beta = 48, 0.5, 1e-2
+    pr = make_problem(n, alpha, beta, 3, 77)
+    lams, Vs = _oracle_eigs(pr)
+    ustar = fg.solve_exact(F.cp_full(pr.yw, pr.yU), lams, Vs, alpha, beta)
+    out = []
+    for tc in (0, 1):
+        with T.Context(pr.coeffs, n, alpha, beta, 1e-6, opts=T.tctl_default_opts(tc_gemm=tc)) as ctx:
+            x, st, _ = ctx.pcg_solve(T.CP.from_numpy(pr.yw, pr.yU))
+            out.append(_full_from_gpu(x))
+    nrm = np.linalg.norm(ustar)
+    for u in out:
+        assert np.linalg.norm(u - ustar) <= 1e-5 * nrm
+    assert np.linalg.norm(out[0] - out[1]) <= 2e-6 * nrm
+
+
 def test_pcg_paper_form_basis0_agrees():
     e1, s1, _ = _pcg_case(30, 0.5, 1e-2, 3, 11, basis=1)
     e0, s0, _ = _pcg_case(30, 0.5, 1e-2, 3, 11, basis=0)

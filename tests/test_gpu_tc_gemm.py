@@ -1,0 +1,88 @@
+"""GPU parity of the digit-split tensor-core GEMM (tctl_gemm) against FP64 numpy.
+
+The split represents each entry of op(A) (op(B)) by d signed 7-bit digits
+below one binary exponent per row (column); the error of an entry of C is
+bounded by about 2^-7d * K * max_k |A(i, k)| * max_k |B(k, j)| (truncation of
+both operands plus the dropped digit products; the accumulation is exact in
+the leading levels). Integers that fit the digits are exact.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # the marker deselects these on CPU hosts
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2006_09314_gb300 import tensorctl as T  # noqa: E402
+from paper_2006_09314_gb300.inputs import make_problem  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    pr = make_problem(16, 0.5, 1e-2, 1, 1)
+    c = T.Context(pr.coeffs, 16, 0.5, 1e-2, 1e-6)
+    yield c
+    c.close()
+
+
+def _bound(A, B, digits, ta, tb):
+    opA = A.T if ta else A
+    opB = B.T if tb else B
+    K = opA.shape[1]
+    return 8.0 * 2.0 ** (-7 * digits) * K * np.abs(opA).max(1)[:, None] * np.abs(opB).max(0)[None, :]
+
+
+@pytest.mark.parametrize("m,n,k,ta,tb", [(300, 77, 1000, False, False), (129, 65, 16, True, False),
+                                         (64, 200, 2048, False, True), (1, 1, 5, True, True),
+                                         (513, 33, 511, False, False), (40, 700, 37, True, True)])
+@pytest.mark.parametrize("digits", [4, 6])
+def test_tc_gemm_error_bound(ctx, m, n, k, ta, tb, digits):
+    rng = np.random.default_rng(m * 7 + n * 3 + k)
+    A = rng.standard_normal((k, m) if ta else (m, k)) * np.exp(rng.uniform(-8, 8, (k, 1) if ta else (m, 1)))
+    B = rng.standard_normal((n, k) if tb else (k, n)) * np.exp(rng.uniform(-8, 8, (1, k) if tb else (1, n)))
+    ref = (A.T if ta else A) @ (B.T if tb else B)
+    C = ctx.gemm(digits, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), trans_a=ta, trans_b=tb)
+    err = np.abs(C.cpu().numpy() - ref)
+    assert np.all(err <= _bound(A, B, digits, ta, tb))
+
+
+def test_tc_gemm_integers_exact_alpha_beta(ctx):
+    rng = np.random.default_rng(3)
+    A = rng.integers(-1000, 1001, (257, 700)).astype(np.float64)
+    B = rng.integers(-1000, 1001, (700, 130)).astype(np.float64)
+    C0 = rng.integers(-5, 6, (257, 130)).astype(np.float64)
+    Ct = torch.from_numpy(C0.copy()).cuda()
+    ctx.gemm(6, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=Ct, alpha=2.0, beta=-0.5)
+    assert np.array_equal(Ct.cpu().numpy(), 2.0 * (A @ B) - 0.5 * C0)
+
+
+def test_tc_gemm_zero_rows_and_nan(ctx):
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((200, 300))
+    B = rng.standard_normal((300, 90))
+    A[5] = 0.0
+    B[:, 7] = 0.0
+    A[9, 17] = np.nan
+    C = ctx.gemm(6, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    assert np.all(C[5] == 0.0) and np.all(C[:, 7][np.arange(200) != 9] == 0.0)
+    assert np.all(np.isnan(C[9]))
+    ok = np.ones(200, bool)
+    ok[9] = False
+    ref = A[ok] @ B
+    assert np.all(np.abs(C[ok] - ref) <= _bound(A[ok], B, 6, False, False))
+
+
+def test_fp64_path_digits0(ctx):
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((70, 50))
+    B = rng.standard_normal((50, 30))
+    C = ctx.gemm(0, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    assert np.allclose(C, A @ B, rtol=0, atol=1e-13 * np.abs(A).max() * np.abs(B).max() * 50)
+
+
+def test_tc_gemm_argument_errors(ctx):
+    lib = T.load()
+    assert lib.tctl_gemm(ctx.handle, 5, 0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4) == -1
+    assert lib.tctl_gemm(ctx.handle, 6, 0, 0, 4, 4, 4, 1.0, None, 2, None, 4, 0.0, None, 4) == -1
