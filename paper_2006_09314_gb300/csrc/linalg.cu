@@ -6,6 +6,7 @@
 // are arithmetic-bound: shared-memory tiles, register micro-tiles, split-K for
 // tall-skinny reductions (Gram matrices with K = n) so that every SM has work.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 
 #include "tctl_internal.cuh"
@@ -146,6 +147,135 @@ __global__ void splitk_reduce(int m, int n, int splits, int batch, double alpha,
   }
 }
 
+// ------------------------------------------------------------------ skinny GEMM
+// C = alpha op(A) op(B) + beta C with n <= 16 columns (basis changes of a few
+// vectors, matrix-vector products): the 64 x 64 tile kernel would leave most
+// of its FP64 lanes idle. op(B) tiles of SK_KT x NC sit in shared memory; the
+// contracted dimension is split across blocks (partial sums, splitk_reduce).
+constexpr int SK_KT = 128;
+
+// op(A) = A, rows contiguous: one thread per row.
+template <int NC, bool TB>
+__global__ void __launch_bounds__(256) skinny_nn_kernel(int m, int n, int k, const double *__restrict__ A,
+                                                        int lda, const double *__restrict__ B, int ldb,
+                                                        int kchunk, double *__restrict__ part) {
+  __shared__ double Bs[SK_KT][NC];
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const int q = blockIdx.y;
+  const int k0 = q * kchunk, k1 = min(k, k0 + kchunk);
+  double acc[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) acc[j] = 0.0;
+  for (int kt = k0; kt < k1; kt += SK_KT) {
+    const int kn = min(SK_KT, k1 - kt);
+    __syncthreads();
+    for (int t = threadIdx.x; t < SK_KT * NC; t += 256) {
+      const int kk = t / NC, j = t % NC;
+      Bs[kk][j] = (kk < kn && j < n)
+                      ? (TB ? B[j + (long long)(kt + kk) * ldb] : B[(kt + kk) + (long long)j * ldb])
+                      : 0.0;
+    }
+    __syncthreads();
+    if (i < m) {
+      for (int kk = 0; kk < kn; ++kk) {
+        const double a = A[i + (long long)(kt + kk) * lda];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] = fma(a, Bs[kk][j], acc[j]);
+      }
+    }
+  }
+  if (i < m)
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+      if (j < n) part[(long long)q * m * n + i + (long long)j * m] = acc[j];
+}
+
+// op(A) = A^T, each row of op(A) contiguous: one warp per row, lanes along k.
+template <int NC, bool TB>
+__global__ void __launch_bounds__(256) skinny_tn_kernel(int m, int n, int k, const double *__restrict__ A,
+                                                        int lda, const double *__restrict__ B, int ldb,
+                                                        int kchunk, double *__restrict__ part) {
+  constexpr int RPW = NC >= 8 ? 2 : 4;  // rows per warp
+  __shared__ double Bs[SK_KT][NC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.y;
+  const int k0 = q * kchunk, k1 = min(k, k0 + kchunk);
+  double acc[RPW][NC];
+#pragma unroll
+  for (int rr = 0; rr < RPW; ++rr)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[rr][j] = 0.0;
+  for (int kt = k0; kt < k1; kt += SK_KT) {
+    const int kn = min(SK_KT, k1 - kt);
+    __syncthreads();
+    for (int t = threadIdx.x; t < SK_KT * NC; t += 256) {
+      const int kk = t / NC, j = t % NC;
+      Bs[kk][j] = (kk < kn && j < n)
+                      ? (TB ? B[j + (long long)(kt + kk) * ldb] : B[(kt + kk) + (long long)j * ldb])
+                      : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < RPW; ++rr) {
+      const int i = blockIdx.x * (8 * RPW) + warp + 8 * rr;
+      if (i >= m) continue;
+      const double *a = A + (long long)i * lda + kt;
+      for (int kk = lane; kk < kn; kk += 32) {
+        const double av = a[kk];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[rr][j] = fma(av, Bs[kk][j], acc[rr][j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int i = blockIdx.x * (8 * RPW) + warp + 8 * rr;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      double v = acc[rr][j];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && i < m && j < n) part[(long long)q * m * n + i + (long long)j * m] = v;
+    }
+  }
+}
+
+template <int NC>
+static void skinny_launch(Ctx &c, bool ta, bool tb, int m, int n, int k, const double *A, int lda,
+                          const double *B, int ldb, double *part, int splits, int kchunk, int rowblocks) {
+  dim3 g(rowblocks, splits);
+#define TCTL_SK(KER, TB_) LAUNCH(c, (KER<NC, TB_>), g, 256, 0, m, n, k, A, lda, B, ldb, kchunk, part)
+  if (!ta) {
+    if (tb) TCTL_SK(skinny_nn_kernel, true);
+    else TCTL_SK(skinny_nn_kernel, false);
+  } else {
+    if (tb) TCTL_SK(skinny_tn_kernel, true);
+    else TCTL_SK(skinny_tn_kernel, false);
+  }
+#undef TCTL_SK
+}
+
+static void gemm_skinny(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const double *A,
+                        int lda, const double *B, int ldb, double beta, double *C, int ldc) {
+  const int NC = n <= 1 ? 1 : n <= 4 ? 4 : n <= 8 ? 8 : 16;
+  const int rows_per_block = ta ? 8 * (NC >= 8 ? 2 : 4) : 256;
+  const int rowblocks = (m + rows_per_block - 1) / rows_per_block;
+  int splits = std::max(1, std::min((2 * 152 + rowblocks - 1) / rowblocks, (k + 63) / 64));
+  splits = std::min(splits, 256);
+  const int kchunk = (k + splits - 1) / splits;
+  splits = (k + kchunk - 1) / kchunk;
+  size_t mk = c.ws.mark();
+  double *part = c.ws.dbl((size_t)m * n * splits);
+  c.next_flops = 2.0 * m * (double)n * k;
+  if (NC == 1) skinny_launch<1>(c, ta, tb, m, n, k, A, lda, B, ldb, part, splits, kchunk, rowblocks);
+  else if (NC == 4) skinny_launch<4>(c, ta, tb, m, n, k, A, lda, B, ldb, part, splits, kchunk, rowblocks);
+  else if (NC == 8) skinny_launch<8>(c, ta, tb, m, n, k, A, lda, B, ldb, part, splits, kchunk, rowblocks);
+  else skinny_launch<16>(c, ta, tb, m, n, k, A, lda, B, ldb, part, splits, kchunk, rowblocks);
+  const long long total = (long long)m * n;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  LAUNCH(c, splitk_reduce, blocks, 256, 0, m, n, splits, 1, alpha, part, beta, C, ldc, 0ll);
+  c.ws.reset(mk);
+}
+
 template <int BM, int BN>
 static void gemm_launch(Ctx &c, bool ta, bool tb, dim3 grid, int m, int n, int k, double alpha,
                         const double *A, int lda, long long sA, int divA, const double *B,
@@ -172,6 +302,10 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
         for (int j = 0; j < n; ++j)
           TCTL_CUDA(cudaMemsetAsync(C + b * sC + (long long)j * ldc, 0, sizeof(double) * m, c.st));
     }
+    return;
+  }
+  if (batch == 1 && n <= 16 && m >= 64 && (long long)m * n * k >= (1 << 16)) {
+    gemm_skinny(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     return;
   }
   const bool small = (m <= 32 && n <= 32);
@@ -222,6 +356,13 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
   size_t mk = c.ws.mark();
   if (splits > 1) part = c.ws.dbl((size_t)m * n * batch * splits);
   dim3 grid(gx, gy, batch * splits);
+  if (c.prof && c.trace) {
+    // per-shape profile names (TCTL_TRACE=1 with profiling on)
+    char nm[96];
+    std::snprintf(nm, sizeof(nm), "dgemm[%s%s %dx%dx%d b%d s%d]", ta ? "T" : "N", tb ? "T" : "N", m, n,
+                  k, batch, splits);
+    c.next_tag = c.intern(nm);
+  }
   c.next_flops = 2.0 * m * n * (double)k * batch;
   if (small)
     gemm_launch<32, 32>(c, ta, tb, grid, m, n, k, alpha, A, lda, sA, divA, B, ldb, sB, divB, beta,

@@ -103,6 +103,15 @@ struct Ctx {
   int *tcg_err = nullptr;            // tensor-core GEMM wait-timeout flag (device)
   bool prof = false;                 // record events around every launch
   bool trace = false;                // TCTL_TRACE=1: per-step ranks on stderr
+  std::vector<std::string> interned;  // stable storage of generated profile names
+  const char *intern(const char *s) {
+    for (const std::string &x : interned)
+      if (x == s) return x.c_str();
+    if (interned.size() >= 4096) return "dgemm[...]";
+    interned.reserve(4096);  // no reallocation: returned pointers stay valid
+    interned.emplace_back(s);
+    return interned.back().c_str();
+  }
   bool prof_phases = false;          // report "phase/kernel" names
   std::vector<ProfRec> prof_recs;
   std::vector<cudaEvent_t> prof_pool;

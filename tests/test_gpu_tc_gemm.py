@@ -74,12 +74,20 @@ def test_tc_gemm_zero_rows_and_nan(ctx):
     assert np.all(np.abs(C[ok] - ref) <= _bound(A[ok], B, 6, False, False))
 
 
-def test_fp64_path_digits0(ctx):
-    rng = np.random.default_rng(5)
-    A = rng.standard_normal((70, 50))
-    B = rng.standard_normal((50, 30))
-    C = ctx.gemm(0, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
-    assert np.allclose(C, A @ B, rtol=0, atol=1e-13 * np.abs(A).max() * np.abs(B).max() * 50)
+@pytest.mark.parametrize("m,n,k", [(70, 30, 50), (2048, 5, 2048), (3000, 1, 126), (500, 16, 700),
+                                   (257, 9, 33)])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+def test_fp64_path_digits0(ctx, m, n, k, ta, tb):
+    """FP64 FMA kernels (64x64 tiles; skinny kernels for n <= 16) vs numpy."""
+    rng = np.random.default_rng(m + 10 * n + 100 * k)
+    A = rng.standard_normal((k, m) if ta else (m, k))
+    B = rng.standard_normal((n, k) if tb else (k, n))
+    C0 = rng.standard_normal((m, n))
+    Ct = torch.from_numpy(C0.copy()).cuda()
+    ctx.gemm(0, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=Ct, trans_a=ta, trans_b=tb,
+             alpha=1.5, beta=0.5)
+    ref = 1.5 * ((A.T if ta else A) @ (B.T if tb else B)) + 0.5 * C0
+    assert np.allclose(Ct.cpu().numpy(), ref, rtol=0, atol=1e-13 * k)
 
 
 def test_tc_gemm_argument_errors(ctx):
