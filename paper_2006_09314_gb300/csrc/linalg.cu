@@ -685,79 +685,90 @@ void sym_eig_multi(Ctx &c, int count, const int *m, const double *const *A, doub
 // Pivoted Cholesky of the Gram matrix G (m x m): P^T G P = L L^T on the first
 // r pivots, stopping when the largest remaining Schur diagonal is <= thr.
 // Writes perm[0..r) and L (r x r, lower, ld 64) and r to out_r.
-__global__ void pivchol_kernel(int m, const double *__restrict__ Gin, double thr_rel_or_abs,
-                               int relative, int rcap, int *perm_out, double *L_out, int *out_r) {
+// Pivoting is virtual: G stays in its original order and a used[] mask marks
+// the chosen indices; column p_j of G is overwritten by column j of L (at the
+// original rows), which no later update touches, so L(a, b) = G[p_a][p_b].
+// Each step is a warp argmax of the remaining diagonal, the new column of L,
+// and a rank-1 update of the remaining block (three barriers).
+__global__ void __launch_bounds__(256) pivchol_kernel(int m, const double *__restrict__ Gin,
+                                                      double thr_rel_or_abs, int relative, int rcap,
+                                                      int *perm_out, double *L_out, int *out_r) {
   __shared__ double G[JMAX][JMAX + 1];
-  __shared__ int perm[JMAX];
+  __shared__ int used[JMAX], perm[JMAX];
   __shared__ int piv;
-  __shared__ double thr;
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x) G[t % m][t / m] = Gin[t];
-  for (int t = threadIdx.x; t < m; t += blockDim.x) perm[t] = t;
+  __shared__ double thr, dpiv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int t = tid; t < m * m; t += blockDim.x) G[t % m][t / m] = Gin[t];
+  for (int t = tid; t < m; t += blockDim.x) used[t] = 0;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
     double dmax = 0.0;
-    for (int i = 0; i < m; ++i) dmax = fmax(dmax, G[i][i]);
-    thr = relative ? thr_rel_or_abs * thr_rel_or_abs * dmax : thr_rel_or_abs * thr_rel_or_abs;
-    if (!(dmax > 0.0)) thr = 1e300;
+    for (int i = lane; i < m; i += 32) dmax = fmax(dmax, G[i][i]);
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if (lane == 0) {
+      thr = relative ? thr_rel_or_abs * thr_rel_or_abs * dmax : thr_rel_or_abs * thr_rel_or_abs;
+      if (!(dmax > 0.0)) thr = 1e300;
+    }
   }
   __syncthreads();
   int r = 0;
   const int rmax = min(m, rcap);
   for (int j = 0; j < rmax; ++j) {
-    if (threadIdx.x == 0) {
-      int best = j;
-      double bv = G[j][j];
-      for (int i = j + 1; i < m; ++i)
-        if (G[i][i] > bv) { bv = G[i][i]; best = i; }
-      piv = (bv > thr && isfinite(bv)) ? best : -1;
+    if (warp == 0) {
+      double bv = -1.0;
+      int bi = m;
+      for (int i = lane; i < m; i += 32) {
+        if (used[i]) continue;
+        const double d = G[i][i];
+        if (d > bv) { bv = d; bi = i; }  // lanes scan ascending i: ties keep the lower index
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        const bool ok = bi < m && bv > thr && isfinite(bv);
+        piv = ok ? bi : -1;
+        if (ok) {
+          used[bi] = 1;
+          perm[j] = bi;
+          dpiv = sqrt(bv);
+        }
+      }
     }
     __syncthreads();
     const int p = piv;
     if (p < 0) break;
-    // symmetric swap of rows/cols j and p
-    if (p != j) {
-      for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        const double tmp = G[j][t];
-        G[j][t] = G[p][t];
-        G[p][t] = tmp;
-      }
-      __syncthreads();
-      for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        const double tmp = G[t][j];
-        G[t][j] = G[t][p];
-        G[t][p] = tmp;
-      }
-      if (threadIdx.x == 0) {
-        const int tmp = perm[j];
-        perm[j] = perm[p];
-        perm[p] = tmp;
-      }
-      __syncthreads();
-    }
-    const double ljj = sqrt(G[j][j]);
+    const double dp = dpiv;
+    for (int i = tid; i < m; i += blockDim.x)
+      G[i][p] = (i == p) ? dp : (used[i] ? 0.0 : G[i][p] / dp);
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) G[i][j] /= ljj;
-    __syncthreads();
-    if (threadIdx.x == 0) G[j][j] = ljj;
-    for (int t = threadIdx.x; t < (m - j - 1) * (m - j - 1); t += blockDim.x) {
-      const int i = j + 1 + t % (m - j - 1), k = j + 1 + t / (m - j - 1);
-      if (k <= i) G[i][k] -= G[i][j] * G[k][j];
-    }
-    __syncthreads();
-    // keep symmetric copy of the trailing block for the next pivot search
-    for (int t = threadIdx.x; t < (m - j - 1) * (m - j - 1); t += blockDim.x) {
-      const int i = j + 1 + t % (m - j - 1), k = j + 1 + t / (m - j - 1);
-      if (k > i) G[i][k] = G[k][i];
+    for (int t = tid; t < m * m; t += blockDim.x) {
+      const int i = t % m, k = t / m;
+      if (!used[i] && !used[k]) G[i][k] -= G[i][p] * G[k][p];
     }
     __syncthreads();
     r = j + 1;
   }
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-    const int i = t % r, k = t / r;
-    L_out[i + k * JMAX] = (k <= i) ? G[i][k] : 0.0;
+  for (int t = tid; t < r * r; t += blockDim.x) {
+    const int a = t % r, b = t / r;
+    L_out[a + b * JMAX] = (b <= a) ? G[perm[a]][perm[b]] : 0.0;
   }
-  for (int t = threadIdx.x; t < r; t += blockDim.x) perm_out[t] = perm[t];
-  if (threadIdx.x == 0) *out_r = r;
+  for (int t = tid; t < r; t += blockDim.x) perm_out[t] = perm[t];
+  if (tid == 0) *out_r = r;
+}
+
+// max_ij |G_ij - delta_ij| > tol  ->  *flag = 1 (G: r x r Gram of nearly orthonormal columns)
+__global__ void orth_check_kernel(int r, const double *__restrict__ G, double tol, int *flag) {
+  int bad = 0;
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+    const int i = t % r, j = t / r;
+    const double d = G[t] - (i == j ? 1.0 : 0.0);
+    if (!(fabs(d) <= tol)) bad = 1;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) *flag = bad;
 }
 
 // Q[i, :] = Y[i, perm] L^{-T}: forward substitution per row (x L^T = y).
@@ -792,28 +803,34 @@ int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relati
   int *perm = c.ws.i32(JMAX);
   int *rdev = c.ws.i32(4);
   double *Q2 = c.ws.dbl((size_t)n * std::min(m, rcap > 0 ? rcap : 1));
-  const int blocks = std::min((n + 127) / 128, 1024);
-  auto read_r = [&]() {
-    int r = 0;
-    TCTL_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  // one warp per block: each thread solves one row, so n rows spread over n/32 SMs
+  const int blocks = std::min((n + 31) / 32, 4096);
+  auto read_int = [&](const int *p) {
+    int v = 0;
+    TCTL_CUDA(cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
     TCTL_CUDA(cudaStreamSynchronize(c.st));
-    return r;
+    return v;
   };
   // pass 1: pivoted Cholesky of Y^T Y picks the columns and the rank
   gemm(c, true, false, m, m, n, 1.0, Y, ldy, 0, Y, ldy, 0, 0.0, G, m, 0);
   LAUNCH(c, pivchol_kernel, 1, 256, 0, m, G, tol, relative ? 1 : 0, rcap, perm, L, rdev);
-  int r = read_r();
+  int r = read_int(rdev);
   if (r > 0) {
-    LAUNCH(c, trsm_rows_kernel, blocks, 128, 0, n, r, Y, ldy, perm, L, Q, n);
+    LAUNCH(c, trsm_rows_kernel, blocks, 32, 0, n, r, Y, ldy, perm, L, Q, n);
     // passes 2 and 3 (Cholesky QR on the result) restore orthogonality to rounding
     // level; a column whose residual has fallen to rounding noise (kept in pass 1 at
     // the edge of the tolerance) is dropped here instead of breaking the factorization.
+    // Pass 3 runs only if pass 2 left Q^T Q further than 1e-13 from the identity.
     for (int pass = 0; pass < 2 && r > 0; ++pass) {
       gemm(c, true, false, r, r, n, 1.0, Q, n, 0, Q, n, 0, 0.0, G, r, 0);
+      if (pass == 1) {
+        LAUNCH(c, orth_check_kernel, 1, 256, 0, r, G, 1e-13, rdev + 1);
+        if (!read_int(rdev + 1)) break;
+      }
       LAUNCH(c, pivchol_kernel, 1, 256, 0, r, G, 1e-10, 1, r, perm, L, rdev);
-      const int r2 = read_r();
+      const int r2 = read_int(rdev);
       if (r2 > 0) {
-        LAUNCH(c, trsm_rows_kernel, blocks, 128, 0, n, r2, Q, n, perm, L, Q2, n);
+        LAUNCH(c, trsm_rows_kernel, blocks, 32, 0, n, r2, Q, n, perm, L, Q2, n);
         copy_d(c, Q, Q2, (size_t)n * r2);
       }
       r = r2;
