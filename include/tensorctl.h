@@ -91,6 +91,15 @@ typedef struct {
                          accumulate with exact low levels, FP64 result; default);
                          0 = FP64 FMA. Gram matrices, orthonormalisation and HOSVD
                          always run in FP64.                                           */
+  int pre_src;        /* preconditioner exp-sum P(s) = s sum_k p_k exp(-theta_k s) ~ 1/F2:
+                         0 = r_pre geometric nodes, NNLS weights (default); 1 = pre_r free
+                         nodes fitted at set-up (tctl_precond_fit); 2 = nodes predicted by a
+                         trained network (pre_model, tctl_mlp_train), weights re-solved
+                         by NNLS. 1 and 2 are used only if their measured
+                         delta = max |P F2 - 1| <= pre_delta_max, else 0 is used.      */
+  int pre_r;          /* terms of pre_src 1 / 2 (default 12; the network's r)          */
+  const float *pre_model; /* HOST model blob of tctl_mlp_train (pre_src 2)              */
+  double pre_delta_max;   /* acceptance bound of pre_src 1 / 2 (default 0.25)           */
 } tctl_opts;
 
 typedef struct {
@@ -106,6 +115,8 @@ typedef struct {
   double t_setup_ms;     /* time of tctl_setup                                       */
   double t_solve_ms;     /* time of the last tctl_pcg_solve                          */
   int expsum_used;       /* representation of F2 in use: 0 sinc, 1 fitted             */
+  int pre_used;          /* preconditioner in use: 0 NNLS nodes, 1 fitted, 2 learned  */
+  double pre_delta;      /* its measured max |P(s) F2(s) - 1| on [s_min, s_max]       */
 } tctl_stats;
 
 /* Fills *o with the defaults listed above. */
@@ -201,6 +212,36 @@ int tctl_gemm(tctl_ctx *ctx, int digits, int trans_a, int trans_b, int m, int n,
  * the buffers hold the best fit found). */
 int tctl_expsum_fit(double alpha, double beta, double s_min, double s_max, double tol, double *t,
                     double *w, int cap, int *r, double *err);
+
+/* Learned preconditioner sums (SURVEY f-1; host buffers, no context).
+ * tctl_precond_fit: r free nodes theta (ascending) and weights p > 0 of
+ * P(s) = s sum_k p_k exp(-theta_k s) ~ 1/F2(s) on [s_min, s_max]
+ * (Levenberg-Marquardt on log parameters, Lawson reweighting; started from
+ * geometric nodes + NNLS); *delta = measured max |P F2 - 1| (2000 points).
+ * tctl_precond_dataset: n_samples seeded inputs X (n x 4: alpha, log10 beta,
+ * ln s_min, ln s_max; alpha in [0.1, 0.9], log10 beta in [-4, 0], s_min in
+ * [15, 45], log10 s_max in [4.5, 8.5]) and fitted targets Y (n x 2r: ln tau_k
+ * ascending, ln q_k with tau = theta s_min, q = p (s_min F2(s_min))) on
+ * `threads` host threads; delta (n) may be NULL.
+ * tctl_mlp_train: MLP 4 -> 64 -> 64 -> 2r (FP32, tanh) trained on the GPU by
+ * the library's kernels (MSE on standardised targets, Adam, cosine decay, one
+ * step captured in a CUDA graph); model: tctl_mlp_model_size(r) floats
+ * (parameters + input / output standardisation); loss[0], loss[1] = dataset
+ * MSE before / after training (may be NULL).
+ * tctl_mlp_grad: loss and parameter gradient of one batch (standardised X
+ * (batch x 4) and T (batch x 2r); params: the first mlp parameters of a model).
+ * tctl_mlp_forward: raw (ln tau, ln q) for n raw inputs (GPU inference kernel).
+ * Errors: TCTL_E_ARG, TCTL_E_CUDA. r in [2, 32]. */
+int tctl_precond_fit(double alpha, double beta, double s_min, double s_max, int r, double *theta,
+                     double *p, double *delta);
+int tctl_precond_dataset(int r, int n_samples, unsigned long long seed, int threads, float *X,
+                         float *Y, double *delta);
+int tctl_mlp_model_size(int r);
+int tctl_mlp_train(int r, int n_samples, const float *X, const float *Y, int steps, int batch,
+                   float lr, unsigned long long seed, float *model, float *loss);
+int tctl_mlp_grad(int r, int batch, const float *params, const float *X, const float *T,
+                  float *grad, float *loss);
+int tctl_mlp_forward(int r, int n, const float *model, const float *X, float *Y);
 
 /* Copies the separable representation in use (Sections 3.4, 3.5): which = 0
  * the operator F2 (R terms), 1 the preconditioner. Term k is the Kronecker

@@ -183,6 +183,10 @@ int tctl_default_opts(tctl_opts *o) {
   o->seed = 1;
   o->range_tol = 0.03;
   o->tc_gemm = 1;
+  o->pre_src = 0;
+  o->pre_r = 12;
+  o->pre_model = nullptr;
+  o->pre_delta_max = 0.25;
   return TCTL_OK;
 }
 
@@ -212,6 +216,9 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
       fail(TCTL_E_ARG, "expsum_src must be 0 (sinc) or 1 (fitted)");
     if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
     if (c->o.tc_gemm != 0 && c->o.tc_gemm != 1) fail(TCTL_E_ARG, "tc_gemm must be 0 or 1");
+    if (c->o.pre_src < 0 || c->o.pre_src > 2) fail(TCTL_E_ARG, "pre_src must be 0, 1 or 2");
+    if (c->o.pre_src && (c->o.pre_r < 2 || c->o.pre_r > kPreRMax)) fail(TCTL_E_ARG, "pre_r must be in [2, 32]");
+    if (c->o.pre_src == 2 && !c->o.pre_model) fail(TCTL_E_ARG, "pre_src 2 needs pre_model");
     if (!(c->o.range_tol >= 0.0 && c->o.range_tol <= 1.0))
       fail(TCTL_E_ARG, "range_tol must lie in [0, 1]");
     if (!(c->o.op_tol > 0 && c->o.op_tol < 1e-2)) fail(TCTL_E_ARG, "op_tol must be in (0, 1e-2)");
@@ -246,6 +253,8 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
     for (int l = 0; l < 3; ++l) c->stats.op_basis[l] = c->op.rD[l];
     c->stats.op_rel_err = c->op_rel_err;
     c->stats.expsum_used = c->expsum_used;
+    c->stats.pre_used = c->pre_used;
+    c->stats.pre_delta = c->pre_delta;
     c->stats.s_min = c->s_min;
     c->stats.s_max = c->s_max;
     *ctx = reinterpret_cast<tctl_ctx *>(c);
@@ -457,6 +466,80 @@ int tctl_expsum_fit(double alpha, double beta, double s_min, double s_max, doubl
     const int s = expsum_fit_host(alpha, beta, s_min, s_max, tol, t, w, cap, r, err);
     if (s == TCTL_E_RANK_CAP) fail(s, "more terms than cap");
     if (s == TCTL_E_NUMERIC) fail(s, "fitted exponential sum misses the tolerance");
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(nullptr, e);
+  }
+}
+
+int tctl_precond_fit(double alpha, double beta, double s_min, double s_max, int r, double *theta,
+                     double *p, double *delta) {
+  try {
+    if (!(alpha > 0.0 && alpha <= 1.0)) fail(TCTL_E_ARG, "alpha must be in (0, 1]");
+    if (!(beta > 0.0) || !std::isfinite(beta)) fail(TCTL_E_ARG, "beta must be positive");
+    if (!(s_min > 0.0 && s_max > s_min && std::isfinite(s_max)))
+      fail(TCTL_E_ARG, "need 0 < s_min < s_max < inf");
+    if (r < 2 || r > kPreRMax) fail(TCTL_E_ARG, "r must be in [2, 32]");
+    if (!theta || !p) fail(TCTL_E_ARG, "NULL output buffer");
+    std::vector<double> tau(r), q(r);
+    const double d = pre_fit(alpha, beta, s_min, s_max, r, tau.data(), q.data());
+    const double h0 = 1.0 / (s_min * (std::pow(s_min, -alpha) + beta * std::pow(s_min, alpha)));
+    for (int k = 0; k < r; ++k) {
+      theta[k] = tau[k] / s_min;
+      p[k] = q[k] * h0;
+    }
+    if (delta) *delta = d;
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(nullptr, e);
+  }
+}
+
+int tctl_precond_dataset(int r, int n_samples, unsigned long long seed, int threads, float *X,
+                         float *Y, double *delta) {
+  try {
+    if (r < 2 || r > kPreRMax) fail(TCTL_E_ARG, "r must be in [2, 32]");
+    if (n_samples < 1 || !X || !Y) fail(TCTL_E_ARG, "need n_samples >= 1 and output buffers");
+    precond_sample_inputs(n_samples, seed, X);
+    precond_dataset(r, n_samples, X, std::max(1, std::min(threads, 256)), Y, delta);
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(nullptr, e);
+  }
+}
+
+int tctl_mlp_model_size(int r) { return (r < 2 || r > kPreRMax) ? -1 : mlp_param_count(2 * r) + 8 + 4 * r; }
+
+int tctl_mlp_train(int r, int n_samples, const float *X, const float *Y, int steps, int batch,
+                   float lr, unsigned long long seed, float *model, float *loss) {
+  try {
+    if (r < 2 || r > kPreRMax) fail(TCTL_E_ARG, "r must be in [2, 32]");
+    if (n_samples < 2 || !X || !Y || !model) fail(TCTL_E_ARG, "need data and a model buffer");
+    if (steps < 1 || batch < 1 || batch > 4096 || !(lr > 0.0f)) fail(TCTL_E_ARG, "bad training parameters");
+    mlp_train(r, n_samples, X, Y, steps, batch, lr, seed, model, loss);
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(nullptr, e);
+  }
+}
+
+int tctl_mlp_grad(int r, int batch, const float *params, const float *X, const float *T, float *grad,
+                  float *loss) {
+  try {
+    if (r < 2 || r > kPreRMax) fail(TCTL_E_ARG, "r must be in [2, 32]");
+    if (batch < 1 || !params || !X || !T || !grad || !loss) fail(TCTL_E_ARG, "NULL buffer");
+    mlp_grad_host(r, batch, params, X, T, grad, loss);
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(nullptr, e);
+  }
+}
+
+int tctl_mlp_forward(int r, int n, const float *model, const float *X, float *Y) {
+  try {
+    if (r < 2 || r > kPreRMax) fail(TCTL_E_ARG, "r must be in [2, 32]");
+    if (n < 1 || !model || !X || !Y) fail(TCTL_E_ARG, "NULL buffer");
+    mlp_forward_host(r, n, model, X, Y, cudaStreamPerThread);
     return TCTL_OK;
   } catch (const Error &e) {
     return handle(nullptr, e);

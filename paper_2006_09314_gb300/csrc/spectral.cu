@@ -407,6 +407,10 @@ void compress_sep(Ctx &c, Sep &D, double tol) {
 
 }  // namespace
 
+std::vector<double> nnls_solve(const std::vector<double> &A, int M, int K, const std::vector<double> &b) {
+  return nnls(A, M, K, b);
+}
+
 int expsum_fit_host(double a, double b, double smin, double smax, double tol, double *t, double *w,
                     int cap, int *r, double *err) {
   const ExpFit f = fit_F2(a, b, smin, smax, tol);
@@ -531,10 +535,50 @@ void setup_spectral(Ctx &c) {
     for (int j = 0; j < kPreSamples; ++j) A[j + (size_t)k * kPreSamples] /= cs[k];
   }
   std::vector<double> p = nnls(A, kPreSamples, K, rhs);
+  for (int k = 0; k < K; ++k) p[k] /= cs[k];
+  // alternatives with r free nodes: fitted at set-up (pre_src 1) or predicted by the
+  // trained network (pre_src 2, weights re-solved on its nodes); each is measured and
+  // replaces the K-node NNLS sum only if its delta = max |P F2 - 1| <= pre_delta_max
+  c.pre_used = 0;
+  c.pre_delta = pre_delta(theta.data(), p.data(), K, a, b, smin, smax);
+  if (c.o.pre_src == 1 || c.o.pre_src == 2) {
+    const int r = c.o.pre_r;
+    std::vector<double> th(r), pr(r);
+    double d = 1e300;
+    if (c.o.pre_src == 1) {
+      std::vector<double> tau(r), q(r);
+      pre_fit(a, b, smin, smax, r, tau.data(), q.data());
+      const double h0 = 1.0 / (smin * F2h(smin, a, b));
+      for (int k = 0; k < r; ++k) {
+        th[k] = tau[k] / smin;
+        pr[k] = q[k] * h0;
+      }
+      d = pre_delta(th.data(), pr.data(), r, a, b, smin, smax);
+    } else {
+      const float xin[4] = {(float)a, (float)std::log10(b), (float)std::log(smin), (float)std::log(smax)};
+      std::vector<float> y(2 * r);
+      mlp_forward_host(r, 1, c.o.pre_model, xin, y.data(), c.st);
+      const double h0 = 1.0 / (smin * F2h(smin, a, b));
+      for (int k = 0; k < r; ++k) {
+        th[k] = std::exp((double)y[k]) / smin;
+        pr[k] = std::exp((double)y[r + k]) * h0;
+      }
+      const double d_raw = pre_delta(th.data(), pr.data(), r, a, b, smin, smax);
+      std::vector<double> pn = pre_weights_nnls(th, a, b, smin, smax);
+      const double d_nnls = pre_delta(th.data(), pn.data(), r, a, b, smin, smax);
+      if (d_nnls < d_raw) pr = pn;
+      d = std::min(d_raw, d_nnls);
+    }
+    if (std::isfinite(d) && d <= c.o.pre_delta_max) {
+      theta = th;
+      p = pr;
+      c.pre_used = c.o.pre_src;
+      c.pre_delta = d;
+    }
+  }
   std::vector<double> pw;
   std::vector<TermDesc> ptd;
-  for (int k = 0; k < K; ++k) {
-    p[k] /= cs[k];
+  for (size_t k = 0; k < theta.size(); ++k) {
     if (p[k] <= 0) continue;
     for (int m = 0; m < 3; ++m) {
       pw.push_back(p[k]);

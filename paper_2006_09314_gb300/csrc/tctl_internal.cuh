@@ -83,6 +83,8 @@ struct Ctx {
   Sep op, pre;
   double op_rel_err = 0;
   int expsum_used = 0;                     // 0 sinc, 1 fitted
+  int pre_used = 0;                        // preconditioner: 0 K-node NNLS, 1 fitted, 2 learned
+  double pre_delta = 0;                    // its measured max |P F2 - 1|
   std::vector<double> op_terms_w, op_terms_t, pre_terms_w, pre_terms_t;  // host copies
   std::vector<int> op_terms_m, pre_terms_m;
   Arena ws;
@@ -229,6 +231,23 @@ void setup_eigs(Ctx &c);
 // ------------------------------------------------------------ spectral.cu
 int expsum_fit_host(double a, double b, double smin, double smax, double tol, double *t, double *w,
                     int cap, int *r, double *err);
+// ------------------------------------------------------------ learned.cu
+constexpr int kMlpIn = 4, kMlpH = 64, kPreRMax = 32;
+double pre_fit(double a, double b, double smin, double smax, int r, double *tau_out, double *q_out);
+double pre_delta(const double *theta, const double *p, int r, double a, double b, double smin,
+                 double smax);
+std::vector<double> pre_weights_nnls(const std::vector<double> &theta, double a, double b,
+                                     double smin, double smax);
+int mlp_param_count(int O);
+void precond_sample_inputs(int N, uint64_t seed, float *X);
+void precond_dataset(int r, int N, const float *X, int threads, float *Y, double *delta);
+void mlp_train(int r, int N, const float *X, const float *Y, int steps, int B, float lr,
+               uint64_t seed, float *model, float *loss_out);
+void mlp_grad_host(int r, int B, const float *params, const float *X, const float *T, float *grad,
+                   float *loss);
+void mlp_forward_host(int r, int n, const float *model, const float *X, float *Yout, cudaStream_t st);
+// Lawson-Hanson NNLS, A M x K column-major.
+std::vector<double> nnls_solve(const std::vector<double> &A, int M, int K, const std::vector<double> &b);
 void setup_spectral(Ctx &c);
 void fullgrid_apply(Ctx &c, const double *y, double *u, int which);
 

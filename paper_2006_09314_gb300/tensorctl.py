@@ -35,7 +35,8 @@ EXPORTED = [
     "tctl_solve_host", "tctl_cp_alloc", "tctl_cp_free", "tctl_get_eigs",
     "tctl_get_stats", "tctl_launch_count", "tctl_destroy", "tctl_last_error",
     "tctl_profile_enable", "tctl_profile_report", "tctl_eig1d_noalloc", "tctl_get_expsum",
-    "tctl_expsum_fit", "tctl_gemm",
+    "tctl_expsum_fit", "tctl_gemm", "tctl_precond_fit", "tctl_precond_dataset",
+    "tctl_mlp_model_size", "tctl_mlp_train", "tctl_mlp_grad", "tctl_mlp_forward",
 ]
 
 ERRORS = {0: "OK", -1: "E_ARG", -2: "E_COEFF", -3: "E_CUDA", -4: "E_NOMEM",
@@ -60,7 +61,8 @@ class Opts(ctypes.Structure):
                 ("basis", ctypes.c_int), ("expsum_src", ctypes.c_int),
                 ("paper_end_rows", ctypes.c_int), ("eps_final", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("range_tol", ctypes.c_double),
-                ("tc_gemm", ctypes.c_int)]
+                ("tc_gemm", ctypes.c_int), ("pre_src", ctypes.c_int), ("pre_r", ctypes.c_int),
+                ("pre_model", ctypes.c_void_p), ("pre_delta_max", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -70,7 +72,8 @@ class Stats(ctypes.Structure):
                 ("pre_rank", ctypes.c_int), ("op_rel_err", ctypes.c_double),
                 ("s_min", ctypes.c_double), ("s_max", ctypes.c_double),
                 ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
-                ("expsum_used", ctypes.c_int)]
+                ("expsum_used", ctypes.c_int), ("pre_used", ctypes.c_int),
+                ("pre_delta", ctypes.c_double)]
 
     def as_dict(self):
         out = {}
@@ -122,6 +125,12 @@ def load(build_if_missing: bool = True):
         "tctl_get_expsum": (I, [P, I, P, P, P, I, P]),
         "tctl_expsum_fit": (I, [D, D, D, D, D, P, P, I, P, P]),
         "tctl_gemm": (I, [P, I, I, I, I, I, I, D, P, I, P, I, D, P, I]),
+        "tctl_precond_fit": (I, [D, D, D, D, I, P, P, P]),
+        "tctl_precond_dataset": (I, [I, I, ctypes.c_ulonglong, I, P, P, P]),
+        "tctl_mlp_model_size": (I, [I]),
+        "tctl_mlp_train": (I, [I, I, P, P, I, I, ctypes.c_float, ctypes.c_ulonglong, P, P]),
+        "tctl_mlp_grad": (I, [I, I, P, P, P, P, P]),
+        "tctl_mlp_forward": (I, [I, I, P, P, P]),
         "tctl_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -319,6 +328,63 @@ def tctl_gemm(ctx, digits, A, B, C=None, trans_a=False, trans_b=False, alpha=1.0
                             B.data_ptr(), B.shape[1], A.data_ptr(), A.shape[1], beta,
                             C.data_ptr(), n), ctx)
     return C
+
+
+def tctl_precond_fit(alpha, beta, s_min, s_max, r):
+    """r free-node preconditioner sum: (theta, p, delta) (host only)."""
+    import numpy as np
+    th, p, d = np.zeros(r), np.zeros(r), ctypes.c_double(0)
+    _check(load().tctl_precond_fit(alpha, beta, s_min, s_max, r, th.ctypes.data, p.ctypes.data,
+                                   ctypes.byref(d)))
+    return th, p, d.value
+
+
+def tctl_precond_dataset(r, n, seed=1, threads=None):
+    """(X (n, 4), Y (n, 2r), delta (n)) float32/float32/float64 (host only)."""
+    import os
+    import numpy as np
+    threads = threads or len(os.sched_getaffinity(0))
+    X = np.zeros((n, 4), np.float32)
+    Y = np.zeros((n, 2 * r), np.float32)
+    d = np.zeros(n)
+    _check(load().tctl_precond_dataset(r, n, seed, threads, X.ctypes.data, Y.ctypes.data,
+                                       d.ctypes.data))
+    return X, Y, d
+
+
+def tctl_mlp_train(r, X, Y, steps=3000, batch=256, lr=2e-3, seed=1):
+    """Train the 4 -> 64 -> 64 -> 2r network on the GPU: (model float32 array, loss[2])."""
+    import numpy as np
+    X = np.ascontiguousarray(X, np.float32)
+    Y = np.ascontiguousarray(Y, np.float32)
+    model = np.zeros(load().tctl_mlp_model_size(r), np.float32)
+    loss = np.zeros(2, np.float32)
+    _check(load().tctl_mlp_train(r, X.shape[0], X.ctypes.data, Y.ctypes.data, steps, batch, lr, seed,
+                                 model.ctypes.data, loss.ctypes.data))
+    return model, loss
+
+
+def tctl_mlp_grad(r, params, X, T):
+    """(loss, grad) of one batch on the GPU (standardised X, T; float32)."""
+    import numpy as np
+    params = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    T = np.ascontiguousarray(T, np.float32)
+    g = np.zeros_like(params)
+    loss = np.zeros(1, np.float32)
+    _check(load().tctl_mlp_grad(r, X.shape[0], params.ctypes.data, X.ctypes.data, T.ctypes.data,
+                                g.ctypes.data, loss.ctypes.data))
+    return float(loss[0]), g
+
+
+def tctl_mlp_forward(r, model, X):
+    """Raw (ln tau, ln q) for raw inputs X (n, 4) through the GPU inference kernel."""
+    import numpy as np
+    X = np.ascontiguousarray(X, np.float32)
+    Y = np.zeros((X.shape[0], 2 * r), np.float32)
+    _check(load().tctl_mlp_forward(r, X.shape[0], np.ascontiguousarray(model, np.float32).ctypes.data,
+                                   X.ctypes.data, Y.ctypes.data))
+    return Y
 
 
 def tctl_expsum_fit(alpha, beta, s_min, s_max, tol, cap=256):
