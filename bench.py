@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=9, help="concurrent solves per step (<= 9)")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP64-sinc / FP64-fitted / learned-preconditioner comparison")
     ap.add_argument("--fullgrid-n", type=int, default=512,
                     help="grid of the full-grid mode-product measurement (0: skip)")
     ap.add_argument("--fullgrid-only", action="store_true",
@@ -265,6 +267,40 @@ def ours_arm(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def batch_runner(cs, steps, warmup):
+        """Concurrent solves of the problems on contexts cs: (ms per step list, results)."""
+        out = [None] * B
+
+        def wk(i, start_evt, end_evt):
+            with torch.cuda.stream(streams[i]):
+                streams[i].wait_event(start_evt)
+                out[i] = cs[i].pcg_solve(bs[i])
+                end_evt.record(streams[i])
+
+        def step():
+            start = torch.cuda.Event(enable_timing=True)
+            final = torch.cuda.Event(enable_timing=True)
+            ends = [torch.cuda.Event() for _ in range(B)]
+            start.record(master)
+            th = [threading.Thread(target=wk, args=(i, start, ends[i])) for i in range(B)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            for e in ends:
+                master.wait_event(e)
+            final.record(master)
+            final.synchronize()
+            return start.elapsed_time(final)
+        for _ in range(warmup):
+            step()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ts.append(step())
+        return ts, out
+
     for _ in range(args.warmup):
         batch_step()
     barrier()
@@ -325,6 +361,10 @@ def ours_arm(args, rank, world):
     h2d = sum(8 * (3 * (n + 1) + RANK + 3 * n * RANK) for _ in probs)
     d2h = sum(8 * (r + 3 * n * r) for r in e2e_rank)
 
+    variants = None
+    if not args.no_variants:
+        variants = variants_section(args, T, probs, streams, bs, master, sols, batch_runner)
+
     if rank != 0:
         return
     fgsec = fullgrid_section(args, check=not args.no_check) if args.fullgrid_n > 0 else None
@@ -368,7 +408,8 @@ def ours_arm(args, rank, world):
         "config": {"workload": (f"rank-structured FP64 PCG control solves, n={n}, the "
                                 f"{len(ALPHAS)}x{len(BETAS)} (alpha, beta) grid "
                                 f"alpha in {ALPHAS}, beta in {BETAS}, design rank {RANK}, "
-                                f"eps={EPS}, sinc F2 to 1e-8; one step = {B} concurrent solves"),
+                                f"eps={EPS}, fitted exp-sum F2 to 1e-8, tensor-core contractions; "
+                                f"one step = {B} concurrent solves"),
                    "n": n, "batch": B, "rank": RANK, "eps_trunc": EPS,
                    "l2": "flushed between timed steps (256 MB write)",
                    "setup_ms_mean": statistics.mean(setup_ms),
@@ -384,6 +425,7 @@ def ours_arm(args, rank, world):
                 "d2h_bytes_per_step": d2h,
                 "note": f"tctl_solve_host x{B} concurrently: setup + H2D (pinned) + PCG + D2H"},
         "mode_products": fgsec,
+        "variants": variants,
         "gpu_launches": launches,
         "clocks": clk,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
@@ -392,6 +434,63 @@ def ours_arm(args, rank, world):
     print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
+
+
+def variants_section(args, T, probs, streams, bs, master, ref_sols, batch_runner):
+    """The same step with other forms of the method, on the same problems.
+
+    fp64_sinc: sinc-quadrature F2 (Section 3.4) and FP64 FMA contractions (the
+    plain method); fp64_fitted: fitted exponential sums, FP64; learned_pre: the
+    default (fitted sums, tensor-core contractions) with an r = 12 preconditioner
+    predicted by a network trained here on the library's own fitted sums;
+    fitted_pre: the same with the r = 12 sum fitted at set-up (what a perfect
+    network would give).
+    Error bound of each solve: the main run's oracle error (checked) plus the
+    canonical-format distance to the main run's solution (exact inner products).
+    """
+    import torch
+    from oracle import formats as Fm
+    n = args.n
+    out = {}
+    t0 = time.perf_counter()
+    r = 12
+    X, Y, dl = T.tctl_precond_dataset(r, 1024, seed=2024)
+    t1 = time.perf_counter()
+    model, loss = T.tctl_mlp_train(r, X, Y, steps=3000, batch=256, lr=3e-3, seed=7)
+    t2 = time.perf_counter()
+    forms = [("fp64_sinc", dict(expsum_src=0, tc_gemm=0)),
+             ("fp64_fitted", dict(expsum_src=1, tc_gemm=0)),
+             ("learned_pre", dict(pre_src=2, pre_r=r, pre_model=model.ctypes.data, pre_delta_max=0.25)),
+             ("fitted_pre", dict(pre_src=1, pre_r=r, pre_delta_max=0.25))]
+    ref = [x.to_numpy() for x in ref_sols]
+    for name, kw in forms:
+        cs = [T.Context(p.coeffs, n, p.alpha, p.beta, EPS, opts=T.tctl_default_opts(**kw),
+                        stream=s.cuda_stream) for p, s in zip(probs, streams)]
+        steps = max(1, min(2, args.steps))
+        ts, res = batch_runner(cs, steps, 1)
+        diffs = []
+        for (w0, U0), (x, st, _) in zip(ref, res):
+            w1, U1 = x.to_numpy()
+            d2 = (Fm.cp_inner(w0, U0, w0, U0) - 2 * Fm.cp_inner(w0, U0, w1, U1)
+                  + Fm.cp_inner(w1, U1, w1, U1))
+            diffs.append(float(np.sqrt(max(d2, 0.0)) / np.sqrt(Fm.cp_inner(w0, U0, w0, U0))))
+        out[name] = {"solves_per_s": len(probs) * steps / (sum(ts) / 1000.0),
+                     "ms_per_step": sum(ts) / steps,
+                     "rel_diff_to_main": diffs,
+                     "iters": [x[1]["iters"] for x in res],
+                     "op_rank": [c.stats()["op_rank"] for c in cs],
+                     "pre_rank": [c.stats()["pre_rank"] for c in cs],
+                     "pre_used": [c.stats()["pre_used"] for c in cs],
+                     "pre_delta": [c.stats()["pre_delta"] for c in cs]}
+        for c in cs:
+            c.close()
+        torch.cuda.synchronize()
+    out["learned_pre"]["training"] = {
+        "r": r, "samples": int(X.shape[0]), "fit_s": t1 - t0, "train_s": t2 - t1,
+        "fitted_delta_median": float(np.median(dl)),
+        "mse_before": float(loss[0]), "mse_after": float(loss[1]),
+        "net": "4 -> 64 -> 64 -> 24 FP32 tanh, Adam 3000 steps x 256, GPU kernels + CUDA graph"}
+    return out
 
 
 def fullgrid_section(args, check=True):
