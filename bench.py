@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=9, help="concurrent solves per step (<= 9)")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="problems of the uneven batch section (0 = skip)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP64-sinc / FP64-fitted / learned-preconditioner comparison")
     ap.add_argument("--fullgrid-n", type=int, default=512,
@@ -368,6 +370,7 @@ def ours_arm(args, rank, world):
     if rank != 0:
         return
     fgsec = fullgrid_section(args, check=not args.no_check) if args.fullgrid_n > 0 else None
+    batchsec = batch_section(args, T, pool) if args.batch_count > 0 else None
     errs = []
     if not args.no_check:
         for p, x in zip(probs, sols):
@@ -417,6 +420,8 @@ def ours_arm(args, rank, world):
                    "rank_x": [s["rank_x"] for s in stats],
                    "op_rank": [c.stats()["op_rank"] for c in ctxs],
                    "op_basis": [c.stats()["op_basis"] for c in ctxs],
+                   "workspace_peak_mb": [round(c.stats()["ws_peak_mb"], 1) for c in ctxs],
+                   "workspace_mb": ctxs[0].stats()["ws_size_mb"],
                    "rel_err_vs_oracle": errs or None, "solves_passing": passing,
                    "parallelism": f"replicas x{world}, {B} concurrent streams per GPU"},
         "roofline": roofline,
@@ -426,6 +431,7 @@ def ours_arm(args, rank, world):
                 "note": f"tctl_solve_host x{B} concurrently: setup + H2D (pinned) + PCG + D2H"},
         "mode_products": fgsec,
         "variants": variants,
+        "uneven_batch": batchsec,
         "gpu_launches": launches,
         "clocks": clk,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
@@ -491,6 +497,35 @@ def variants_section(args, T, probs, streams, bs, master, ref_sols, batch_runner
         "mse_before": float(loss[0]), "mse_after": float(loss[1]),
         "net": "4 -> 64 -> 64 -> 24 FP32 tanh, Adam 3000 steps x 256, GPU kernels + CUDA graph"}
     return out
+
+
+def batch_section(args, T, pool):
+    """Uneven batch: `batch_count` problems (n in {64, 96, ..., 512}, design rank 1-8,
+    alpha ~ U[0.2, 0.8], log10 beta ~ U[-4, 0]) through tctl_solve_batch (host buffers,
+    16 worker threads, each problem set up, solved and torn down); per-problem latency
+    percentiles. Four problems (the smallest n) are checked against the oracle."""
+    from paper_2006_09314_gb300.inputs import batch_problems
+    probs = batch_problems(args.batch_count, 4000)
+    items = [dict(coeffs=p.coeffs, n=p.n, alpha=p.alpha, beta=p.beta, yw=p.yw, yU=p.yU) for p in probs]
+    T.tctl_solve_batch(items[:8], EPS, workers=8)  # warm-up (module load, first allocations)
+    t0 = time.perf_counter()
+    res = T.tctl_solve_batch(items, EPS, workers=16)
+    wall = time.perf_counter() - t0
+    lat = np.array([r["latency_ms"] for r in res])
+    ws = max(r["stats"]["ws_peak_mb"] / r["stats"]["ws_size_mb"] for r in res)
+    ok = [r["status"] == 0 for r in res]
+    errs = []
+    if pool is not None and not args.no_check:
+        for i in np.argsort([p.n for p in probs])[:4]:
+            errs.append(oracle_error(probs[i], res[i]["uw"], res[i]["uU"], pool))
+    return {"problems": len(probs), "workers": 16, "wall_s": wall,
+            "problems_per_s": len(probs) / wall, "all_ok": bool(all(ok)),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
+            "workspace_peak_frac_max": ws,
+            "rel_err_sample": errs or None,
+            "note": "latency = set-up (eigendecomposition, exp-sum fits) + H2D + PCG + D2H + teardown"}
 
 
 def fullgrid_section(args, check=True):

@@ -100,6 +100,8 @@ typedef struct {
   int pre_r;          /* terms of pre_src 1 / 2 (default 12; the network's r)          */
   const float *pre_model; /* HOST model blob of tctl_mlp_train (pre_src 2)              */
   double pre_delta_max;   /* acceptance bound of pre_src 1 / 2 (default 0.25)           */
+  int workspace_mb;   /* device workspace arena of the context in MiB; 0 = automatic
+                         (sized from n); too small an arena fails with TCTL_E_NOMEM   */
 } tctl_opts;
 
 typedef struct {
@@ -117,6 +119,8 @@ typedef struct {
   int expsum_used;       /* representation of F2 in use: 0 sinc, 1 fitted             */
   int pre_used;          /* preconditioner in use: 0 NNLS nodes, 1 fitted, 2 learned  */
   double pre_delta;      /* its measured max |P(s) F2(s) - 1| on [s_min, s_max]       */
+  double ws_peak_mb;     /* peak use of the context's workspace arena so far (MiB)    */
+  double ws_size_mb;     /* size of the arena (MiB)                                    */
 } tctl_stats;
 
 /* Fills *o with the defaults listed above. */
@@ -143,6 +147,20 @@ int tctl_apply_op(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y);
 
 /* y = trunc(P(A) x, eps_trunc), P ~ F2^-1 the preconditioner (Section 3.5 (B)). */
 int tctl_apply_precond(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y);
+
+/* State recovery (state equation "State" of Section 3.1 with beta_p = 1):
+ * y = trunc(A^-alpha u, eps_trunc) with the fitted exponential sum of
+ * s^-alpha (one Kronecker term per node; measured relative error <= op_tol,
+ * built on the first call). u, y: canonical, physical coordinates; y->cap as
+ * in tctl_apply_op. Errors: as tctl_apply_op, TCTL_E_NUMERIC if no sum meets
+ * op_tol. */
+int tctl_apply_state(tctl_ctx *ctx, const tctl_cp *u, tctl_cp *y);
+
+/* The paper's general constants (Section 3.1): beta_p A^-alpha u +
+ * (gamma / beta_p) A^alpha u = y_Omega equals beta_p (A^-alpha + beta A^alpha) u
+ * = y_Omega with beta = gamma / beta_p^2, so u_paper = u_scale * u with
+ * u_scale = 1 / beta_p, u the solution for tctl_setup's beta. Host only. */
+int tctl_map_constants(double beta_p, double gamma, double *beta, double *u_scale);
 
 /* y = trunc(x, eps) (Appendix 1: canonical-to-Tucker by reduced HOSVD, core
  * truncation, Tucker-to-canonical). ||x - y|| <= eps ||x||. y may equal x. */
@@ -174,6 +192,31 @@ int tctl_solve_host(const double *coeffs, int n, double alpha, double beta,
                     double eps_trunc, const tctl_opts *opts, const double *yw,
                     const double *yU, int S, double *uw, double *uU, int cap,
                     int *u_rank, tctl_stats *st);
+
+/* One problem of tctl_solve_batch: inputs as tctl_solve_host (HOST buffers;
+ * yU: 3 x n x S mode-major, uU: 3 x n x cap); outputs u_rank, status (a
+ * TCTL_* code), latency_ms (wall time of this problem: set-up, copies, PCG,
+ * copy back, teardown) and *st when st is not NULL. */
+typedef struct {
+  const double *coeffs;
+  int n;
+  double alpha, beta;
+  const double *yw, *yU;
+  int S;
+  double *uw, *uU;
+  int cap;
+  tctl_stats *st;
+  int u_rank;
+  int status;
+  double latency_ms;
+} tctl_batch_item;
+
+/* Batched solves (SURVEY f-2): `count` independent problems of any n, rank,
+ * alpha and beta, scheduled dynamically over `workers` host threads, each
+ * issuing to its own stream so that the problems overlap on the GPU. Returns
+ * TCTL_OK, or the first non-OK item status (every item is attempted). */
+int tctl_solve_batch(tctl_batch_item *items, int count, double eps_trunc, const tctl_opts *opts,
+                     int workers);
 
 /* Allocates a canonical tensor with cap terms (device memory, zero rank). */
 int tctl_cp_alloc(tctl_ctx *ctx, int cap, tctl_cp *out);

@@ -5,8 +5,12 @@
 #include <cstdlib>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <atomic>
+#include <mutex>
+#include <thread>
 
 #include "tctl_internal.cuh"
 
@@ -157,6 +161,8 @@ int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
   c.stats.rel_res = rel;
   for (int l = 0; l < 3; ++l) c.stats.rank_x[l] = X.r[l];
   c.stats.max_rank = maxr;
+  c.stats.ws_peak_mb = (double)c.ws.peak / (1 << 20);
+  c.stats.ws_size_mb = (double)c.ws.size / (1 << 20);
   c.ws.reset(mk);
   c.stats.t_solve_ms = timer.stop_ms();
   if (st) *st = c.stats;
@@ -166,6 +172,34 @@ int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
 }  // namespace tctl
 
 extern "C" {
+
+// Contexts allocate from the device's default memory pool, stream-ordered, so
+// that creating and destroying contexts on concurrent streams never
+// synchronises the device; freed blocks stay in the pool (release threshold
+// raised once per device and process) for the next context.
+static void keep_pool_memory() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done.push_back(dev);
+}
+
+// Automatic workspace: the set-up needs 6 n^2 doubles; a solve's peak grows
+// about linearly in n (sketch and Khatri-Rao matrices of n x 64^2, their digit
+// planes, the core-projection chunks capped at 48 Mi doubles).
+static size_t auto_arena_bytes(int n) {
+  const size_t setup = (size_t)6 * n * n * sizeof(double);
+  const size_t solve = std::min<size_t>((size_t)3 << 30, ((size_t)512 << 20) + (size_t)n * (1280u << 10));
+  return setup + solve;
+}
 
 int tctl_default_opts(tctl_opts *o) {
   if (!o) return TCTL_E_ARG;
@@ -216,6 +250,7 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
       fail(TCTL_E_ARG, "expsum_src must be 0 (sinc) or 1 (fitted)");
     if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
     if (c->o.tc_gemm != 0 && c->o.tc_gemm != 1) fail(TCTL_E_ARG, "tc_gemm must be 0 or 1");
+    if (c->o.workspace_mb < 0) fail(TCTL_E_ARG, "workspace_mb must be >= 0");
     if (c->o.pre_src < 0 || c->o.pre_src > 2) fail(TCTL_E_ARG, "pre_src must be 0, 1 or 2");
     if (c->o.pre_src && (c->o.pre_r < 2 || c->o.pre_r > kPreRMax)) fail(TCTL_E_ARG, "pre_r must be in [2, 32]");
     if (c->o.pre_src == 2 && !c->o.pre_model) fail(TCTL_E_ARG, "pre_src 2 needs pre_model");
@@ -235,19 +270,26 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
     c->eps = eps_trunc;
     c->st = static_cast<cudaStream_t>(cuda_stream);
     auto t0 = std::chrono::steady_clock::now();
-    const size_t arena = (size_t)6 * n * n * sizeof(double) + ((size_t)3 << 30);
+    const size_t arena = c->o.workspace_mb > 0 ? ((size_t)c->o.workspace_mb << 20) : auto_arena_bytes(n);
     void *base = nullptr;
-    check_cuda(cudaMalloc(&base, arena), "cudaMalloc(workspace)");
+    keep_pool_memory();
+    check_cuda(cudaMallocAsync(&base, arena, c->st), "cudaMallocAsync(workspace)");
     c->owned.push_back(base);
     c->ws.base = static_cast<char *>(base);
     c->ws.size = arena;
     c->coef = c->dmalloc((size_t)3 * (n + 1));
     to_dev(*c, c->coef, coeffs, (size_t)3 * (n + 1));
     setup_eigs(*c);
+    TCTL_CUDA(cudaStreamSynchronize(c->st));
+    auto t_eig = std::chrono::steady_clock::now();
     setup_spectral(*c);
     TCTL_CUDA(cudaStreamSynchronize(c->st));
     auto t1 = std::chrono::steady_clock::now();
     c->stats.t_setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    if (c->trace)
+      std::fprintf(stderr, "[tctl] setup n=%d: eigenpairs %.1f ms, spectral sums + factors %.1f ms\n", n,
+                   std::chrono::duration<double, std::milli>(t_eig - t0).count(),
+                   std::chrono::duration<double, std::milli>(t1 - t_eig).count());
     c->stats.op_rank = c->op.R;
     c->stats.pre_rank = c->pre.R;
     for (int l = 0; l < 3; ++l) c->stats.op_basis[l] = c->op.rD[l];
@@ -266,19 +308,21 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
   }
 }
 
-static int apply_common(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, bool precond) {
+// which: 0 = F2(A), 1 = the preconditioner, 2 = A^-alpha (state)
+static int apply_common(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, int which) {
   Ctx *c = reinterpret_cast<Ctx *>(ctx);
   if (!c) return TCTL_E_ARG;
   try {
     check_cp(*c, x, "x", true);
     check_cp(*c, y, "y", false);
+    if (which == 2) ensure_state_sep(*c);
     size_t mk = c->ws.mark();
     Tucker tx, ty;
     tucker_alloc(*c, tx, kCap);
     tucker_alloc(*c, ty, kCap);
     const double e2 = c->eps / std::sqrt(2.0);
     cp_to_tucker(*c, x->rank, x->w, x->U, true, tx, 1e-12);
-    sep_apply_trunc(*c, precond ? c->pre : c->op, tx, ty, e2);
+    sep_apply_trunc(*c, which == 0 ? c->op : which == 1 ? c->pre : c->state, tx, ty, e2);
     const int s = tucker_to_cp(*c, ty, true, e2, y);
     c->ws.reset(mk);
     return s;
@@ -287,10 +331,26 @@ static int apply_common(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, bool precon
   }
 }
 
-int tctl_apply_op(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y) { return apply_common(ctx, x, y, false); }
+int tctl_apply_op(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y) { return apply_common(ctx, x, y, 0); }
 
 int tctl_apply_precond(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y) {
-  return apply_common(ctx, x, y, true);
+  return apply_common(ctx, x, y, 1);
+}
+
+int tctl_apply_state(tctl_ctx *ctx, const tctl_cp *u, tctl_cp *y) { return apply_common(ctx, u, y, 2); }
+
+int tctl_map_constants(double beta_p, double gamma, double *beta, double *u_scale) {
+  try {
+    if (!(beta_p > 0.0) || !(gamma > 0.0) || !std::isfinite(beta_p) || !std::isfinite(gamma))
+      fail(TCTL_E_ARG, "beta_p and gamma must be positive");
+    if (!beta || !u_scale) fail(TCTL_E_ARG, "NULL output");
+    // beta_p A^-alpha + (gamma / beta_p) A^alpha = beta_p (A^-alpha + (gamma / beta_p^2) A^alpha)
+    *beta = gamma / (beta_p * beta_p);
+    *u_scale = 1.0 / beta_p;
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(nullptr, e);
+  }
 }
 
 int tctl_truncate(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, double eps) {
@@ -357,9 +417,9 @@ int tctl_cp_alloc(tctl_ctx *ctx, int cap, tctl_cp *out) {
   for (int l = 0; l < 3; ++l) out->n[l] = c->n;
   out->cap = cap;
   if (cap == 0) return TCTL_OK;
-  if (cudaMalloc(&out->w, sizeof(double) * cap) != cudaSuccess) return TCTL_E_NOMEM;
+  if (cudaMallocAsync(&out->w, sizeof(double) * cap, c->st) != cudaSuccess) return TCTL_E_NOMEM;
   for (int l = 0; l < 3; ++l)
-    if (cudaMalloc(&out->U[l], sizeof(double) * cap * (size_t)c->n) != cudaSuccess) {
+    if (cudaMallocAsync(&out->U[l], sizeof(double) * cap * (size_t)c->n, c->st) != cudaSuccess) {
       tctl_cp_free(ctx, out);
       return TCTL_E_NOMEM;
     }
@@ -367,10 +427,12 @@ int tctl_cp_alloc(tctl_ctx *ctx, int cap, tctl_cp *out) {
 }
 
 void tctl_cp_free(tctl_ctx *ctx, tctl_cp *cp) {
-  (void)ctx;
   if (!cp) return;
-  cudaFree(cp->w);
-  for (int l = 0; l < 3; ++l) cudaFree(cp->U[l]);
+  // stream-ordered frees on the context's stream (no device-wide synchronisation)
+  const cudaStream_t st = ctx ? reinterpret_cast<Ctx *>(ctx)->st : cudaStreamPerThread;
+  if (cp->w) cudaFreeAsync(cp->w, st);
+  for (int l = 0; l < 3; ++l)
+    if (cp->U[l]) cudaFreeAsync(cp->U[l], st);
   cp->w = nullptr;
   cp->U[0] = cp->U[1] = cp->U[2] = nullptr;
   cp->rank = cp->cap = 0;
@@ -391,6 +453,8 @@ int tctl_get_eigs(tctl_ctx *ctx, int mode, double *lam, double *V) {
 int tctl_get_stats(tctl_ctx *ctx, tctl_stats *st) {
   Ctx *c = reinterpret_cast<Ctx *>(ctx);
   if (!c || !st) return TCTL_E_ARG;
+  c->stats.ws_peak_mb = (double)c->ws.peak / (1 << 20);
+  c->stats.ws_size_mb = (double)c->ws.size / (1 << 20);
   *st = c->stats;
   return TCTL_OK;
 }
@@ -428,6 +492,34 @@ int tctl_solve_host(const double *coeffs, int n, double alpha, double beta, doub
   tctl_cp_free(ctx, &x);
   tctl_destroy(ctx);
   return s;
+}
+
+int tctl_solve_batch(tctl_batch_item *items, int count, double eps_trunc, const tctl_opts *opts,
+                     int workers) {
+  if (count < 0 || (count > 0 && !items) || workers < 1) return TCTL_E_ARG;
+  // independent problems, dynamically scheduled over `workers` host threads; each
+  // thread's launches go to its own per-thread default stream, so the problems
+  // overlap on the device while every solve keeps its own host-side decisions
+  std::atomic<int> next{0};
+  auto run = [&]() {
+    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+      tctl_batch_item &it = items[i];
+      const auto t0 = std::chrono::steady_clock::now();
+      it.status = tctl_solve_host(it.coeffs, it.n, it.alpha, it.beta, eps_trunc, opts, it.yw, it.yU,
+                                  it.S, it.uw, it.uU, it.cap, &it.u_rank, it.st);
+      const auto t1 = std::chrono::steady_clock::now();
+      it.latency_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    }
+  };
+  const int nt = std::min(workers, std::max(count, 1));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(run);
+  run();
+  for (auto &th : pool) th.join();
+  int worst = TCTL_OK;
+  for (int i = 0; i < count; ++i)
+    if (items[i].status != TCTL_OK && worst == TCTL_OK) worst = items[i].status;
+  return worst;
 }
 
 int tctl_gemm(tctl_ctx *ctx, int digits, int trans_a, int trans_b, int m, int n, int k,
@@ -630,10 +722,12 @@ int tctl_profile_report(tctl_ctx *ctx, char *buf, int buflen) {
 void tctl_destroy(tctl_ctx *ctx) {
   Ctx *c = reinterpret_cast<Ctx *>(ctx);
   if (!c) return;
-  if (c->st) cudaStreamSynchronize(c->st);
-  else cudaDeviceSynchronize();
+  // the library is built with per-thread default streams: a NULL stream is the
+  // calling thread's, and nothing here synchronises the whole device
+  cudaStreamSynchronize(c->st);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
-  for (void *p : c->owned) cudaFree(p);
+  for (void *p : c->owned) cudaFreeAsync(p, c->st);
+  cudaStreamSynchronize(c->st);
   delete c;
 }
 

@@ -94,6 +94,13 @@ __device__ __forceinline__ int sturm_count(int n, const double *__restrict__ d,
   return cnt;
 }
 
+// Bisection brackets: with T = D^T diag(a) D / h^2 (a at the n + 1 half points;
+// the boundary ones recovered from the end rows of T), the Courant-Fischer
+// theorem gives a_min mu_k <= lambda_k <= a_max mu_k, mu_k = 4/h^2 sin^2(k pi h / 2)
+// the eigenvalues for a = 1. The bracket [0.99 a_min mu_k, 1.01 a_max mu_k] is
+// checked by two inertia counts and replaced by the Gershgorin interval if it
+// fails (or if a recovered coefficient is not positive); it saves the ~20
+// halvings that separate a small eigenvalue from the width of the spectrum.
 __global__ void bisect_kernel(int n, const double *d0, const double *d1, const double *d2,
                               const double *e0, const double *e1, const double *e2,
                               const double *bounds, double *l0, double *l1, double *l2) {
@@ -102,8 +109,40 @@ __global__ void bisect_kernel(int n, const double *d0, const double *d1, const d
   const double *e = l == 0 ? e0 : (l == 1 ? e1 : e2);
   double *lam = l == 0 ? l0 : (l == 1 ? l1 : l2);
   const double glo = bounds[4 * l], ghi = bounds[4 * l + 1], pivmin = bounds[4 * l + 2];
+  const double h = 1.0 / (n + 1), h2 = h * h;
+  __shared__ double s_min[64], s_max[64];
+  double amin = 1e300, amax = -1e300;
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+    double ai;
+    if (i == 0) ai = d[0] * h2 + (n > 1 ? e[0] * h2 : 0.0);
+    else if (i == n) ai = d[n - 1] * h2 + (n > 1 ? e[n - 2] * h2 : 0.0);
+    else ai = -e[i - 1] * h2;
+    amin = fmin(amin, ai);
+    amax = fmax(amax, ai);
+  }
+  s_min[threadIdx.x] = amin;
+  s_max[threadIdx.x] = amax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_min[threadIdx.x] = fmin(s_min[threadIdx.x], s_min[threadIdx.x + o]);
+      s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  amin = s_min[0];
+  amax = s_max[0];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     double lo = glo, hi = ghi;
+    if (amin > 0.0 && n > 1) {
+      const double sn = sin(0.5 * M_PI * h * (k + 1));
+      const double mu = 4.0 * sn * sn / h2;
+      const double blo = fmax(glo, 0.99 * amin * mu), bhi = fmin(ghi, 1.01 * amax * mu);
+      if (blo < bhi && sturm_count(n, d, e, blo, pivmin) <= k && sturm_count(n, d, e, bhi, pivmin) > k) {
+        lo = blo;
+        hi = bhi;
+      }
+    }
     // invariant: count(lo) <= k < count(hi)
     for (int it = 0; it < 200; ++it) {
       const double mid = 0.5 * (lo + hi);

@@ -35,7 +35,7 @@ void *Arena::alloc(size_t bytes) {
 
 double *Ctx::dmalloc(size_t count) {
   void *p = nullptr;
-  check_cuda(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(double)), "cudaMalloc");
+  check_cuda(cudaMallocAsync(&p, std::max<size_t>(count, 1) * sizeof(double), st), "cudaMallocAsync");
   owned.push_back(p);
   return static_cast<double *>(p);
 }

@@ -34,6 +34,8 @@
 // product of three diagonal matrices in the eigenbasis; the factor matrices
 // E_l[i, k] = (lambda_i^(l) or 1) * exp(-t_k lambda_i^(l)) are built on the GPU.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <numeric>
 
@@ -186,7 +188,11 @@ std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::
 
 // The fitted function: g = F2/s for alpha < 1 (F2 ~ s g); for alpha = 1 the
 // positive power is exactly beta s and g = 1/s (F2 ~ g + beta s).
+// beta = kStateFn selects the state operator's symbol s^-alpha itself (no
+// positive power, approximated without the factor s).
+constexpr double kStateFn = -1.0;
 double g_of_s(double s, double a, double b) {
+  if (b == kStateFn) return std::pow(s, -a);
   return a >= 1.0 ? 1.0 / s : std::pow(s, -1.0 - a) + b * std::pow(s, a - 1.0);
 }
 
@@ -202,8 +208,8 @@ double measure_F2_fit(const ExpFit &f, double a, double b, double smin, double s
     const double s = std::exp(std::log(smin) + (std::log(smax) - std::log(smin)) * j / (M - 1));
     double v = 0;
     for (size_t k = 0; k < f.t.size(); ++k) v += f.w[k] * std::exp(-f.t[k] * s);
-    const double ex = F2h(s, a, b);
-    const double ap = a >= 1.0 ? v + b * s : s * v;
+    const double ex = b == kStateFn ? std::pow(s, -a) : F2h(s, a, b);
+    const double ap = b == kStateFn ? v : (a >= 1.0 ? v + b * s : s * v);
     emax = std::max(emax, std::fabs(ap - ex) / ex);
   }
   return emax;
@@ -244,15 +250,18 @@ ExpFit fit_g(double a, double b, double smin, double smax, int r, double lo, dou
 }
 
 // Smallest fitted sum (to a few nodes) with measured error <= tol: nodes in
-// [0.1/s_max, 20/s_min]; r starts at 40 and is then set from the observed
-// rate of about a decade per 5 nodes, raised by 3 until the fit passes.
+// [0.1/s_max, 20/s_min]; r starts at 2.5 ln(s_max / s_min) (16..40) and is then
+// set from the observed rate of about a decade per 5 nodes, raised by 3 until
+// the fit passes. (Starting low matters on short intervals: there, dense nodes
+// make the basis so collinear that more nodes can fit worse.)
 ExpFit fit_F2(double a, double b, double smin, double smax, double tol) {
-  constexpr int r0 = 40, rmax = 96;
+  constexpr int rmax = 96;
   constexpr double lo = 0.1, hi = 20.0;
+  const int r0 = std::max(16, std::min(40, (int)std::lround(2.5 * std::log(smax / smin))));
   ExpFit best = fit_g(a, b, smin, smax, r0, lo, hi);
   if (best.err <= tol) return best;
-  int r = r0 + (int)std::ceil(5.0 * std::log10(best.err / tol));
-  for (int attempt = 0; attempt < 8 && r <= rmax; ++attempt, r += 3) {
+  int r = r0 + std::max(3, (int)std::ceil(5.0 * std::log10(best.err / tol)));
+  for (int attempt = 0; attempt < 10 && r <= rmax; ++attempt, r += 3) {
     ExpFit f = fit_g(a, b, smin, smax, r, lo, hi);
     if (f.err <= tol) return f;
     if (f.err < best.err) best = f;
@@ -427,6 +436,10 @@ int expsum_fit_host(double a, double b, double smin, double smax, double tol, do
 
 void setup_spectral(Ctx &c) {
   const double a = c.alpha, b = c.beta, smin = c.s_min, smax = c.s_max;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto ms = [&]() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  };
   const double delta = c.o.op_tol;
   // ---- operator F2 (term order as in the canonical factor layout)
   std::vector<double> w;
@@ -512,8 +525,10 @@ void setup_spectral(Ctx &c) {
     c.op_terms_t.push_back(d.t);
     c.op_terms_m.push_back(d.lam_mode);
   }
+  const double t_fit = ms();
   build_sep(c, c.op, w, td);
   compress_sep(c, c.op, 1e-13);
+  const double t_op = ms();
 
   // ---- preconditioner P(s) = s sum_k p_k exp(-theta_k s), NNLS weights
   const int K = std::max(1, c.o.r_pre);
@@ -595,6 +610,24 @@ void setup_spectral(Ctx &c) {
   }
   build_sep(c, c.pre, pw, ptd);
   compress_sep(c, c.pre, 1e-13);
+  if (c.trace)
+    std::fprintf(stderr, "[tctl] spectral: F2 fit %.1f ms, operator factors %.1f ms, preconditioner %.1f ms\n",
+                 t_fit, t_op - t_fit, ms() - t_op);
+}
+
+// State operator A^-alpha (state equation of Section 3.1, y = A^-alpha u): the
+// fitted exponential sum of s^-alpha (completely monotone), one Kronecker term
+// per node; built on first use.
+void ensure_state_sep(Ctx &c) {
+  if (c.state.R > 0) return;
+  const ExpFit f = fit_F2(c.alpha, kStateFn, c.s_min, c.s_max, c.o.op_tol);
+  if (!(f.err <= c.o.op_tol)) fail(TCTL_E_NUMERIC, "state operator: exponential sum misses op_tol");
+  std::vector<double> w(f.w);
+  std::vector<TermDesc> td;
+  for (double t : f.t) td.push_back({t, -1});
+  build_sep(c, c.state, w, td);
+  compress_sep(c, c.state, 1e-13);
+  c.state_rel_err = f.err;
 }
 
 // ------------------------------------------------------------------ full grid

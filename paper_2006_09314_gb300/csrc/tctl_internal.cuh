@@ -83,6 +83,8 @@ struct Ctx {
   Sep op, pre;
   double op_rel_err = 0;
   int expsum_used = 0;                     // 0 sinc, 1 fitted
+  Sep state;                               // A^-alpha (state equation), built on first use
+  double state_rel_err = 0;
   int pre_used = 0;                        // preconditioner: 0 K-node NNLS, 1 fitted, 2 learned
   double pre_delta = 0;                    // its measured max |P F2 - 1|
   std::vector<double> op_terms_w, op_terms_t, pre_terms_w, pre_terms_t;  // host copies
@@ -248,6 +250,7 @@ void mlp_grad_host(int r, int B, const float *params, const float *X, const floa
 void mlp_forward_host(int r, int n, const float *model, const float *X, float *Yout, cudaStream_t st);
 // Lawson-Hanson NNLS, A M x K column-major.
 std::vector<double> nnls_solve(const std::vector<double> &A, int M, int K, const std::vector<double> &b);
+void ensure_state_sep(Ctx &c);
 void setup_spectral(Ctx &c);
 void fullgrid_apply(Ctx &c, const double *y, double *u, int which);
 

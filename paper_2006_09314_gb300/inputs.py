@@ -36,6 +36,7 @@ __all__ = [
     "sine_factors",
     "CONFIGS",
     "problem_seed",
+    "batch_problems",
 ]
 
 
@@ -109,3 +110,17 @@ CONFIGS = {
     # precision: full grid n = 512 and rank-structured n = 2048
     2: dict(n=[512, 2048], alpha=[0.5], beta=[1e-2], rank=5, eps=1e-6),
 }
+
+
+def batch_problems(count: int, seed: int, n_choices=tuple(range(64, 513, 32))):
+    """Uneven batch (f-2 workload): n uniform in n_choices, design rank uniform in
+    1..8, alpha ~ U[0.2, 0.8], log10 beta ~ U[-4, 0]; problem i from seed + i."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = int(rng.choice(n_choices))
+        rank = int(rng.integers(1, 9))
+        alpha = float(rng.uniform(0.2, 0.8))
+        beta = float(10.0 ** rng.uniform(-4.0, 0.0))
+        out.append(make_problem(n, alpha, beta, rank, seed + 1 + i))
+    return out

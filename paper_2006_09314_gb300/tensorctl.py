@@ -37,6 +37,7 @@ EXPORTED = [
     "tctl_profile_enable", "tctl_profile_report", "tctl_eig1d_noalloc", "tctl_get_expsum",
     "tctl_expsum_fit", "tctl_gemm", "tctl_precond_fit", "tctl_precond_dataset",
     "tctl_mlp_model_size", "tctl_mlp_train", "tctl_mlp_grad", "tctl_mlp_forward",
+    "tctl_apply_state", "tctl_map_constants", "tctl_solve_batch",
 ]
 
 ERRORS = {0: "OK", -1: "E_ARG", -2: "E_COEFF", -3: "E_CUDA", -4: "E_NOMEM",
@@ -54,6 +55,14 @@ class _CP(ctypes.Structure):
                 ("w", ctypes.c_void_p), ("U", ctypes.c_void_p * 3)]
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("coeffs", ctypes.c_void_p), ("n", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("yw", ctypes.c_void_p), ("yU", ctypes.c_void_p),
+                ("S", ctypes.c_int), ("uw", ctypes.c_void_p), ("uU", ctypes.c_void_p),
+                ("cap", ctypes.c_int), ("st", ctypes.c_void_p), ("u_rank", ctypes.c_int),
+                ("status", ctypes.c_int), ("latency_ms", ctypes.c_double)]
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("pcg_rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("op_tol", ctypes.c_double), ("r_pre", ctypes.c_int),
@@ -62,7 +71,8 @@ class Opts(ctypes.Structure):
                 ("paper_end_rows", ctypes.c_int), ("eps_final", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("range_tol", ctypes.c_double),
                 ("tc_gemm", ctypes.c_int), ("pre_src", ctypes.c_int), ("pre_r", ctypes.c_int),
-                ("pre_model", ctypes.c_void_p), ("pre_delta_max", ctypes.c_double)]
+                ("pre_model", ctypes.c_void_p), ("pre_delta_max", ctypes.c_double),
+                ("workspace_mb", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -73,7 +83,8 @@ class Stats(ctypes.Structure):
                 ("s_min", ctypes.c_double), ("s_max", ctypes.c_double),
                 ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
                 ("expsum_used", ctypes.c_int), ("pre_used", ctypes.c_int),
-                ("pre_delta", ctypes.c_double)]
+                ("pre_delta", ctypes.c_double), ("ws_peak_mb", ctypes.c_double),
+                ("ws_size_mb", ctypes.c_double)]
 
     def as_dict(self):
         out = {}
@@ -131,6 +142,9 @@ def load(build_if_missing: bool = True):
         "tctl_mlp_train": (I, [I, I, P, P, I, I, ctypes.c_float, ctypes.c_ulonglong, P, P]),
         "tctl_mlp_grad": (I, [I, I, P, P, P, P, P]),
         "tctl_mlp_forward": (I, [I, I, P, P, P]),
+        "tctl_apply_state": (I, [P, PCP, PCP]),
+        "tctl_map_constants": (I, [D, D, P, P]),
+        "tctl_solve_batch": (I, [P, I, D, P, I]),
         "tctl_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -235,6 +249,56 @@ def tctl_apply_op(ctx, x: CP, cap=4096) -> CP:
 
 def tctl_apply_precond(ctx, x: CP, cap=4096) -> CP:
     return _apply(load().tctl_apply_precond, ctx, x, cap)
+
+
+def tctl_apply_state(ctx, u: CP, cap=4096) -> CP:
+    """y = trunc(A^-alpha u) (state recovery)."""
+    return _apply(load().tctl_apply_state, ctx, u, cap)
+
+
+def tctl_solve_batch(problems, eps_trunc, opts=None, workers=8, cap=4096):
+    """Solve independent problems concurrently (host buffers).
+
+    problems: list of dicts with coeffs (3, n+1), n, alpha, beta, yw (S,), yU (3 arrays n x S).
+    Returns a list of dicts: uw, uU (list of 3 n x rank), status, latency_ms, stats.
+    """
+    import numpy as np
+    keep = []
+    items = (_BatchItem * len(problems))()
+    stats = [Stats() for _ in problems]
+    outs = []
+    for i, p in enumerate(problems):
+        n = int(p["n"])
+        co = np.ascontiguousarray(p["coeffs"], np.float64)
+        yw = np.ascontiguousarray(p["yw"], np.float64)
+        S = yw.size
+        yU = np.ascontiguousarray(np.stack([np.asarray(u, np.float64) for u in p["yU"]])
+                                  .transpose(0, 2, 1))  # (3, S, n): column-major n x S per mode
+        uw = np.zeros(cap)
+        uU = np.zeros((3, cap, n))
+        keep += [co, yw, yU, uw, uU]
+        it = items[i]
+        it.coeffs, it.n, it.alpha, it.beta = co.ctypes.data, n, float(p["alpha"]), float(p["beta"])
+        it.yw, it.yU, it.S = yw.ctypes.data, yU.ctypes.data, S
+        it.uw, it.uU, it.cap = uw.ctypes.data, uU.ctypes.data, cap
+        it.st = ctypes.addressof(stats[i])
+        outs.append((uw, uU))
+    load().tctl_solve_batch(items, len(problems), eps_trunc,
+                            ctypes.byref(opts) if opts is not None else None, workers)
+    res = []
+    for i, (uw, uU) in enumerate(outs):
+        r = items[i].u_rank
+        res.append({"uw": uw[:r].copy(), "uU": [uU[l, :r, :].T.copy() for l in range(3)],
+                    "status": items[i].status, "latency_ms": items[i].latency_ms,
+                    "stats": stats[i].as_dict()})
+    return res
+
+
+def tctl_map_constants(beta_p, gamma):
+    """(beta, u_scale) of the paper's (beta_p, gamma) form."""
+    b, sc = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().tctl_map_constants(beta_p, gamma, ctypes.byref(b), ctypes.byref(sc)))
+    return b.value, sc.value
 
 
 def tctl_truncate(ctx, x: CP, eps, cap=4096) -> CP:
@@ -477,6 +541,9 @@ class Context:
 
     def apply_precond(self, x, cap=4096):
         return tctl_apply_precond(self.handle, x, cap)
+
+    def apply_state(self, u, cap=4096):
+        return tctl_apply_state(self.handle, u, cap)
 
     def truncate(self, x, eps, cap=4096):
         return tctl_truncate(self.handle, x, eps, cap)

@@ -58,3 +58,15 @@ def test_inputs_generator_is_seeded():
     b = make_problem(16, 0.5, 1e-2, 3, 5)
     assert np.array_equal(a.coeffs, b.coeffs) and all(np.array_equal(x, y) for x, y in zip(a.yU, b.yU))
     assert a.coeffs.min() >= 0.5 - 1e-15 and a.coeffs.max() <= 1.5 + 1e-15
+
+
+def test_map_constants_without_gpu():
+    """(beta_p, gamma) of Section 3.1 -> beta = gamma / beta_p^2, u_paper = u / beta_p."""
+    from paper_2006_09314_gb300 import tensorctl as T
+    b, sc = T.tctl_map_constants(2.0, 0.5)
+    assert b == 0.125 and sc == 0.5
+    b, sc = T.tctl_map_constants(1.0, 1e-2)
+    assert b == 1e-2 and sc == 1.0
+    import pytest
+    with pytest.raises(T.TctlError):
+        T.tctl_map_constants(0.0, 1.0)

@@ -202,6 +202,18 @@ def test_fitted_operator_on_the_spectrum(n, alpha, beta):
     assert np.linalg.norm(_full_from_gpu(y) - exact) <= 1.2e-6 * np.linalg.norm(exact)
 
 
+@pytest.mark.parametrize("n,alpha", [(32, 0.5), (29, 0.25), (24, 0.75), (20, 1.0)])
+def test_apply_state_matches_oracle(n, alpha):
+    """State recovery y = A^-alpha u (canonical) against the oracle's full-grid state."""
+    pr = make_problem(n, alpha, 1e-2, 3, 700 + n)
+    lams, Vs = _oracle_eigs(pr)
+    U = F.cp_full(pr.yw, pr.yU)
+    exact = fg.state_exact(U, lams, Vs, alpha)
+    with T.Context(pr.coeffs, n, alpha, 1e-2, 1e-6) as ctx:
+        y = ctx.apply_state(T.CP.from_numpy(pr.yw, pr.yU))
+    assert np.linalg.norm(_full_from_gpu(y) - exact) <= 1.2e-6 * np.linalg.norm(exact)
+
+
 @pytest.mark.parametrize("n,alpha,beta", [(32, 0.5, 1e-2), (27, 0.75, 1.0)])
 def test_apply_precond_matches_oracle(n, alpha, beta):
     pr = make_problem(n, alpha, beta, 3, 600 + n)
@@ -280,6 +292,20 @@ def test_solve_host_buffers():
 
 
 # ------------------------------------------------------------------ edge cases
+def test_solve_batch_uneven_problems():
+    """tctl_solve_batch: problems of different n, rank, alpha, beta against the oracle."""
+    from paper_2006_09314_gb300.inputs import batch_problems
+    probs = batch_problems(6, 4242, n_choices=(16, 24, 32, 40))
+    res = T.tctl_solve_batch([dict(coeffs=p.coeffs, n=p.n, alpha=p.alpha, beta=p.beta, yw=p.yw,
+                                   yU=p.yU) for p in probs], 1e-6, workers=4)
+    for p, r in zip(probs, res):
+        assert r["status"] == 0 and r["latency_ms"] > 0
+        lams, Vs = _oracle_eigs(p)
+        ustar = fg.solve_exact(F.cp_full(p.yw, p.yU), lams, Vs, p.alpha, p.beta)
+        u = F.cp_full(r["uw"], r["uU"])
+        assert np.linalg.norm(u - ustar) <= 1e-5 * np.linalg.norm(ustar)
+
+
 def test_edge_cases_and_errors():
     n = 12
     pr = make_problem(n, 0.5, 1e-2, 2, 17)
