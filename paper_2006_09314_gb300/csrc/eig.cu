@@ -17,6 +17,8 @@
 //     the sign).
 // Eigenvalues are ascending; V_l is column-major with eigenvectors as columns.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
 #include <cfloat>
 #include <cmath>
 #include <mutex>
@@ -240,8 +242,17 @@ void setup_eigs(Ctx &c) {
   double *bounds = c.ws.dbl(12);
   LAUNCH(c, gersh_kernel, 3, 256, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds);
   dim3 gb((n + 63) / 64, 3);
-  LAUNCH(c, bisect_kernel, gb, 64, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds,
+  // one warp per block spreads the 3n eigenvalues over all SMs (the inertia
+  // counts are bound by the FP64 pipe of the SMs they run on)
+  dim3 gbis((n + 31) / 32, 3);
+  const auto tb0 = std::chrono::steady_clock::now();
+  LAUNCH(c, bisect_kernel, gbis, 32, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds,
          c.lam[0], c.lam[1], c.lam[2]);
+  if (c.trace) {
+    TCTL_CUDA(cudaStreamSynchronize(c.st));
+    std::fprintf(stderr, "[tctl] bisection %.1f ms\n",
+                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tb0).count());
+  }
   double *Dp = c.ws.dbl((size_t)3 * n * n);
   double *Um = c.ws.dbl((size_t)3 * n * n);
   LAUNCH(c, twisted_kernel, gb, 64, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds,
