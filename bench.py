@@ -450,7 +450,8 @@ def variants_section(args, T, probs, streams, bs, master, ref_sols, batch_runner
     default (fitted sums, tensor-core contractions) with an r = 12 preconditioner
     predicted by a network trained here on the library's own fitted sums;
     fitted_pre: the same with the r = 12 sum fitted at set-up (what a perfect
-    network would give).
+    network would give); aniso_pre: the paper's case (A) preconditioner, 1/F2
+    of the anisotropic constant-coefficient Laplacian in its sine basis.
     Error bound of each solve: the main run's oracle error (checked) plus the
     canonical-format distance to the main run's solution (exact inner products).
     """
@@ -467,7 +468,8 @@ def variants_section(args, T, probs, streams, bs, master, ref_sols, batch_runner
     forms = [("fp64_sinc", dict(expsum_src=0, tc_gemm=0)),
              ("fp64_fitted", dict(expsum_src=1, tc_gemm=0)),
              ("learned_pre", dict(pre_src=2, pre_r=r, pre_model=model.ctypes.data, pre_delta_max=0.25)),
-             ("fitted_pre", dict(pre_src=1, pre_r=r, pre_delta_max=0.25))]
+             ("fitted_pre", dict(pre_src=1, pre_r=r, pre_delta_max=0.25)),
+             ("aniso_pre", dict(pre_src=3))]
     ref = [x.to_numpy() for x in ref_sols]
     for name, kw in forms:
         cs = [T.Context(p.coeffs, n, p.alpha, p.beta, EPS, opts=T.tctl_default_opts(**kw),

@@ -96,7 +96,11 @@ typedef struct {
                          nodes fitted at set-up (tctl_precond_fit); 2 = nodes predicted by a
                          trained network (pre_model, tctl_mlp_train), weights re-solved
                          by NNLS. 1 and 2 are used only if their measured
-                         delta = max |P F2 - 1| <= pre_delta_max, else 0 is used.      */
+                         delta = max |P F2 - 1| <= pre_delta_max, else 0 is used.
+                         3 = case (A) of Section 3.5: 1/F2 of the anisotropic
+                         constant-coefficient Laplacian B0 = sum_l b0_l Delta_l,
+                         b0_l = (max a_l + min a_l)/2, applied in its sine basis
+                         (W_l = S^T V_l, 3 n^2 doubles); r_pre nodes, NNLS weights.    */
   int pre_r;          /* terms of pre_src 1 / 2 (default 12; the network's r)          */
   const float *pre_model; /* HOST model blob of tctl_mlp_train (pre_src 2)              */
   double pre_delta_max;   /* acceptance bound of pre_src 1 / 2 (default 0.25)           */

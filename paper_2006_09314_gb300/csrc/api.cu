@@ -63,15 +63,20 @@ struct Timer {
 
 // fun / precond of Algorithm 1 on Tucker vectors; in the paper form (basis 0)
 // the vectors are in grid coordinates and every apply goes through V_l^T / V_l.
+// The anisotropic-Laplacian preconditioner (pre_src 3) is diagonal in the sine
+// basis: its factors move there (W_l = S^T V_l) and back around the Hadamard step.
 void apply_sep(Ctx &c, const Sep &D, const Tucker &x, Tucker &y, Tucker &tmp, double eps) {
-  if (c.o.basis == 1) {
+  const bool sine = (&D == &c.pre) && c.pre_used == 3;
+  if (c.o.basis == 1 && !sine) {
     sep_apply_trunc(c, D, x, y, eps);
-  } else {
-    tucker_copy(c, x, tmp);
-    tucker_basis_change(c, tmp, true);
-    sep_apply_trunc(c, D, tmp, y, eps);
-    tucker_basis_change(c, y, false);
+    return;
   }
+  tucker_copy(c, x, tmp);
+  if (c.o.basis == 0) tucker_basis_change(c, tmp, true);
+  if (sine) tucker_factor_change(c, tmp, c.W, false);
+  sep_apply_trunc(c, D, tmp, y, eps);
+  if (sine) tucker_factor_change(c, y, c.W, true);
+  if (c.o.basis == 0) tucker_basis_change(c, y, false);
 }
 
 }  // namespace
@@ -251,8 +256,9 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
     if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
     if (c->o.tc_gemm != 0 && c->o.tc_gemm != 1) fail(TCTL_E_ARG, "tc_gemm must be 0 or 1");
     if (c->o.workspace_mb < 0) fail(TCTL_E_ARG, "workspace_mb must be >= 0");
-    if (c->o.pre_src < 0 || c->o.pre_src > 2) fail(TCTL_E_ARG, "pre_src must be 0, 1 or 2");
-    if (c->o.pre_src && (c->o.pre_r < 2 || c->o.pre_r > kPreRMax)) fail(TCTL_E_ARG, "pre_r must be in [2, 32]");
+    if (c->o.pre_src < 0 || c->o.pre_src > 3) fail(TCTL_E_ARG, "pre_src must be 0, 1, 2 or 3");
+    if ((c->o.pre_src == 1 || c->o.pre_src == 2) && (c->o.pre_r < 2 || c->o.pre_r > kPreRMax))
+      fail(TCTL_E_ARG, "pre_r must be in [2, 32]");
     if (c->o.pre_src == 2 && !c->o.pre_model) fail(TCTL_E_ARG, "pre_src 2 needs pre_model");
     if (!(c->o.range_tol >= 0.0 && c->o.range_tol <= 1.0))
       fail(TCTL_E_ARG, "range_tol must lie in [0, 1]");
@@ -278,6 +284,7 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
     c->ws.base = static_cast<char *>(base);
     c->ws.size = arena;
     c->coef = c->dmalloc((size_t)3 * (n + 1));
+    c->coef_host.assign(coeffs, coeffs + 3 * (size_t)(n + 1));
     to_dev(*c, c->coef, coeffs, (size_t)3 * (n + 1));
     setup_eigs(*c);
     TCTL_CUDA(cudaStreamSynchronize(c->st));

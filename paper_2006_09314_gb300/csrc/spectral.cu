@@ -290,7 +290,8 @@ __global__ void factors_kernel(int n, int R, const double *__restrict__ lam,
   }
 }
 
-void build_sep(Ctx &c, Sep &D, const std::vector<double> &w, const std::vector<TermDesc> &td) {
+void build_sep(Ctx &c, Sep &D, const std::vector<double> &w, const std::vector<TermDesc> &td,
+               double *const *lam_override = nullptr) {
   const int n = c.n;
   D.R = (int)w.size();
   D.w_host = w;
@@ -317,7 +318,8 @@ void build_sep(Ctx &c, Sep &D, const std::vector<double> &w, const std::vector<T
   for (int l = 0; l < 3; ++l) {
     D.E[l] = c.dmalloc((size_t)n * D.R);
     const int blocks = (int)std::min<long long>(((long long)n * D.R + 255) / 256, 4096);
-    LAUNCH(c, factors_kernel, blocks, 256, 0, n, D.R, c.lam[l], td_t, td_m, l, D.E[l]);
+    LAUNCH(c, factors_kernel, blocks, 256, 0, n, D.R, lam_override ? lam_override[l] : c.lam[l], td_t,
+           td_m, l, D.E[l]);
     col_norms(c, n, D.R, D.E[l], n, nrm);
     to_host(c, nh.data(), nrm, D.R);
     for (int k = 0; k < D.R; ++k) {
@@ -415,6 +417,27 @@ void compress_sep(Ctx &c, Sep &D, double tol) {
 }
 
 }  // namespace
+
+// S[i + j n] = sqrt(2 / (n + 1)) sin((i + 1)(j + 1) pi / (n + 1)): the orthonormal
+// eigenvectors of every constant-coefficient Dirichlet FD Laplacian (symmetric, S^2 = I)
+__global__ void sine_basis_kernel(int n, double *S) {
+  const long long total = (long long)n * n;
+  const double c = sqrt(2.0 / (n + 1));
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t % n, j = t / n;
+    const long long m = ((i + 1) * (j + 1)) % (2 * (n + 1));  // exact argument reduction
+    S[t] = c * sinpi((double)m / (double)(n + 1));
+  }
+}
+
+__global__ void scaled_laplacian_eigs_kernel(int n, double b0, double *lam) {
+  const double h = 1.0 / (n + 1);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const double s = sinpi(0.5 * h * (k + 1));
+    lam[k] = b0 * 4.0 * s * s / (h * h);
+  }
+}
 
 std::vector<double> nnls_solve(const std::vector<double> &A, int M, int K, const std::vector<double> &b) {
   return nnls(A, M, K, b);
@@ -531,13 +554,41 @@ void setup_spectral(Ctx &c) {
   const double t_op = ms();
 
   // ---- preconditioner P(s) = s sum_k p_k exp(-theta_k s), NNLS weights
+  // pre_src 3 (case (A) of Section 3.5): the anisotropic constant-coefficient
+  // Laplacian B0 = sum_l b0_l Delta_l, b0_l = (max a_l + min a_l) / 2, whose
+  // eigenbasis is the sine basis: P ~ 1/F2 on its spectrum, applied there.
+  double psmin = smin, psmax = smax;
+  if (c.o.pre_src == 3) {
+    const int n = c.n;
+    size_t mks = c.ws.mark();
+    double *S = c.ws.dbl((size_t)n * n);
+    const int blocks = (int)std::min<long long>(((long long)n * n + 255) / 256, 4096);
+    LAUNCH(c, sine_basis_kernel, blocks, 256, 0, n, S);
+    double mu1 = 0, mun = 0;
+    for (int l = 0; l < 3; ++l) {
+      const double *al = c.coef_host.data() + (size_t)l * (n + 1);
+      const double amax = *std::max_element(al, al + n + 1), amin = *std::min_element(al, al + n + 1);
+      c.b0[l] = 0.5 * (amax + amin);
+      c.lamB[l] = c.dmalloc(n);
+      LAUNCH(c, scaled_laplacian_eigs_kernel, (n + 255) / 256, 256, 0, n, c.b0[l], c.lamB[l]);
+      c.W[l] = c.dmalloc((size_t)n * n);
+      // W_l = S^T V_l (S symmetric): FP64 for the basis change of the preconditioner
+      gemm(c, true, false, n, n, n, 1.0, S, n, 0, c.V[l], n, 0, 0.0, c.W[l], n, 0);
+      const double h = 1.0 / (n + 1);
+      mu1 += c.b0[l] * 4.0 * std::pow(std::sin(0.5 * M_PI * h), 2) / (h * h);
+      mun += c.b0[l] * 4.0 * std::pow(std::sin(0.5 * M_PI * h * n), 2) / (h * h);
+    }
+    c.ws.reset(mks);
+    psmin = mu1;
+    psmax = mun;
+  }
   const int K = std::max(1, c.o.r_pre);
   std::vector<double> theta(K), smp(kPreSamples);
   for (int k = 0; k < K; ++k)
-    theta[k] = std::exp(std::log(0.05 / smax) +
-                        (K == 1 ? 0.0 : (std::log(20.0 / smin) - std::log(0.05 / smax)) * k / (K - 1)));
+    theta[k] = std::exp(std::log(0.05 / psmax) +
+                        (K == 1 ? 0.0 : (std::log(20.0 / psmin) - std::log(0.05 / psmax)) * k / (K - 1)));
   for (int j = 0; j < kPreSamples; ++j)
-    smp[j] = std::exp(std::log(smin) + (std::log(smax) - std::log(smin)) * j / (kPreSamples - 1));
+    smp[j] = std::exp(std::log(psmin) + (std::log(psmax) - std::log(psmin)) * j / (kPreSamples - 1));
   std::vector<double> A((size_t)kPreSamples * K), cs(K, 0.0), rhs(kPreSamples, 1.0);
   for (int k = 0; k < K; ++k) {
     double nrm = 0;
@@ -554,8 +605,8 @@ void setup_spectral(Ctx &c) {
   // alternatives with r free nodes: fitted at set-up (pre_src 1) or predicted by the
   // trained network (pre_src 2, weights re-solved on its nodes); each is measured and
   // replaces the K-node NNLS sum only if its delta = max |P F2 - 1| <= pre_delta_max
-  c.pre_used = 0;
-  c.pre_delta = pre_delta(theta.data(), p.data(), K, a, b, smin, smax);
+  c.pre_used = c.o.pre_src == 3 ? 3 : 0;
+  c.pre_delta = pre_delta(theta.data(), p.data(), K, a, b, psmin, psmax);
   if (c.o.pre_src == 1 || c.o.pre_src == 2) {
     const int r = c.o.pre_r;
     std::vector<double> th(r), pr(r);
@@ -608,7 +659,7 @@ void setup_spectral(Ctx &c) {
     c.pre_terms_t.push_back(d.t);
     c.pre_terms_m.push_back(d.lam_mode);
   }
-  build_sep(c, c.pre, pw, ptd);
+  build_sep(c, c.pre, pw, ptd, c.o.pre_src == 3 ? c.lamB : nullptr);
   compress_sep(c, c.pre, 1e-13);
   if (c.trace)
     std::fprintf(stderr, "[tctl] spectral: F2 fit %.1f ms, operator factors %.1f ms, preconditioner %.1f ms\n",

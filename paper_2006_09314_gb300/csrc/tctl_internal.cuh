@@ -85,7 +85,11 @@ struct Ctx {
   int expsum_used = 0;                     // 0 sinc, 1 fitted
   Sep state;                               // A^-alpha (state equation), built on first use
   double state_rel_err = 0;
-  int pre_used = 0;                        // preconditioner: 0 K-node NNLS, 1 fitted, 2 learned
+  int pre_used = 0;                        // preconditioner: 0 K-node NNLS, 1 fitted, 2 learned, 3 anisotropic
+  double *W[3] = {nullptr, nullptr, nullptr};  // pre_src 3: W_l = S^T V_l (sine basis <- eigenbasis)
+  double *lamB[3] = {nullptr, nullptr, nullptr};  // pre_src 3: b0_l mu_k
+  double b0[3] = {0, 0, 0};
+  std::vector<double> coef_host;          // 3 x (n + 1) coefficients
   double pre_delta = 0;                    // its measured max |P F2 - 1|
   std::vector<double> op_terms_w, op_terms_t, pre_terms_w, pre_terms_t;  // host copies
   std::vector<int> op_terms_m, pre_terms_m;
@@ -280,6 +284,8 @@ double tucker_inner(Ctx &c, const Tucker &x, const Tucker &y);
 void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps);
 // Apply V_l (from_eig) or V_l^T (to_eig) to the Tucker factors in place.
 void tucker_basis_change(Ctx &c, Tucker &x, bool to_eig);
+// Q_l <- M_l^T Q_l (transpose) or M_l Q_l for n x n matrices M_l.
+void tucker_factor_change(Ctx &c, Tucker &x, double *const M[3], bool transpose);
 
 // Records the message returned by tctl_last_error(NULL) (entry points without a context).
 void set_noalloc_error(const std::string &msg);

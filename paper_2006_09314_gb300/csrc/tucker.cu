@@ -370,12 +370,17 @@ void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucke
 }
 
 void tucker_basis_change(Ctx &c, Tucker &x, bool to_eig) {
+  tucker_factor_change(c, x, c.V, to_eig);
+}
+
+// Q_l <- M_l^T Q_l (transpose) or M_l Q_l; orthogonal M_l keep Q_l orthonormal.
+void tucker_factor_change(Ctx &c, Tucker &x, double *const M[3], bool transpose) {
   const int n = c.n;
   size_t mk = c.ws.mark();
   double *t = c.ws.dbl((size_t)n * kMaxRank);
   for (int l = 0; l < 3; ++l) {
     if (!x.r[l]) continue;
-    gemm(c, to_eig, false, n, x.r[l], n, 1.0, c.V[l], n, 0, x.Q[l], n, 0, 0.0, t, n, 0);
+    gemm(c, transpose, false, n, x.r[l], n, 1.0, M[l], n, 0, x.Q[l], n, 0, 0.0, t, n, 0);
     copy_d(c, x.Q[l], t, (size_t)n * x.r[l]);
   }
   c.ws.reset(mk);
