@@ -20,19 +20,25 @@
 // maxima (an element far below its row or column maximum keeps fewer digits;
 // the bound on the error of a product is 2^-35 n relative, 1.5e-8 at n = 512).
 //
-// Kernel structure: one CTA (8 warps) computes a 128 x 128 tile of C (M = rows
-// of W, N = 128 consecutive j), K in 32-deep stages, two shared-memory
-// buffers of 80 KB. The W digits (precomputed in the tile layout, 40 KB per stage) are
-// brought in by the bulk-copy engine (cp.async.bulk, completion counted on an
-// mbarrier); the X values of the next stage are loaded into registers while
-// the current stage's X digits are cut from FP32 bits with integer operations
-// and written to shared memory in the SWIZZLE_NONE K-major core-matrix layout
-// (8 rows x 16 bytes; K-direction core stride 128 B, 8-row-group stride 512 B).
-// One thread issues the tcgen05.mma instructions and commits them to the
-// buffer's mbarrier, which gates the reuse of the buffer; the
-// epilogue reads both accumulators with tcgen05.ld, scales, optionally divides
-// by F2(lambda_i + lambda_j + lambda_k) (the spectral divide of the last
-// forward product), and stores FP32. Every mbarrier wait is bounded; on
+// Kernel structure: one CTA (8 warps) per SM computes a 128 x 128 tile of C
+// (M = rows of W, N = 128 consecutive j) with K in 16-deep stages, four
+// shared-memory stages of 40 KB. The digit planes of W (built once per
+// context) and of X (cut once per mode product by x_digits_kernel) are stored
+// in the tile layout, so one stage is two bulk copies (cp.async.bulk, completion
+// counted on the stage's mbarrier) issued by one producer thread. One thread
+// issues the 15 tcgen05.mma of a stage (M = 128, N = 128, K = 16, BF16 -> FP32,
+// SWIZZLE_NONE K-major core matrices: 8 rows x 16 bytes, 128 B between K
+// cores, 256 B between 8-row groups) into three TMEM accumulators of 128
+// columns and commits them to the stage's empty barrier, which gates the next
+// copy into it. At N = 128 an MMA reads 8 KB of shared memory per 128 x 128 x
+// 16 product (N = 64 tiles were limited by shared-memory bandwidth: 52% vs
+// 58% tensor-pipe activity measured). A persistent variant with two TMEM
+// buffers (epilogue overlapped with the next tile) needs 6 x 128 columns for
+// three accumulators, more than the 512 of an SM; with two accumulators the
+// FP32 accumulation error reached 1e-6 at n = 512, and at N = 64 it ran slower.
+// The epilogue reads the accumulators with tcgen05.ld, scales, optionally
+// divides by F2(lambda_i + lambda_j + lambda_k) (the spectral divide of the
+// last forward product), and stores FP32. Every mbarrier wait is bounded; on
 // timeout the CTA records an error flag, skips its stores and frees TMEM.
 #include <cuda_bf16.h>
 
@@ -45,18 +51,18 @@ namespace tctl {
 
 namespace {
 
-constexpr int TM = 128, TN = 64, BK = 16, NSTAGE = 3;
+constexpr int TM = 128, TN = 128, BK = 16, NSTAGE = 4;
 constexpr int NPLANE = 5;                                    // digits of W
 constexpr int XPLANE = 5;                                    // digits of X
 constexpr int NTHREADS = 256;  // 8 warps: producer, MMA issuer, all in the epilogue
 constexpr int PLANE_ELEMS = TM * BK;                         // W plane: 2048 bf16 = 4 KB
-constexpr int XPLANE_ELEMS = TN * BK;                        // X plane: 1024 bf16 = 2 KB
+constexpr int XPLANE_ELEMS = TN * BK;                        // X plane: 2048 bf16 = 4 KB
 constexpr int W_BYTES = NPLANE * PLANE_ELEMS * 2;            // 20 KB per stage
-constexpr int X_BYTES = XPLANE * XPLANE_ELEMS * 2;           // 10 KB per stage
-constexpr int STAGE_BYTES = W_BYTES + X_BYTES;               // 30 KB
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 2048;      // 92 KB: two CTAs per SM
-constexpr int TMEM_COLS = 256;                               // 3 accumulators of TN columns
-constexpr int XD_KS = 4;                                     // K slices per x_digits block
+constexpr int X_BYTES = XPLANE * XPLANE_ELEMS * 2;           // 20 KB per stage
+constexpr int STAGE_BYTES = W_BYTES + X_BYTES;               // 40 KB
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 2048;      // 162 KB: one CTA per SM
+constexpr int TMEM_COLS = 512;                               // 3 accumulators of TN columns
+constexpr int XD_KS = 2;                                     // K slices per x_digits block
 constexpr uint32_t LBO = 128, SBO = (BK / 8) * 128;          // bytes
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(512) x_digits_kernel(int n, const float *__res
 // bulk-copy engine (thread 0 of warp 0, completion counted on full[b]); one
 // thread of warp 1 waits for them, issues the 30 tcgen05.mma of the stage and
 // commits them to empty[b], which gates the next copy into the buffer.
-__global__ void __launch_bounds__(NTHREADS, 2) tc_modeprod_kernel(TcArgs a) {
+__global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
@@ -376,14 +382,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tc_modeprod_kernel(TcArgs a) {
   if (!ok && tid == 0) atomicExch(a.err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows m), columns 32 (w / 4) .. +31,
-    // 16 at a time
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows m), columns (TN / 2) (w / 4) .. +
+    // TN / 2 - 1, 16 at a time
     const int row = (warp & 3) * 32 + lane;
     const int m = mt * TM + row;
     const int em = a.e_row[m];
 #pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-      const int cb = (warp >> 2) * 32 + half * 16;
+    for (int half = 0; half < TN / 32; ++half) {
+      const int cb = (warp >> 2) * (TN / 2) + half * 16;
       uint32_t hi[16], l1[16], rs[16];
       const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb;
 #define TCTL_LD16(dst, addr)                                                                     \
