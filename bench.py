@@ -380,6 +380,25 @@ def ours_arm(args, rank, world):
     value = (world * passing * args.steps) / (total_ms_max / 1000.0)
     e2e_value = world * B / statistics.mean(e2e_times)
 
+    # the same kernels traced on one solve alone (alpha = 0.5, beta = 1e-2): per-launch
+    # durations without the other streams' kernels interleaved
+    iso = None
+    if rank == 0:
+        k_iso = min(range(B), key=lambda i: abs(probs[i].alpha - 0.5) + abs(math.log10(probs[i].beta) + 2))
+        ctxs[k_iso].profile(True)
+        with torch.cuda.stream(streams[k_iso]):
+            ctxs[k_iso].pcg_solve(bs[k_iso])
+        rep = ctxs[k_iso].profile_report()
+        ctxs[k_iso].profile(False)
+        tot_iso = sum(v["ms"] for v in rep.values())
+        iso = {"solve_ms": tot_iso, "kernels": {}}
+        for kname, v in sorted(rep.items(), key=lambda kv: -kv[1]["ms"])[:6]:
+            e = {"launches": v["launches"], "ms": round(v["ms"], 3), "share": round(v["ms"] / tot_iso, 3)}
+            if v["flops"] > 0:
+                tf = v["flops"] / (v["ms"] / 1000.0) / 1e12
+                e["fp64_class_tflops"] = round(tf, 3)
+                e["frac_of_fp64_peak"] = round(tf / FP64_PEAK_TFLOPS, 3)
+            iso["kernels"][kname] = e
     dname, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
     tot_prof_ms = sum(v["ms"] for v in prof.values())
     achieved = (d["flops"] / (d["ms"] / 1000.0) / 1e12) if d["flops"] > 0 else None
@@ -425,6 +444,7 @@ def ours_arm(args, rank, world):
                    "rel_err_vs_oracle": errs or None, "solves_passing": passing,
                    "parallelism": f"replicas x{world}, {B} concurrent streams per GPU"},
         "roofline": roofline,
+        "roofline_isolated": iso,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,

@@ -690,9 +690,9 @@ void sym_eig_multi(Ctx &c, int count, const int *m, const double *const *A, doub
 // original rows), which no later update touches, so L(a, b) = G[p_a][p_b].
 // Each step is a warp argmax of the remaining diagonal, the new column of L,
 // and a rank-1 update of the remaining block (three barriers).
-__global__ void __launch_bounds__(256) pivchol_kernel(int m, const double *__restrict__ Gin,
-                                                      double thr_rel_or_abs, int relative, int rcap,
-                                                      int *perm_out, double *L_out, int *out_r) {
+__device__ __forceinline__ void pivchol_body(int m, const double *__restrict__ Gin,
+                                             double thr_rel_or_abs, int relative, int rcap,
+                                             int *perm_out, double *L_out, int *out_r) {
   __shared__ double G[JMAX][JMAX + 1];
   __shared__ int used[JMAX], perm[JMAX];
   __shared__ int piv;
@@ -759,6 +759,27 @@ __global__ void __launch_bounds__(256) pivchol_kernel(int m, const double *__res
   if (tid == 0) *out_r = r;
 }
 
+__global__ void __launch_bounds__(256) pivchol_kernel(int m, const double *__restrict__ Gin,
+                                                      double thr_rel_or_abs, int relative, int rcap,
+                                                      int *perm_out, double *L_out, int *out_r) {
+  pivchol_body(m, Gin, thr_rel_or_abs, relative, rcap, perm_out, L_out, out_r);
+}
+
+// Several independent pivoted Cholesky factorizations, one CTA each.
+struct PcDesc {
+  const double *G;
+  int m, rcap;
+  int *perm;
+  double *L;
+  int *r;
+};
+
+__global__ void __launch_bounds__(256) pivchol_multi_kernel(const PcDesc *__restrict__ d,
+                                                            double thr_rel_or_abs, int relative) {
+  const PcDesc x = d[blockIdx.x];
+  pivchol_body(x.m, x.G, thr_rel_or_abs, relative, x.rcap, x.perm, x.L, x.r);
+}
+
 // max_ij |G_ij - delta_ij| > tol  ->  *flag = 1 (G: r x r Gram of nearly orthonormal columns)
 __global__ void orth_check_kernel(int r, const double *__restrict__ G, double tol, int *flag) {
   int bad = 0;
@@ -772,15 +793,16 @@ __global__ void orth_check_kernel(int r, const double *__restrict__ G, double to
 }
 
 // Q[i, :] = Y[i, perm] L^{-T}: forward substitution per row (x L^T = y).
-__global__ void trsm_rows_kernel(int n, int r, const double *__restrict__ Y, int ldy,
-                                 const int *__restrict__ perm, const double *__restrict__ Lg,
-                                 double *__restrict__ Q, int ldq) {
+__device__ __forceinline__ void trsm_rows_body(int n, int r, const double *__restrict__ Y, int ldy,
+                                               const int *__restrict__ perm,
+                                               const double *__restrict__ Lg, double *__restrict__ Q,
+                                               int ldq, int bx, int gx) {
   __shared__ double L[JMAX][JMAX + 1];
   __shared__ int pm[JMAX];
   for (int t = threadIdx.x; t < r * r; t += blockDim.x) L[t % r][t / r] = Lg[(t % r) + (t / r) * JMAX];
   for (int t = threadIdx.x; t < r; t += blockDim.x) pm[t] = perm[t];
   __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = bx * blockDim.x + threadIdx.x; i < n; i += gx * blockDim.x) {
     double x[JMAX];
 #pragma unroll 1
     for (int j = 0; j < r; ++j) {
@@ -791,6 +813,27 @@ __global__ void trsm_rows_kernel(int n, int r, const double *__restrict__ Y, int
 #pragma unroll 1
     for (int j = 0; j < r; ++j) Q[i + (long long)j * ldq] = x[j];
   }
+}
+
+__global__ void trsm_rows_kernel(int n, int r, const double *__restrict__ Y, int ldy,
+                                 const int *__restrict__ perm, const double *__restrict__ Lg,
+                                 double *__restrict__ Q, int ldq) {
+  trsm_rows_body(n, r, Y, ldy, perm, Lg, Q, ldq, blockIdx.x, gridDim.x);
+}
+
+struct TrDesc {
+  const double *Y;
+  int ldy, r;
+  const int *perm;
+  const double *L;
+  double *Q;
+};
+
+// blockIdx.y selects the problem; problems with r = 0 do nothing
+__global__ void trsm_rows_multi_kernel(int n, const TrDesc *__restrict__ d) {
+  const TrDesc x = d[blockIdx.y];
+  if (x.r <= 0) return;
+  trsm_rows_body(n, x.r, x.Y, x.ldy, x.perm, x.L, x.Q, n, blockIdx.x, gridDim.x);
 }
 
 int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relative, int rcap,
@@ -838,6 +881,109 @@ int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relati
   }
   c.ws.reset(mk);
   return r;
+}
+
+// Orthonormal bases of several independent matrices at once (same algorithm as
+// orth: pivoted Cholesky QR, up to three passes): one pivoted Cholesky launch
+// (one CTA per matrix), one rank read-back and one triangular-solve launch per
+// pass instead of one per matrix.
+void orth_multi(Ctx &c, int count, int n, const int *m, double *const *Y, const int *ldy, double tol,
+                bool relative, const int *rcap, double *const *Q, int *r_out) {
+  if (count <= 0) return;
+  for (int i = 0; i < count; ++i)
+    if (m[i] > JMAX) fail(TCTL_E_ARG, "orth: more than 64 columns");
+  size_t mk = c.ws.mark();
+  std::vector<double *> G(count), L(count), Q2(count);
+  std::vector<int *> perm(count);
+  int *rdev = c.ws.i32((size_t)2 * count + 2);
+  for (int i = 0; i < count; ++i) {
+    G[i] = c.ws.dbl((size_t)JMAX * JMAX);
+    L[i] = c.ws.dbl((size_t)JMAX * JMAX);
+    perm[i] = c.ws.i32(JMAX);
+    Q2[i] = c.ws.dbl((size_t)n * std::max(1, std::min(m[i], rcap[i] > 0 ? rcap[i] : 1)));
+  }
+  PcDesc *pcd = static_cast<PcDesc *>(c.ws.alloc(sizeof(PcDesc) * count));
+  TrDesc *trd = static_cast<TrDesc *>(c.ws.alloc(sizeof(TrDesc) * count));
+  std::vector<PcDesc> hp(count);
+  std::vector<TrDesc> ht(count);
+  std::vector<int> r(count, 0), rr(2 * count);
+  const int blocks = std::min((n + 31) / 32, 4096);
+  auto read_ints = [&](int k) {
+    TCTL_CUDA(cudaMemcpyAsync(rr.data(), rdev, sizeof(int) * k, cudaMemcpyDeviceToHost, c.st));
+    TCTL_CUDA(cudaStreamSynchronize(c.st));
+  };
+  auto pivchol_all = [&](const std::vector<int> &mm, const std::vector<int> &cap, double thr, int rel) {
+    for (int i = 0; i < count; ++i) hp[i] = PcDesc{G[i], mm[i], cap[i], perm[i], L[i], rdev + i};
+    TCTL_CUDA(cudaMemcpyAsync(pcd, hp.data(), sizeof(PcDesc) * count, cudaMemcpyHostToDevice, c.st));
+    LAUNCH(c, pivchol_multi_kernel, count, 256, 0, pcd, thr, rel);
+    read_ints(count);
+  };
+  auto trsm_all = [&](const std::vector<const double *> &src, const std::vector<int> &ld,
+                      const std::vector<int> &rk, const std::vector<double *> &dst) {
+    for (int i = 0; i < count; ++i) ht[i] = TrDesc{src[i], ld[i], rk[i], perm[i], L[i], dst[i]};
+    TCTL_CUDA(cudaMemcpyAsync(trd, ht.data(), sizeof(TrDesc) * count, cudaMemcpyHostToDevice, c.st));
+    LAUNCH(c, trsm_rows_multi_kernel, dim3(blocks, count), 32, 0, n, trd);
+  };
+  // pass 1: pivoted Cholesky of Y^T Y picks the columns and the ranks
+  std::vector<int> mm(m, m + count), cap(count);
+  for (int i = 0; i < count; ++i) {
+    cap[i] = rcap[i];
+    if (m[i] > 0) gemm(c, true, false, m[i], m[i], n, 1.0, Y[i], ldy[i], 0, Y[i], ldy[i], 0, 0.0, G[i], m[i], 0);
+  }
+  pivchol_all(mm, cap, tol, relative ? 1 : 0);
+  for (int i = 0; i < count; ++i) r[i] = m[i] > 0 ? rr[i] : 0;
+  {
+    std::vector<const double *> src(Y, Y + count);
+    std::vector<int> ld(ldy, ldy + count);
+    std::vector<double *> dst(Q, Q + count);
+    trsm_all(src, ld, r, dst);
+  }
+  // passes 2 and 3: Cholesky QR of the result (see orth); pass 3 only where pass 2
+  // left Q^T Q further than 1e-13 from the identity
+  std::vector<char> active(count);
+  for (int i = 0; i < count; ++i) active[i] = r[i] > 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    bool any = false;
+    for (int i = 0; i < count; ++i)
+      if (active[i]) {
+        gemm(c, true, false, r[i], r[i], n, 1.0, Q[i], n, 0, Q[i], n, 0, 0.0, G[i], r[i], 0);
+        any = true;
+      }
+    if (!any) break;
+    if (pass == 1) {
+      for (int i = 0; i < count; ++i)
+        if (active[i]) LAUNCH(c, orth_check_kernel, 1, 256, 0, r[i], G[i], 1e-13, rdev + count + i);
+      read_ints(2 * count);
+      any = false;
+      for (int i = 0; i < count; ++i) {
+        if (active[i] && !rr[count + i]) active[i] = 0;
+        any = any || active[i];
+      }
+      if (!any) break;
+    }
+    std::vector<int> m2(count, 0), c2(count, 0);
+    for (int i = 0; i < count; ++i)
+      if (active[i]) {
+        m2[i] = r[i];
+        c2[i] = r[i];
+      }
+    pivchol_all(m2, c2, 1e-10, 1);
+    std::vector<int> r2(count, 0);
+    for (int i = 0; i < count; ++i) r2[i] = active[i] ? rr[i] : 0;
+    {
+      std::vector<const double *> src(Q, Q + count);
+      std::vector<int> ld(count, n);
+      trsm_all(src, ld, r2, Q2);
+    }
+    for (int i = 0; i < count; ++i)
+      if (active[i]) {
+        if (r2[i] > 0) copy_d(c, Q[i], Q2[i], (size_t)n * r2[i]);
+        r[i] = r2[i];
+        if (r[i] == 0) active[i] = 0;
+      }
+  }
+  for (int i = 0; i < count; ++i) r_out[i] = r[i];
+  c.ws.reset(mk);
 }
 
 }  // namespace tctl

@@ -217,6 +217,9 @@ void sym_eig_multi(Ctx &c, int count, const int *m, const double *const *A, doub
 // columns whose residual norm falls below tol * (reference) are dropped, where
 // reference = max column norm (relative=true) or 1 (relative=false). Writes Q
 // (n x r, ld n) and returns r (r <= min(m, rcap)). Two passes (CholeskyQR2).
+// orth for `count` independent matrices (batched launches, one read-back per pass).
+void orth_multi(Ctx &c, int count, int n, const int *m, double *const *Y, const int *ldy, double tol,
+                bool relative, const int *rcap, double *const *Q, int *r_out);
 int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relative,
          int rcap, double *Q);
 // Column 2-norms of an n x m matrix.

@@ -325,7 +325,7 @@ void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucke
   size_t mk = c.ws.mark();
   double *My[3];
   int rz[3];
-  double *Qz[3];
+  double *Qz[3], *Wl[3];
   for (int l = 0; l < 3; ++l) {
     const int rx = x.r[l], ry = y.r[l];
     double *C1 = c.ws.dbl((size_t)rx * ry);
@@ -339,9 +339,24 @@ void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucke
     gemm(c, false, false, n, ry, rx, -1.0, x.Q[l], n, 0, C2, rx, 0, 1.0, W, n, 0);
     Qz[l] = c.ws.dbl((size_t)n * kMaxRank);
     copy_d(c, Qz[l], x.Q[l], (size_t)n * rx);
-    const int rw = orth(c, n, ry, W, n, 1e-8, false, std::max(0, kMaxRank - rx), Qz[l] + (size_t)n * rx);
-    rz[l] = rx + rw;
+    Wl[l] = W;
+  }
+  // orthonormal complements of the three modes in one batched call
+  {
+    int ms[3], lds[3], caps[3], rw[3];
+    double *Qw[3];
+    for (int l = 0; l < 3; ++l) {
+      ms[l] = y.r[l];
+      lds[l] = n;
+      caps[l] = std::max(0, kMaxRank - x.r[l]);
+      Qw[l] = Qz[l] + (size_t)n * x.r[l];
+    }
+    orth_multi(c, 3, n, ms, Wl, lds, 1e-8, false, caps, Qw, rw);
+    for (int l = 0; l < 3; ++l) rz[l] = x.r[l] + rw[l];
+  }
+  for (int l = 0; l < 3; ++l) {
     // coordinates of Q_y in [Q_x | Q_w]: [C1 + C2 ; Q_w^T Q_y]
+    const int ry = y.r[l];
     My[l] = c.ws.dbl((size_t)rz[l] * ry);
     gemm(c, true, false, rz[l], ry, n, 1.0, Qz[l], n, 0, y.Q[l], n, 0, 0.0, My[l], rz[l], 0);
   }
@@ -566,23 +581,39 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
     rn[l] = 0;
   }
   {
+    // the three mode sketches first, then their bases in one batched orthonormalisation;
+    // a saturated sketch (rank = width) is redone at width 64
     size_t mks = c.ws.mark();
     double *P[3] = {nullptr, nullptr, nullptr};
-    int ls_p = 0;  // width the probe factors were drawn with
-    double *Y = c.ws.dbl((size_t)n * kMaxRank);
-    for (int l = 0; l < 3; ++l) {
-      for (int attempt = 0; attempt < 2; ++attempt) {
-        if (ls_p != ls) {
-          c.ws.reset(mks);
-          Y = c.ws.dbl((size_t)n * kMaxRank);
-          for (int m = 0; m < 3; ++m) P[m] = sketch_factor(c, D, x, m, ls);
-          ls_p = ls;
-        }
-        sketch_mode(c, D, x, Cl[l], l, ls, P, Y);
-        rn[l] = orth(c, n, ls, Y, n, rtol, true, kMaxRank, Qn[l]);
-        if (rn[l] < ls || ls >= kMaxRank) break;
-        ls = kMaxRank;  // saturated sketch: enlarge and redo this mode
+    double *Y[3];
+    for (int l = 0; l < 3; ++l) Y[l] = c.ws.dbl((size_t)n * kMaxRank);
+    bool todo[3] = {true, true, true};
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      size_t mkp = c.ws.mark();
+      for (int m = 0; m < 3; ++m) P[m] = sketch_factor(c, D, x, m, ls);
+      int cnt = 0, ms[3], lds[3], caps[3], rr[3], idx[3];
+      double *Ys[3], *Qs[3];
+      for (int l = 0; l < 3; ++l) {
+        if (!todo[l]) continue;
+        sketch_mode(c, D, x, Cl[l], l, ls, P, Y[l]);
+        idx[cnt] = l;
+        ms[cnt] = ls;
+        lds[cnt] = n;
+        caps[cnt] = kMaxRank;
+        Ys[cnt] = Y[l];
+        Qs[cnt] = Qn[l];
+        ++cnt;
       }
+      orth_multi(c, cnt, n, ms, Ys, lds, rtol, true, caps, Qs, rr);
+      bool again = false;
+      for (int t = 0; t < cnt; ++t) {
+        rn[idx[t]] = rr[t];
+        todo[idx[t]] = (rr[t] >= ls && ls < kMaxRank);
+        again = again || todo[idx[t]];
+      }
+      c.ws.reset(mkp);
+      if (!again) break;
+      ls = kMaxRank;
     }
     c.ws.reset(mks);
   }
