@@ -279,6 +279,7 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
     const size_t arena = c->o.workspace_mb > 0 ? ((size_t)c->o.workspace_mb << 20) : auto_arena_bytes(n);
     void *base = nullptr;
     keep_pool_memory();
+    c->hstage = stage_acquire();
     check_cuda(cudaMallocAsync(&base, arena, c->st), "cudaMallocAsync(workspace)");
     c->owned.push_back(base);
     c->ws.base = static_cast<char *>(base);
@@ -735,6 +736,7 @@ void tctl_destroy(tctl_ctx *ctx) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   for (void *p : c->owned) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
+  stage_release(c->hstage);
   delete c;
 }
 

@@ -8,6 +8,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "tctl_internal.cuh"
 
@@ -487,15 +490,79 @@ void axpby(Ctx &c, size_t count, double a, const double *x, double b, double *y)
   LAUNCH(c, axpby_kernel, blocks, 256, 0, count, a, x, b, y);
 }
 
+// Pinned staging buffers are recycled through a process-wide free list rather
+// than freed: releasing pinned memory may synchronise the device, which would
+// stall the other contexts' streams.
+static std::mutex g_stage_mu;
+static std::vector<char *> g_stage_free;
+
+char *stage_acquire() {
+  {
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (!g_stage_free.empty()) {
+      char *p = g_stage_free.back();
+      g_stage_free.pop_back();
+      return p;
+    }
+  }
+  void *p = nullptr;
+  if (cudaHostAlloc(&p, kStageBytes, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;  // transfers then take the pageable path
+  }
+  return static_cast<char *>(p);
+}
+
+void stage_release(char *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  g_stage_free.push_back(p);
+}
+
+// A copy between device and pageable host memory may wait inside the driver
+// for the stream to drain, and with many contexts working on concurrent
+// streams that wait costs far more than synchronising the stream and copying
+// from pinned memory. Small transfers therefore go through the context's
+// pinned staging buffer; large ones synchronise first and copy directly.
+void read_host(Ctx &c, void *dst, const void *src, size_t bytes) {
+  if (!bytes) return;
+  if (c.hstage && bytes <= kStageRead) {
+    TCTL_CUDA(cudaMemcpyAsync(c.hstage, src, bytes, cudaMemcpyDeviceToHost, c.st));
+    TCTL_CUDA(cudaStreamSynchronize(c.st));
+    std::memcpy(dst, c.hstage, bytes);
+  } else {
+    TCTL_CUDA(cudaStreamSynchronize(c.st));
+    TCTL_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c.st));
+    TCTL_CUDA(cudaStreamSynchronize(c.st));
+  }
+  c.hstage_top = 0;  // the stream is idle: every staged upload has landed
+}
+
+void write_dev(Ctx &c, void *dst, const void *src, size_t bytes) {
+  if (!bytes) return;
+  constexpr size_t ring = kStageBytes - kStageRead;
+  if (!c.hstage || bytes > ring) {
+    TCTL_CUDA(cudaStreamSynchronize(c.st));
+    TCTL_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c.st));
+    return;
+  }
+  size_t off = (c.hstage_top + 15) & ~size_t(15);
+  if (off + bytes > ring) {  // ring full: wait until the queued uploads have landed
+    TCTL_CUDA(cudaStreamSynchronize(c.st));
+    off = 0;
+  }
+  char *p = c.hstage + kStageRead + off;
+  std::memcpy(p, src, bytes);
+  TCTL_CUDA(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, c.st));
+  c.hstage_top = off + bytes;
+}
+
 void to_host(Ctx &c, double *dst, const double *src, size_t count) {
-  if (!count) return;
-  TCTL_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-  TCTL_CUDA(cudaStreamSynchronize(c.st));
+  read_host(c, dst, src, count * sizeof(double));
 }
 
 void to_dev(Ctx &c, double *dst, const double *src, size_t count) {
-  if (!count) return;
-  TCTL_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, c.st));
+  write_dev(c, dst, src, count * sizeof(double));
 }
 
 // ------------------------------------------------------------------ Jacobi
@@ -774,9 +841,14 @@ struct PcDesc {
   int *r;
 };
 
-__global__ void __launch_bounds__(256) pivchol_multi_kernel(const PcDesc *__restrict__ d,
+constexpr int ORTH_BATCH = 8;
+struct PcBatch {
+  PcDesc d[ORTH_BATCH];
+};
+
+__global__ void __launch_bounds__(256) pivchol_multi_kernel(const __grid_constant__ PcBatch b,
                                                             double thr_rel_or_abs, int relative) {
-  const PcDesc x = d[blockIdx.x];
+  const PcDesc x = b.d[blockIdx.x];
   pivchol_body(x.m, x.G, thr_rel_or_abs, relative, x.rcap, x.perm, x.L, x.r);
 }
 
@@ -829,9 +901,13 @@ struct TrDesc {
   double *Q;
 };
 
+struct TrBatch {
+  TrDesc d[ORTH_BATCH];
+};
+
 // blockIdx.y selects the problem; problems with r = 0 do nothing
-__global__ void trsm_rows_multi_kernel(int n, const TrDesc *__restrict__ d) {
-  const TrDesc x = d[blockIdx.y];
+__global__ void trsm_rows_multi_kernel(int n, const __grid_constant__ TrBatch b) {
+  const TrDesc x = b.d[blockIdx.y];
   if (x.r <= 0) return;
   trsm_rows_body(n, x.r, x.Y, x.ldy, x.perm, x.L, x.Q, n, blockIdx.x, gridDim.x);
 }
@@ -850,8 +926,7 @@ int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relati
   const int blocks = std::min((n + 31) / 32, 4096);
   auto read_int = [&](const int *p) {
     int v = 0;
-    TCTL_CUDA(cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-    TCTL_CUDA(cudaStreamSynchronize(c.st));
+    read_host(c, &v, p, sizeof(int));
     return v;
   };
   // pass 1: pivoted Cholesky of Y^T Y picks the columns and the rank
@@ -890,6 +965,7 @@ int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relati
 void orth_multi(Ctx &c, int count, int n, const int *m, double *const *Y, const int *ldy, double tol,
                 bool relative, const int *rcap, double *const *Q, int *r_out) {
   if (count <= 0) return;
+  if (count > ORTH_BATCH) fail(TCTL_E_ARG, "orth_multi: more than 8 matrices");
   for (int i = 0; i < count; ++i)
     if (m[i] > JMAX) fail(TCTL_E_ARG, "orth: more than 64 columns");
   size_t mk = c.ws.mark();
@@ -902,27 +978,22 @@ void orth_multi(Ctx &c, int count, int n, const int *m, double *const *Y, const 
     perm[i] = c.ws.i32(JMAX);
     Q2[i] = c.ws.dbl((size_t)n * std::max(1, std::min(m[i], rcap[i] > 0 ? rcap[i] : 1)));
   }
-  PcDesc *pcd = static_cast<PcDesc *>(c.ws.alloc(sizeof(PcDesc) * count));
-  TrDesc *trd = static_cast<TrDesc *>(c.ws.alloc(sizeof(TrDesc) * count));
-  std::vector<PcDesc> hp(count);
-  std::vector<TrDesc> ht(count);
+  PcBatch hp{};
+  TrBatch ht{};
   std::vector<int> r(count, 0), rr(2 * count);
   const int blocks = std::min((n + 31) / 32, 4096);
   auto read_ints = [&](int k) {
-    TCTL_CUDA(cudaMemcpyAsync(rr.data(), rdev, sizeof(int) * k, cudaMemcpyDeviceToHost, c.st));
-    TCTL_CUDA(cudaStreamSynchronize(c.st));
+    read_host(c, rr.data(), rdev, sizeof(int) * k);
   };
   auto pivchol_all = [&](const std::vector<int> &mm, const std::vector<int> &cap, double thr, int rel) {
-    for (int i = 0; i < count; ++i) hp[i] = PcDesc{G[i], mm[i], cap[i], perm[i], L[i], rdev + i};
-    TCTL_CUDA(cudaMemcpyAsync(pcd, hp.data(), sizeof(PcDesc) * count, cudaMemcpyHostToDevice, c.st));
-    LAUNCH(c, pivchol_multi_kernel, count, 256, 0, pcd, thr, rel);
+    for (int i = 0; i < count; ++i) hp.d[i] = PcDesc{G[i], mm[i], cap[i], perm[i], L[i], rdev + i};
+    LAUNCH(c, pivchol_multi_kernel, count, 256, 0, hp, thr, rel);
     read_ints(count);
   };
   auto trsm_all = [&](const std::vector<const double *> &src, const std::vector<int> &ld,
                       const std::vector<int> &rk, const std::vector<double *> &dst) {
-    for (int i = 0; i < count; ++i) ht[i] = TrDesc{src[i], ld[i], rk[i], perm[i], L[i], dst[i]};
-    TCTL_CUDA(cudaMemcpyAsync(trd, ht.data(), sizeof(TrDesc) * count, cudaMemcpyHostToDevice, c.st));
-    LAUNCH(c, trsm_rows_multi_kernel, dim3(blocks, count), 32, 0, n, trd);
+    for (int i = 0; i < count; ++i) ht.d[i] = TrDesc{src[i], ld[i], rk[i], perm[i], L[i], dst[i]};
+    LAUNCH(c, trsm_rows_multi_kernel, dim3(blocks, count), 32, 0, n, ht);
   };
   // pass 1: pivoted Cholesky of Y^T Y picks the columns and the ranks
   std::vector<int> mm(m, m + count), cap(count);

@@ -307,7 +307,7 @@ void build_sep(Ctx &c, Sep &D, const std::vector<double> &w, const std::vector<T
   double *td_t = c.ws.dbl(D.R);
   int *td_m = c.ws.i32(D.R);
   to_dev(c, td_t, t.data(), D.R);
-  TCTL_CUDA(cudaMemcpyAsync(td_m, lm.data(), sizeof(int) * D.R, cudaMemcpyHostToDevice, c.st));
+  write_dev(c, td_m, lm.data(), sizeof(int) * D.R);
   // Factor columns are stored with unit 2-norm and their norms moved into the
   // weights, w_k E_0k E_1k E_2k unchanged: every term then enters a contraction
   // at the scale of its contribution (the tensor-core GEMMs bound their error

@@ -485,8 +485,7 @@ void gemm_tc_cm(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, doubl
 void tcg_check(Ctx &c) {
   if (!c.tcg_err) return;
   int herr = 0;
-  TCTL_CUDA(cudaMemcpyAsync(&herr, c.tcg_err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-  TCTL_CUDA(cudaStreamSynchronize(c.st));
+  read_host(c, &herr, c.tcg_err, sizeof(int));
   if (herr) {
     TCTL_CUDA(cudaMemsetAsync(c.tcg_err, 0, sizeof(int), c.st));
     fail(TCTL_E_NUMERIC, "tensor-core GEMM: bounded mbarrier wait timed out");

@@ -532,8 +532,7 @@ void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
     LAUNCH(c, f32_to_f64_kernel, blocks, 256, 0, n3, A, u);
   }
   int herr = 0;
-  TCTL_CUDA(cudaMemcpyAsync(&herr, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-  TCTL_CUDA(cudaStreamSynchronize(c.st));
+  read_host(c, &herr, c.tc_err, sizeof(int));
   if (herr) fail(TCTL_E_NUMERIC, "tensor-core mode product: bounded mbarrier wait timed out");
 }
 

@@ -94,6 +94,11 @@ struct Ctx {
   std::vector<double> op_terms_w, op_terms_t, pre_terms_w, pre_terms_t;  // host copies
   std::vector<int> op_terms_m, pre_terms_m;
   Arena ws;
+  // pinned host staging for small transfers: [0, kStageRead) receives
+  // device-to-host reads, the rest is a ring of host-to-device uploads whose
+  // space is reused once a read has synchronised the stream
+  char *hstage = nullptr;
+  size_t hstage_top = 0;
   double *full_tmp = nullptr;        // n^3 temporary of the FP64 full-grid solve
   // tensor-core full grid: digit planes of V_l^T / V_l, row exponents, two FP32
   // n^3 buffers, column exponents, error flag (allocated on first use)
@@ -229,7 +234,14 @@ void fill_gaussian(Ctx &c, double *x, size_t count, uint64_t seed);
 void fill_zero(Ctx &c, double *x, size_t count);
 void copy_d(Ctx &c, double *dst, const double *src, size_t count);
 void axpby(Ctx &c, size_t count, double a, const double *x, double b, double *y);
-// Host copies (synchronous on the context stream).
+// Host copies. to_host / read_host return once the data is on the host (the
+// context stream is synchronised); to_dev / write_dev are stream-ordered and
+// the caller's buffer may be reused at once.
+constexpr size_t kStageBytes = 1 << 20, kStageRead = 256 << 10;
+char *stage_acquire();
+void stage_release(char *p);
+void read_host(Ctx &c, void *dst, const void *src, size_t bytes);
+void write_dev(Ctx &c, void *dst, const void *src, size_t bytes);
 void to_host(Ctx &c, double *dst, const double *src, size_t count);
 void to_dev(Ctx &c, double *dst, const double *src, size_t count);
 

@@ -226,9 +226,10 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
   double *perm = c.ws.dbl(sz);
   double *G[3], *lam[3], *U[3];
   std::vector<double> lh[3];
+  double *lam_all = c.ws.dbl((size_t)r[0] + r[1] + r[2]);  // one read-back for the three modes
   for (int l = 0; l < 3; ++l) {
     G[l] = c.ws.dbl((size_t)r[l] * r[l]);
-    lam[l] = c.ws.dbl(r[l]);
+    lam[l] = lam_all + (l == 0 ? 0 : l == 1 ? r[0] : r[0] + r[1]);
     U[l] = c.ws.dbl((size_t)r[l] * r[l]);
     const double *src = x.core;
     if (l == 1) { permute3(c, r, x.core, 1, 0, 2, perm); src = perm; }
@@ -239,9 +240,14 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
   }
   sym_eig_multi(c, 3, r, G, lam, U);
   double tot = 0.0;
-  for (int l = 0; l < 3; ++l) {
-    lh[l].resize(r[l]);
-    to_host(c, lh[l].data(), lam[l], r[l]);
+  {
+    std::vector<double> all((size_t)r[0] + r[1] + r[2]);
+    to_host(c, all.data(), lam_all, all.size());
+    size_t o = 0;
+    for (int l = 0; l < 3; ++l) {
+      lh[l].assign(all.begin() + o, all.begin() + o + r[l]);
+      o += r[l];
+    }
   }
   for (double v : lh[0]) tot += std::max(v, 0.0);
   if (!std::isfinite(tot)) fail(TCTL_E_NAN, "non-finite core in truncation");
@@ -754,8 +760,8 @@ int tucker_to_cp(Ctx &c, const Tucker &x, bool from_eig, double eps, tctl_cp *y)
   }
   if (keep > 0) {
     int *idx = c.ws.i32(keep), *idc = c.ws.i32(keep);
-    TCTL_CUDA(cudaMemcpyAsync(idx, ia.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.st));
-    TCTL_CUDA(cudaMemcpyAsync(idc, ic.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.st));
+    write_dev(c, idx, ia.data(), sizeof(int) * keep);
+    write_dev(c, idc, ic.data(), sizeof(int) * keep);
     double *Asel = c.ws.dbl((size_t)r0 * keep), *Bsel = c.ws.dbl((size_t)r1 * keep);
     double *invd = c.ws.dbl(keep);
     to_dev(c, invd, inv.data(), keep);
@@ -766,7 +772,6 @@ int tucker_to_cp(Ctx &c, const Tucker &x, bool from_eig, double eps, tctl_cp *y)
     gemm(c, false, false, n, keep, r1, 1.0, Qp[1], n, 0, Bsel, r1, 0, 0.0, y->U[1], n, 0);
     gather_cols(c, n, Qp[2], n, idc, keep, y->U[2], n);
     to_dev(c, y->w, wv.data(), keep);
-    TCTL_CUDA(cudaStreamSynchronize(c.st));
   }
   y->rank = keep;
   c.ws.reset(mk);
