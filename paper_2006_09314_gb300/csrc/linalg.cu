@@ -144,6 +144,9 @@ __global__ void splitk_reduce(int m, int n, int splits, int batch, double alpha,
     const long long r = t - (long long)b * m * n;
     const int i = (int)(r % m), j = (int)(r / m);
     double s = 0.0;
+    // unrolled so that several partial sums are in flight (the summation order,
+    // and so the result, is unchanged)
+#pragma unroll 16
     for (int q = 0; q < splits; ++q) s += part[((long long)b * splits + q) * m * n + r];
     double *p = C + (long long)b * sC + i + (long long)j * ldc;
     *p = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *p);

@@ -336,6 +336,7 @@ __global__ void tcg_reduce_kernel(int M, int N, int batch, int nchunk, const dou
     const int j = (int)((t / M) % N);
     const int b = (int)(t / ((long long)M * N));
     double s = 0.0;
+#pragma unroll 8
     for (int ch = 0; ch < nchunk; ++ch) s += part[((long long)(b * nchunk + ch) * N + j) * M + m];
     double *out = C + (long long)b * cb + (long long)(m % cd) * cm0 + (long long)(m / cd) * cm1 +
                   (long long)j * cj;
