@@ -53,6 +53,19 @@ __device__ __forceinline__ long long row_off(const TcOpnd &o, int r) {
   return (long long)(r % o.d) * o.s0 + (long long)(r / o.d) * o.s1;
 }
 
+// Row r of an operand: its two factor rows for the Khatri-Rao form, else one
+// strided row (y unused).
+struct RowPtr {
+  const double *x, *y;
+  __device__ __forceinline__ double at(long long k, long long sk, bool kr) const {
+    return kr ? x[k * sk] * y[k * sk] : x[k * sk];
+  }
+};
+__device__ __forceinline__ RowPtr row_ptr(const TcOpnd &o, int item, int r) {
+  if (o.q) return RowPtr{o.p + (long long)(r % o.d) * o.s0, o.q + (long long)(r / o.d) * o.s1};
+  return RowPtr{o.p + (long long)item * o.sb + row_off(o, r), nullptr};
+}
+
 // Row exponents, stored biased: e_out[item * Rpad + r] = E_BIAS + (smallest e
 // with |X(r, k)| < 2^e for all k); 0 for an all-zero row (the buffer is
 // zeroed first), E_NONFINITE if the row holds Inf/NaN. A block covers 32 rows
@@ -73,7 +86,7 @@ __global__ void row_exp_kernel(TcOpnd o, int R, int K, int Rpad, int *__restrict
   const int item = blockIdx.z;
   const int r0 = blockIdx.x * 32, k0 = blockIdx.y * RE_K;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 8 warps
-  const double *base = o.p + (long long)item * o.sb;
+  const bool kr = o.q != nullptr;
   const int kend = min(K, k0 + RE_K);
   if (o.sk == 1) {
     // k contiguous: warp w takes rows r0 + w, r0 + w + 8, ...; lanes along k
@@ -81,8 +94,8 @@ __global__ void row_exp_kernel(TcOpnd o, int R, int K, int Rpad, int *__restrict
       const int r = r0 + rr;
       int c = 0;
       if (r < R) {
-        const double *x = base + row_off(o, r);
-        for (int k = k0 + lane; k < kend; k += 32) c = max(c, exp_code(x[k]));
+        const RowPtr x = row_ptr(o, item, r);
+        for (int k = k0 + lane; k < kend; k += 32) c = max(c, exp_code(x.at(k, 1, kr)));
       }
       for (int s = 16; s > 0; s >>= 1) c = max(c, __shfl_xor_sync(0xffffffffu, c, s));
       if (lane == 0 && r < R && c > 0) atomicMax(&e_out[(long long)item * Rpad + r], c);
@@ -92,8 +105,8 @@ __global__ void row_exp_kernel(TcOpnd o, int R, int K, int Rpad, int *__restrict
     const int r = r0 + lane;
     int c = 0;
     if (r < R) {
-      const double *x = base + row_off(o, r);
-      for (int k = k0 + w; k < kend; k += 8) c = max(c, exp_code(x[(long long)k * o.sk]));
+      const RowPtr x = row_ptr(o, item, r);
+      for (int k = k0 + w; k < kend; k += 8) c = max(c, exp_code(x.at(k, o.sk, kr)));
     }
     __shared__ int red[8][32];
     red[w][lane] = c;
@@ -131,12 +144,13 @@ __global__ void __launch_bounds__(2 * TR) split_kernel(TcOpnd o, int R, int K, i
 #pragma unroll
     for (int h = 0; h < 4; ++h) w[p][h] = 0;
   if (r < R && ec != 0 && ec != E_NONFINITE) {
-    const double *x = o.p + (long long)item * o.sb + row_off(o, r);
+    const RowPtr x = row_ptr(o, item, r);
+    const bool kr = o.q != nullptr;
     const double cap = ldexp(1.0, 7 * D) - 1.0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = k0 + i;
-      const double v = (k < K) ? x[(long long)k * o.sk] : 0.0;
+      const double v = (k < K) ? x.at(k, o.sk, kr) : 0.0;
       if (v == 0.0) continue;
       const uint64_t F = (uint64_t)fmin(ldexp(fabs(v), 7 * D - e), cap);  // 7D-bit fixed point
       const float sg = v < 0.0 ? -1.0f : 1.0f;
@@ -442,6 +456,7 @@ void gemm_tc(Ctx &c, int digits, int M, int N, int K, int batch, int divA, int d
              int cd, long long cj, long long cb) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K <= 0) fail(TCTL_E_ARG, "gemm_tc: K must be positive");
+  if ((A.q || B.q) && batch != 1) fail(TCTL_E_ARG, "gemm_tc: a Khatri-Rao operand takes no batch");
   static_assert(TMEM_COLS >= 4 * TN, "four accumulators");
   if (digits <= 4)
     run_tcg<4, 4>(c, M, N, K, batch, divA, divB, alpha, A, B, beta, C, cm0, cm1, cd, cj, cb);

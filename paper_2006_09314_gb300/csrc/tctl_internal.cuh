@@ -179,10 +179,14 @@ struct PhaseScope {
 // Operand of the digit-split tensor-core GEMM: rows r (m of A, j of B),
 // contracted index k, batch item i; element at
 // p + i sb + (r % d) s0 + (r / d) s1 + k sk.
+// With q set, the operand is a Khatri-Rao product formed on the fly (no batch):
+// element (r, k) = p[(r % d) s0 + k sk] * q[(r / d) s1 + k sk], the value
+// khatri_rao() would have stored, so both forms give identical results.
 struct TcOpnd {
   const double *p;
   long long s0, s1, sk, sb;
   int d;
+  const double *q = nullptr;
 };
 // C[b sC' + (m % cd) cm0 + (m / cd) cm1 + j cj] = alpha sum_k A(m, k) B(j, k) + beta C,
 // batch item b of A / B = b / divA, b / divB; digits 4 (28-bit) or 6 (42-bit).

@@ -77,16 +77,18 @@ __global__ void contract_b_kernel(int ra, int rb, int ls, int K, const double *_
   }
 }
 
-// u[a + ra*(p + rp*s)] = v[(a + ra*s) + ra*ls*p]   ((a,s,p) -> (a,p,s))
-__global__ void perm_asp_kernel(int ra, int ls, int rp, const double *__restrict__ v,
-                                double *__restrict__ u) {
-  const long long total = (long long)ra * ls * rp;
+// Y[i, s] = sum_a Q[i, a] W[i, a + ra s] for s < ns: the Khatri-Rao
+// contraction of W = B_l U^T with the factor Q (one thread per (i, s)).
+__global__ void rowdot_kernel(int n, int ra, int ns, const double *__restrict__ Q, int ldq,
+                              const double *__restrict__ W, int ldw, double *__restrict__ Y, int ldy) {
+  const long long total = (long long)n * ns;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(t % ra);
-    const int s = (int)((t / ra) % ls);
-    const int p = (int)(t / ((long long)ra * ls));
-    u[a + (long long)ra * (p + (long long)rp * s)] = v[t];
+    const int i = (int)(t % n), s = (int)(t / n);
+    const double *w = W + i + (long long)ra * s * ldw;
+    double acc = 0.0;
+    for (int a = 0; a < ra; ++a) acc = fma(Q[i + (long long)a * ldq], w[(long long)a * ldw], acc);
+    Y[i + (long long)s * ldy] = acc;
   }
 }
 
@@ -463,6 +465,31 @@ void cp_to_tucker(Ctx &c, int m, const double *w, double *const U[3], bool to_ei
   if (eps_core > 0) tucker_hosvd_trunc(c, out, eps_core);
 }
 
+// out (ra rb x N, ld ldo) = KR(X, Y)^T E, i.e.
+// out[a + ra b, j] = sum_i X[i, a] Y[i, b] E[i, j], contracted over i < n.
+// The tensor-core path forms the Khatri-Rao rows inside its digit split; the
+// FP64 path materialises KR(X, Y) (n x ra rb) first.
+static void kr_t_gemm(Ctx &c, int n, const double *X, int ldx, int ra, const double *Y, int ldy,
+                      int rb, const double *E, int lde, int N, double *out, int ldo) {
+  const int M = ra * rb;
+  if (M <= 0 || N <= 0) return;
+  if (c.o.tc_gemm && gemm_tc_fits(std::max(M, N), std::min(M, N), n, 1)) {
+    const TcOpnd kr{X, (long long)ldx, (long long)ldy, 1, 0, ra, Y};
+    const TcOpnd e{E, (long long)lde, 0, 1, 0, 1 << 30};
+    // the larger dimension takes the 128-row side of the tile
+    if (M >= N)
+      gemm_tc(c, kDigits, M, N, n, 1, 1, 1, 1.0, kr, e, 0.0, out, 1, 0, 1 << 30, ldo, 0);
+    else
+      gemm_tc(c, kDigits, N, M, n, 1, 1, 1, 1.0, e, kr, 0.0, out, ldo, 0, 1 << 30, 1, 0);
+    return;
+  }
+  size_t mk = c.ws.mark();
+  double *KR = c.ws.dbl((size_t)n * M);
+  khatri_rao(c, n, X, ldx, ra, Y, ldy, rb, KR, n);
+  gemm_x(c, kDigits, true, false, M, N, n, 1.0, KR, n, 0, E, lde, 0, 0.0, out, ldo, 0);
+  c.ws.reset(mk);
+}
+
 // Probe factor of mode m for the Khatri-Rao sketches: with Om (n x ls) a fresh
 // Gaussian matrix, P_m[(a,s),k] = sum_i Q_m[i,a] Om[i,s] E_m[i,k]
 // = (KR(Q_m, Om)^T B_m) Z_m, an (r_m ls) x R matrix in the workspace. The same
@@ -475,18 +502,14 @@ static double *sketch_factor(Ctx &c, const Sep &D, const Tucker &x, int m, int l
   size_t mk = c.ws.mark();
   double *Om = c.ws.dbl((size_t)n * ls);
   fill_gaussian(c, Om, (size_t)n * ls, c.o.seed * 0x9E3779B97F4A7C15ull + (c.rng_counter++));
-  double *KRm = c.ws.dbl((size_t)n * rm * ls);
-  khatri_rao(c, n, x.Q[m], n, rm, Om, n, ls, KRm, n);
   if (D.Z[m]) {
     double *T = c.ws.dbl((size_t)rm * ls * D.rD[m]);
-    gemm_x(c, kDigits, true, false, rm * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, T,
-           rm * ls, 0);
+    kr_t_gemm(c, n, x.Q[m], n, rm, Om, n, ls, D.B[m], n, D.rD[m], T, rm * ls);
     gemm_x(c, kDigits, false, false, rm * ls, R, D.rD[m], 1.0, T, rm * ls, 0, D.Z[m], D.rD[m], 0,
            0.0, P, rm * ls, 0);
   } else {
     // uncompressed operator: B_m holds the R factor columns themselves
-    gemm_x(c, kDigits, true, false, rm * ls, D.rD[m], n, 1.0, KRm, n, 0, D.B[m], n, 0, 0.0, P,
-           rm * ls, 0);
+    kr_t_gemm(c, n, x.Q[m], n, rm, Om, n, ls, D.B[m], n, D.rD[m], P, rm * ls);
   }
   c.ws.reset(mk);
   return P;
@@ -524,20 +547,19 @@ static void sketch_mode(Ctx &c, const Sep &D, const Tucker &x, const double *Cl,
       copy_d(c, uT + (size_t)r[l] * ls * k0, v, (size_t)r[l] * ls * nk);
     }
   }
-  // Y = KR(Q_l, B_l) (n x r_l rD) U2 (r_l rD x ls), U2[(a,p),s] = uT[(a,s),p]
-  double *U2 = c.ws.dbl((size_t)r[l] * D.rD[l] * ls);
-  {
-    const long long tot = (long long)r[l] * ls * D.rD[l];
+  // Y[i, s] = sum_{a,p} Q_l[i, a] B_l[i, p] uT[(a,s), p], contracted over p
+  // first: W[i, a + r_l s] = (B_l uT^T)[i, (a,s)] (n x r_l ls, in slices of s),
+  // then over a row by row. The Khatri-Rao product KR(Q_l, B_l) (n x r_l rD)
+  // is never formed.
+  const int sc = std::max(1, std::min(ls, (int)((64ll << 20) / ((long long)n * r[l] * 8))));
+  double *W = c.ws.dbl((size_t)n * r[l] * sc);
+  for (int s0 = 0; s0 < ls; s0 += sc) {
+    const int ns = std::min(sc, ls - s0);
+    gemm_x(c, kDigits, false, true, n, r[l] * ns, D.rD[l], 1.0, D.B[l], n, 0,
+           uT + (size_t)r[l] * s0, r[l] * ls, 0, 0.0, W, n, 0);
+    const long long tot = (long long)n * ns;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-    LAUNCH(c, perm_asp_kernel, blocks, 256, 0, r[l], ls, D.rD[l], uT, U2);
-  }
-  const int pc = std::max(1, std::min(D.rD[l], (int)((64ll << 20) / ((long long)n * r[l]))));
-  double *KRl = c.ws.dbl((size_t)n * r[l] * pc);
-  for (int p0 = 0; p0 < D.rD[l]; p0 += pc) {
-    const int np_ = std::min(pc, D.rD[l] - p0);
-    khatri_rao(c, n, x.Q[l], n, r[l], D.B[l] + (size_t)n * p0, n, np_, KRl, n);
-    gemm_x(c, kDigits, false, false, n, ls, r[l] * np_, 1.0, KRl, n, 0, U2 + (size_t)r[l] * p0,
-           r[l] * D.rD[l], 0, p0 == 0 ? 0.0 : 1.0, Y, n, 0);
+    LAUNCH(c, rowdot_kernel, blocks, 256, 0, n, r[l], ns, x.Q[l], n, W, n, Y + (size_t)n * s0, n);
   }
   c.ws.reset(mk);
 }
@@ -628,11 +650,8 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
   double *M[3];
   for (int l = 0; l < 3; ++l) {
     // N_l[(a',b), p] = sum_i Qn[i,a'] Q[i,b] B[i,p];  M_l = N_l Z_l : (rn r) x R
-    double *KR = c.ws.dbl((size_t)n * rn[l] * r[l]);
-    khatri_rao(c, n, Qn[l], n, rn[l], x.Q[l], n, r[l], KR, n);
     double *N = c.ws.dbl((size_t)rn[l] * r[l] * D.rD[l]);
-    gemm_x(c, kDigits, true, false, rn[l] * r[l], D.rD[l], n, 1.0, KR, n, 0, D.B[l], n, 0, 0.0, N,
-           rn[l] * r[l], 0);
+    kr_t_gemm(c, n, Qn[l], n, rn[l], x.Q[l], n, r[l], D.B[l], n, D.rD[l], N, rn[l] * r[l]);
     if (D.Z[l]) {
       M[l] = c.ws.dbl((size_t)rn[l] * r[l] * R);
       gemm_x(c, kDigits, false, false, rn[l] * r[l], R, D.rD[l], 1.0, N, rn[l] * r[l], 0, D.Z[l],
