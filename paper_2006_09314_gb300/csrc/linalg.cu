@@ -134,22 +134,33 @@ dgemm_kernel(int m, int n, int k, double alpha, const double *__restrict__ A, in
   }
 }
 
-__global__ void splitk_reduce(int m, int n, int splits, int batch, double alpha,
-                              const double *__restrict__ part, double beta, double *C, int ldc,
-                              long long sC) {
-  const long long total = (long long)m * n * batch;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / ((long long)m * n));
-    const long long r = t - (long long)b * m * n;
+// C = alpha sum_q part_q + beta C. A block takes 32 consecutive outputs (x)
+// and spreads the partial sums over 8 groups (y) that run concurrently, so a
+// small output with many K-splits is not one long chain of loads per thread;
+// the order of summation is fixed, so results are reproducible.
+__global__ void __launch_bounds__(256) splitk_reduce(int m, int n, int splits, int batch, double alpha,
+                                                     const double *__restrict__ part, double beta,
+                                                     double *C, int ldc, long long sC) {
+  __shared__ double red[8][33];
+  const long long mn = (long long)m * n, total = mn * batch;
+  const long long t = blockIdx.x * 32ll + threadIdx.x;
+  double s = 0.0;
+  int b = 0;
+  long long r = 0;
+  if (t < total) {
+    b = (int)(t / mn);
+    r = t - (long long)b * mn;
+    const double *p = part + (long long)b * splits * mn + r;
+#pragma unroll 4
+    for (int q = threadIdx.y; q < splits; q += 8) s += p[q * mn];
+  }
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && t < total) {
+    for (int g = 1; g < 8; ++g) s += red[g][threadIdx.x];
     const int i = (int)(r % m), j = (int)(r / m);
-    double s = 0.0;
-    // unrolled so that several partial sums are in flight (the summation order,
-    // and so the result, is unchanged)
-#pragma unroll 16
-    for (int q = 0; q < splits; ++q) s += part[((long long)b * splits + q) * m * n + r];
-    double *p = C + (long long)b * sC + i + (long long)j * ldc;
-    *p = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *p);
+    double *out = C + (long long)b * sC + i + (long long)j * ldc;
+    *out = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *out);
   }
 }
 
@@ -277,8 +288,8 @@ static void gemm_skinny(Ctx &c, bool ta, bool tb, int m, int n, int k, double al
   else if (NC == 8) skinny_launch<8>(c, ta, tb, m, n, k, A, lda, B, ldb, part, splits, kchunk, rowblocks);
   else skinny_launch<16>(c, ta, tb, m, n, k, A, lda, B, ldb, part, splits, kchunk, rowblocks);
   const long long total = (long long)m * n;
-  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
-  LAUNCH(c, splitk_reduce, blocks, 256, 0, m, n, splits, 1, alpha, part, beta, C, ldc, 0ll);
+  LAUNCH(c, splitk_reduce, (unsigned)((total + 31) / 32), dim3(32, 8), 0, m, n, splits, 1, alpha, part,
+         beta, C, ldc, 0ll);
   c.ws.reset(mk);
 }
 
@@ -378,8 +389,8 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
                         C, ldc, sC, splits, kchunk, part);
   if (splits > 1) {
     const long long total = (long long)m * n * batch;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
-    LAUNCH(c, splitk_reduce, blocks, 256, 0, m, n, splits, batch, alpha, part, beta, C, ldc, sC);
+    LAUNCH(c, splitk_reduce, (unsigned)((total + 31) / 32), dim3(32, 8), 0, m, n, splits, batch, alpha,
+           part, beta, C, ldc, sC);
   }
   c.ws.reset(mk);
 }

@@ -373,6 +373,32 @@ void split_operand(Ctx &c, const TcOpnd &o, int R, int K, int items, int Rpad, i
   LAUNCH(c, (split_kernel<D, TR>), g, 2 * TR, 0, o, R, K, Rpad, nks, e, planes);
 }
 
+// Digit planes and row exponents of one operand: in the workspace, or for a
+// kept operand (context-owned, constant) from the context's store, cut on
+// first use.
+template <int D, int TR>
+void operand_planes(Ctx &c, const TcOpnd &o, int R, int K, int items, int Rpad, int nks, int *&e,
+                    __nv_bfloat16 *&planes) {
+  const size_t nplane = (size_t)items * (Rpad / TR) * nks * D * TR * BK;
+  if (o.keep && items == 1 && !o.q) {
+    for (const Ctx::TcKept &k : c.tc_keep)
+      if (k.p == o.p && k.s0 == o.s0 && k.s1 == o.s1 && k.sk == o.sk && k.d == o.d && k.R == R &&
+          k.K == K && k.D == D && k.TR == TR) {
+        e = k.e;
+        planes = static_cast<__nv_bfloat16 *>(k.planes);
+        return;
+      }
+    e = reinterpret_cast<int *>(c.dmalloc(((size_t)Rpad + 1) / 2));
+    planes = reinterpret_cast<__nv_bfloat16 *>(c.dmalloc((nplane * 2 + 7) / 8));
+    split_operand<D, TR>(c, o, R, K, 1, Rpad, nks, e, planes);
+    c.tc_keep.push_back(Ctx::TcKept{o.p, o.s0, o.s1, o.sk, o.d, R, K, D, TR, e, planes});
+    return;
+  }
+  e = c.ws.i32((size_t)items * Rpad);
+  planes = reinterpret_cast<__nv_bfloat16 *>(c.ws.dbl((nplane * 2 + 7) / 8));
+  split_operand<D, TR>(c, o, R, K, items, Rpad, nks, e, planes);
+}
+
 template <int D, int NST>
 void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double alpha,
              const TcOpnd &A, const TcOpnd &B, double beta, double *C, long long cm0, long long cm1,
@@ -383,12 +409,10 @@ void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double 
   const int nchunk = (nks * BK + KCHUNK - 1) / KCHUNK;
   const int itemsA = (batch - 1) / divA + 1, itemsB = (batch - 1) / divB + 1;
   size_t mk = c.ws.mark();
-  int *ea = c.ws.i32((size_t)itemsA * Mpad);
-  int *eb = c.ws.i32((size_t)itemsB * Npad);
-  auto *pa = reinterpret_cast<__nv_bfloat16 *>(
-      c.ws.dbl(((size_t)itemsA * Mt * nks * D * TM * BK * 2 + 7) / 8));
-  auto *pb = reinterpret_cast<__nv_bfloat16 *>(
-      c.ws.dbl(((size_t)itemsB * Nt * nks * D * TN * BK * 2 + 7) / 8));
+  int *ea = nullptr, *eb = nullptr;
+  __nv_bfloat16 *pa = nullptr, *pb = nullptr;
+  operand_planes<D, TM>(c, A, M, K, itemsA, Mpad, nks, ea, pa);
+  operand_planes<D, TN>(c, B, N, K, itemsB, Npad, nks, eb, pb);
   double *part = nchunk > 1 ? c.ws.dbl((size_t)batch * nchunk * M * N) : nullptr;
   if (!c.tcg_err) {
     c.tcg_err = reinterpret_cast<int *>(c.dmalloc(1));
@@ -398,8 +422,6 @@ void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double 
   static const cudaError_t attr = cudaFuncSetAttribute(
       tcg_kernel<D, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg_smem<D, NST>());
   TCTL_CUDA(attr);
-  split_operand<D, TM>(c, A, M, K, itemsA, Mpad, nks, ea, pa);
-  split_operand<D, TN>(c, B, N, K, itemsB, Npad, nks, eb, pb);
   TcgArgs ar;
   ar.M = M;
   ar.N = N;
@@ -466,7 +488,7 @@ void gemm_tc(Ctx &c, int digits, int M, int N, int K, int batch, int divA, int d
 
 void gemm_x(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double alpha, const double *A,
             int lda, long long sA, const double *B, int ldb, long long sB, double beta, double *C,
-            int ldc, long long sC, int batch, int divA, int divB) {
+            int ldc, long long sC, int batch, int divA, int divB, bool a_kept) {
   const bool use = digits > 0 && c.o.tc_gemm != 0;
   // a batch that reuses one operand (stride 0) splits it once
   if (sA == 0) divA = batch;
@@ -481,6 +503,7 @@ void gemm_x(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double al
   // op(A)(i, kk) = ta ? A[kk + i lda] : A[i + kk lda];  op(B)(kk, j) = tb ? B[j + kk ldb] : B[kk + j ldb]
   TcOpnd opA{A, ta ? (long long)lda : 1ll, 0ll, ta ? 1ll : (long long)lda, sA, 1 << 30};
   TcOpnd opB{B, tb ? 1ll : (long long)ldb, 0ll, tb ? (long long)ldb : 1ll, sB, 1 << 30};
+  opA.keep = a_kept && batch == 1;
   if (!swap)
     gemm_tc(c, digits, m, n, k, batch, divA, divB, alpha, opA, opB, beta, C, 1, 0, 1 << 30, ldc, sC);
   else  // C^T = op(B)^T op(A)^T: rows j of op(B) become the 128-row operand

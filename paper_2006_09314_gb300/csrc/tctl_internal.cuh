@@ -114,6 +114,16 @@ struct Ctx {
   uint64_t rng_counter = 0;
   std::vector<void *> owned;         // device allocations freed at destroy
   int *tcg_err = nullptr;            // tensor-core GEMM wait-timeout flag (device)
+  // digit planes of constant tensor-core operands (the operator's factor
+  // matrices), keyed by the operand's address, strides and split geometry
+  struct TcKept {
+    const double *p;
+    long long s0, s1, sk;
+    int d, R, K, D, TR;
+    int *e;
+    void *planes;
+  };
+  std::vector<TcKept> tc_keep;
   bool prof = false;                 // record events around every launch
   bool trace = false;                // TCTL_TRACE=1: per-step ranks on stderr
   std::vector<std::string> interned;  // stable storage of generated profile names
@@ -187,6 +197,9 @@ struct TcOpnd {
   long long s0, s1, sk, sb;
   int d;
   const double *q = nullptr;
+  // the operand is owned by the context and never changes: its digit planes
+  // are cut on first use and kept (Ctx::tc_keep)
+  bool keep = false;
 };
 // C[b sC' + (m % cd) cm0 + (m / cd) cm1 + j cj] = alpha sum_k A(m, k) B(j, k) + beta C,
 // batch item b of A / B = b / divA, b / divB; digits 4 (28-bit) or 6 (42-bit).
@@ -198,7 +211,7 @@ bool gemm_tc_fits(int M, int N, int K, int batch);
 void gemm_x(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double alpha,
             const double *A, int lda, long long sA, const double *B, int ldb, long long sB,
             double beta, double *C, int ldc, long long sC, int batch = 1, int divA = 1,
-            int divB = 1);
+            int divB = 1, bool a_kept = false);
 // Column-major C = alpha op(A) op(B) + beta C on the tensor cores whatever the shape.
 void gemm_tc_cm(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double alpha,
                 const double *A, int lda, const double *B, int ldb, double beta, double *C, int ldc);

@@ -475,7 +475,8 @@ static void kr_t_gemm(Ctx &c, int n, const double *X, int ldx, int ra, const dou
   if (M <= 0 || N <= 0) return;
   if (c.o.tc_gemm && gemm_tc_fits(std::max(M, N), std::min(M, N), n, 1)) {
     const TcOpnd kr{X, (long long)ldx, (long long)ldy, 1, 0, ra, Y};
-    const TcOpnd e{E, (long long)lde, 0, 1, 0, 1 << 30};
+    TcOpnd e{E, (long long)lde, 0, 1, 0, 1 << 30};
+    e.keep = true;  // E is a factor matrix of the context's operator
     // the larger dimension takes the 128-row side of the tile
     if (M >= N)
       gemm_tc(c, kDigits, M, N, n, 1, 1, 1, 1.0, kr, e, 0.0, out, 1, 0, 1 << 30, ldo, 0);
@@ -556,7 +557,7 @@ static void sketch_mode(Ctx &c, const Sep &D, const Tucker &x, const double *Cl,
   for (int s0 = 0; s0 < ls; s0 += sc) {
     const int ns = std::min(sc, ls - s0);
     gemm_x(c, kDigits, false, true, n, r[l] * ns, D.rD[l], 1.0, D.B[l], n, 0,
-           uT + (size_t)r[l] * s0, r[l] * ls, 0, 0.0, W, n, 0);
+           uT + (size_t)r[l] * s0, r[l] * ls, 0, 0.0, W, n, 0, 1, 1, 1, true);
     const long long tot = (long long)n * ns;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
     LAUNCH(c, rowdot_kernel, blocks, 256, 0, n, r[l], ns, x.Q[l], n, W, n, Y + (size_t)n * s0, n);
