@@ -87,7 +87,7 @@ typedef struct {
                          largest sketch column (default 0.03)                          */
   int tc_gemm;        /* rank-structured contractions (sketches, core projection of
                          the Hadamard products): 1 = tensor cores, BF16 digit split
-                         (4 digits for the sketches, 6 = 42 bits for the core; FP32
+                         (6 digits = 42 bits for sketches and core; FP32
                          accumulate with exact low levels, FP64 result; default);
                          0 = FP64 FMA. Gram matrices, orthonormalisation and HOSVD
                          always run in FP64.                                           */
@@ -246,6 +246,22 @@ int tctl_get_stats(tctl_ctx *ctx, tctl_stats *st);
 int tctl_gemm(tctl_ctx *ctx, int digits, int trans_a, int trans_b, int m, int n, int k,
               double alpha, const double *A, int lda, const double *B, int ldb, double beta,
               double *C, int ldc);
+
+/* C (ra rb x n) = alpha KR(X, Y)^T B + beta C for DEVICE FP64 column-major
+ * matrices: X (k x ra, ld ldx), Y (k x rb, ld ldy), B (k x n, ld ldb), C (ld
+ * ldc), where column a + ra b of the Khatri-Rao product KR(X, Y) is the
+ * entrywise product X(:, a) .* Y(:, b) -- the contraction of the sketches and
+ * core projections of Section 3.4's Hadamard products (probe factors and
+ * factor-basis products), contracted over the grid index. digits = 0: the
+ * product is formed in the context's workspace and multiplied by the FP64
+ * kernels; digits = 4 or 6: the tensor-core digit split of tctl_gemm forms
+ * each product X(i, a) Y(i, b) while splitting (nothing k x ra rb is stored),
+ * with the same result as tctl_gemm on the stored product. Ordered on the
+ * context's stream; synchronizes when digits > 0. Errors: TCTL_E_ARG,
+ * TCTL_E_NOMEM (workspace, digits = 0), TCTL_E_CUDA, TCTL_E_NUMERIC. */
+int tctl_gemm_kr(tctl_ctx *ctx, int digits, int k, int ra, int rb, int n, double alpha,
+                 const double *X, int ldx, const double *Y, int ldy, const double *B, int ldb,
+                 double beta, double *C, int ldc);
 
 /* The fitted exponential sum behind expsum_src = 1 (host only, no device
  * work, no context): g(s) ~ sum_k w_k exp(-t_k s) on [s_min, s_max], t_k >= 0

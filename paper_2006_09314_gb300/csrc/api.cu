@@ -554,6 +554,37 @@ int tctl_gemm(tctl_ctx *ctx, int digits, int trans_a, int trans_b, int m, int n,
   }
 }
 
+int tctl_gemm_kr(tctl_ctx *ctx, int digits, int k, int ra, int rb, int n, double alpha,
+                 const double *X, int ldx, const double *Y, int ldy, const double *B, int ldb,
+                 double beta, double *C, int ldc) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c) return TCTL_E_ARG;
+  try {
+    if (k < 0 || ra < 0 || rb < 0 || n < 0) fail(TCTL_E_ARG, "negative dimension");
+    if (digits != 0 && digits != 4 && digits != 6) fail(TCTL_E_ARG, "digits must be 0, 4 or 6");
+    const long long m = (long long)ra * rb;
+    if (m > (1 << 30)) fail(TCTL_E_ARG, "ra * rb too large");
+    if ((m && n && k) && (!X || !Y || !B || !C)) fail(TCTL_E_ARG, "NULL matrix");
+    if (ldx < std::max(1, k) || ldy < std::max(1, k) || ldb < std::max(1, k) ||
+        ldc < std::max<long long>(1, m))
+      fail(TCTL_E_ARG, "leading dimension too small");
+    if (m == 0 || n == 0) return TCTL_OK;
+    if (digits == 0 || k == 0) {
+      size_t mk = c->ws.mark();
+      double *KR = c->ws.dbl((size_t)std::max(k, 1) * m);
+      if (k > 0) khatri_rao(*c, k, X, ldx, ra, Y, ldy, rb, KR, k);
+      gemm(*c, true, false, (int)m, n, k, alpha, KR, std::max(k, 1), 0, B, ldb, 0, beta, C, ldc, 0);
+      c->ws.reset(mk);
+    } else {
+      gemm_tc_kr(*c, digits, k, ra, rb, n, alpha, X, ldx, Y, ldy, B, ldb, beta, C, ldc);
+      tcg_check(*c);
+    }
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(c, e);
+  }
+}
+
 int tctl_expsum_fit(double alpha, double beta, double s_min, double s_max, double tol, double *t,
                     double *w, int cap, int *r, double *err) {
   try {

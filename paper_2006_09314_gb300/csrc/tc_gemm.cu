@@ -521,6 +521,19 @@ void gemm_tc_cm(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, doubl
   gemm_tc(c, digits, m, n, k, 1, 1, 1, alpha, opA, opB, beta, C, 1, 0, 1 << 30, ldc, 0);
 }
 
+void gemm_tc_kr(Ctx &c, int digits, int k, int ra, int rb, int n, double alpha, const double *X,
+                int ldx, const double *Y, int ldy, const double *B, int ldb, double beta, double *C,
+                int ldc) {
+  const int m = ra * rb;
+  if (m <= 0 || n <= 0) return;
+  if (k <= 0) fail(TCTL_E_ARG, "k must be positive");
+  if ((m + TM - 1) / TM > 65535 || (n + TN - 1) / TN > 65535)
+    fail(TCTL_E_ARG, "matrix too large for one tensor-core GEMM launch");
+  const TcOpnd kr{X, (long long)ldx, (long long)ldy, 1ll, 0, ra, Y};
+  const TcOpnd opB{B, (long long)ldb, 0ll, 1ll, 0, 1 << 30};
+  gemm_tc(c, digits, m, n, k, 1, 1, 1, alpha, kr, opB, beta, C, 1, 0, 1 << 30, ldc, 0);
+}
+
 void tcg_check(Ctx &c) {
   if (!c.tcg_err) return;
   int herr = 0;

@@ -212,6 +212,11 @@ void gemm_x(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double al
             const double *A, int lda, long long sA, const double *B, int ldb, long long sB,
             double beta, double *C, int ldc, long long sC, int batch = 1, int divA = 1,
             int divB = 1, bool a_kept = false);
+// C (ra rb x n) = alpha KR(X, Y)^T B + beta C on the tensor cores, the
+// Khatri-Rao rows formed inside the digit split (X k x ra, Y k x rb, B k x n).
+void gemm_tc_kr(Ctx &c, int digits, int k, int ra, int rb, int n, double alpha, const double *X,
+                int ldx, const double *Y, int ldy, const double *B, int ldb, double beta, double *C,
+                int ldc);
 // Column-major C = alpha op(A) op(B) + beta C on the tensor cores whatever the shape.
 void gemm_tc_cm(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double alpha,
                 const double *A, int lda, const double *B, int ldb, double beta, double *C, int ldc);

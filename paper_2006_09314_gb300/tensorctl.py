@@ -35,7 +35,7 @@ EXPORTED = [
     "tctl_solve_host", "tctl_cp_alloc", "tctl_cp_free", "tctl_get_eigs",
     "tctl_get_stats", "tctl_launch_count", "tctl_destroy", "tctl_last_error",
     "tctl_profile_enable", "tctl_profile_report", "tctl_eig1d_noalloc", "tctl_get_expsum",
-    "tctl_expsum_fit", "tctl_gemm", "tctl_precond_fit", "tctl_precond_dataset",
+    "tctl_expsum_fit", "tctl_gemm", "tctl_gemm_kr", "tctl_precond_fit", "tctl_precond_dataset",
     "tctl_mlp_model_size", "tctl_mlp_train", "tctl_mlp_grad", "tctl_mlp_forward",
     "tctl_apply_state", "tctl_map_constants", "tctl_solve_batch",
 ]
@@ -136,6 +136,7 @@ def load(build_if_missing: bool = True):
         "tctl_get_expsum": (I, [P, I, P, P, P, I, P]),
         "tctl_expsum_fit": (I, [D, D, D, D, D, P, P, I, P, P]),
         "tctl_gemm": (I, [P, I, I, I, I, I, I, D, P, I, P, I, D, P, I]),
+        "tctl_gemm_kr": (I, [P, I, I, I, I, I, D, P, I, P, I, P, I, D, P, I]),
         "tctl_precond_fit": (I, [D, D, D, D, I, P, P, P]),
         "tctl_precond_dataset": (I, [I, I, ctypes.c_ulonglong, I, P, P, P]),
         "tctl_mlp_model_size": (I, [I]),
@@ -394,6 +395,29 @@ def tctl_gemm(ctx, digits, A, B, C=None, trans_a=False, trans_b=False, alpha=1.0
     return C
 
 
+def tctl_gemm_kr(ctx, digits, X, Y, B, C=None, alpha=1.0, beta=0.0):
+    """C = alpha KR(X, Y)^T B + beta C on CUDA float64 tensors given as row-major views.
+
+    X (ra, k), Y (rb, k), B (n, k) hold the columns of the column-major k x ra,
+    k x rb, k x n operands as rows; C (n, ra rb) is the column-major
+    (ra rb) x n result: C[j, a + ra b] = alpha sum_i X[a, i] Y[b, i] B[j, i].
+    """
+    import torch
+    for t in (X, Y, B):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("X, Y, B must be contiguous CUDA float64 tensors")
+    ra, k = X.shape
+    rb, n = Y.shape[0], B.shape[0]
+    if Y.shape[1] != k or B.shape[1] != k:
+        raise ValueError("X, Y, B must share the contracted length")
+    if C is None:
+        C = torch.zeros(n, ra * rb, dtype=torch.float64, device=X.device)
+    _check(load().tctl_gemm_kr(ctx, digits, k, ra, rb, n, alpha, X.data_ptr(), max(k, 1),
+                               Y.data_ptr(), max(k, 1), B.data_ptr(), max(k, 1), beta,
+                               C.data_ptr(), max(ra * rb, 1)), ctx)
+    return C
+
+
 def tctl_precond_fit(alpha, beta, s_min, s_max, r):
     """r free-node preconditioner sum: (theta, p, delta) (host only)."""
     import numpy as np
@@ -568,6 +592,9 @@ class Context:
 
     def gemm(self, digits, A, B, C=None, trans_a=False, trans_b=False, alpha=1.0, beta=0.0):
         return tctl_gemm(self.handle, digits, A, B, C, trans_a, trans_b, alpha, beta)
+
+    def gemm_kr(self, digits, X, Y, B, C=None, alpha=1.0, beta=0.0):
+        return tctl_gemm_kr(self.handle, digits, X, Y, B, C, alpha, beta)
 
     def expsum(self, which=0):
         return tctl_get_expsum(self.handle, which)

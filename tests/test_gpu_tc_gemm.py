@@ -94,3 +94,45 @@ def test_tc_gemm_argument_errors(ctx):
     lib = T.load()
     assert lib.tctl_gemm(ctx.handle, 5, 0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4) == -1
     assert lib.tctl_gemm(ctx.handle, 6, 0, 0, 4, 4, 4, 1.0, None, 2, None, 4, 0.0, None, 4) == -1
+
+
+@pytest.mark.parametrize("k,ra,rb,n", [(700, 5, 37, 70), (2048, 12, 36, 126), (33, 1, 1, 1),
+                                       (257, 64, 3, 130)])
+@pytest.mark.parametrize("digits", [4, 6])
+def test_gemm_kr_equals_stored_product(ctx, k, ra, rb, n, digits):
+    """The Khatri-Rao operand formed inside the digit split gives, bit for bit, what
+    tctl_gemm gives on the stored product (same split, same kernel), and meets the
+    digit-split error bound against FP64 numpy."""
+    g = torch.Generator().manual_seed(k * 7 + ra * 3 + rb + digits)
+    X = torch.randn(ra, k, generator=g, dtype=torch.float64).cuda()
+    Y = torch.randn(rb, k, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(n, k, generator=g, dtype=torch.float64).cuda()
+    C0 = torch.randn(n, ra * rb, generator=g, dtype=torch.float64).cuda()
+    C = ctx.gemm_kr(digits, X, Y, B, C=C0.clone(), alpha=0.75, beta=-0.5)
+    KR = (Y[:, None, :] * X[None, :, :]).reshape(ra * rb, k).contiguous()  # row a + ra b
+    Cs = C0.clone()
+    # column-major: Cs^T (m x n) = 0.75 KR^T(k x m)^T B (k x n) - 0.5 Cs^T, trans_a = 1
+    lib = T.load()
+    assert lib.tctl_gemm(ctx.handle, digits, 1, 0, ra * rb, n, k, 0.75, KR.data_ptr(), k,
+                         B.data_ptr(), k, -0.5, Cs.data_ptr(), ra * rb) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(C, Cs)
+    ref = 0.75 * (B.cpu().numpy() @ KR.cpu().numpy().T) - 0.5 * C0.cpu().numpy()
+    bound = _bound(KR.cpu().numpy().T, B.cpu().numpy().T, digits, True, False).T
+    assert np.all(np.abs(C.cpu().numpy() - ref) <= bound * 0.75 + 1e-15 * np.abs(C0.cpu().numpy()))
+
+
+def test_gemm_kr_fp64_path_and_errors(ctx):
+    g = torch.Generator().manual_seed(5)
+    k, ra, rb, n = 300, 7, 9, 11
+    X = torch.randn(ra, k, generator=g, dtype=torch.float64).cuda()
+    Y = torch.randn(rb, k, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(n, k, generator=g, dtype=torch.float64).cuda()
+    C = ctx.gemm_kr(0, X, Y, B)
+    KR = (Y[:, None, :] * X[None, :, :]).reshape(ra * rb, k)
+    ref = B.cpu().numpy() @ KR.cpu().numpy().T
+    assert np.abs(C.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    lib = T.load()
+    assert lib.tctl_gemm_kr(ctx.handle, 5, 4, 2, 2, 4, 1.0, None, 4, None, 4, None, 4, 0.0, None, 4) == -1
+    assert lib.tctl_gemm_kr(ctx.handle, 6, 4, 2, 2, 4, 1.0, X.data_ptr(), 2, Y.data_ptr(), 4,
+                            B.data_ptr(), 4, 0.0, C.data_ptr(), 4) == -1
