@@ -378,6 +378,14 @@ def ours_arm(args, rank, world):
             errs.append(oracle_error(p, xw, xU, pool))
     passing = B if args.no_check else sum(e <= 1e-6 for e in errs)
     value = (world * passing * args.steps) / (total_ms_max / 1000.0)
+    if variants and errs:
+        # each variant solve's oracle error is at most the main solve's (checked)
+        # plus their distance: a solve counts as verified when that bound is <= 1e-6
+        for v in variants.values():
+            bnd = [e + d for e, d in zip(errs, v["rel_diff_to_main"])]
+            v["err_bound_vs_oracle"] = bnd
+            v["verified_le_1e-6"] = sum(b <= 1e-6 for b in bnd)
+            v["verified_solves_per_s"] = v["solves_per_s"] * v["verified_le_1e-6"] / len(bnd)
     e2e_value = world * B / statistics.mean(e2e_times)
 
     # the same kernels traced on one solve alone (alpha = 0.5, beta = 1e-2): per-launch
