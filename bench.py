@@ -27,6 +27,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -134,7 +135,9 @@ class Clocks:
     def __init__(self, dev):
         self.dev = dev
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{dev}.csv")
+        # the raw samples go to $TCTL_CLOCKS_DIR (default: the temp directory)
+        out = os.environ.get("TCTL_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_rank{dev}.csv")
 
     def start(self):
         try:

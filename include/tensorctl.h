@@ -215,7 +215,7 @@ typedef struct {
   double latency_ms;
 } tctl_batch_item;
 
-/* Batched solves (SURVEY f-2): `count` independent problems of any n, rank,
+/* Batched solves: `count` independent problems of any n, rank,
  * alpha and beta, scheduled dynamically over `workers` host threads, each
  * issuing to its own stream so that the problems overlap on the GPU. Returns
  * TCTL_OK, or the first non-OK item status (every item is attempted). */
@@ -276,7 +276,7 @@ int tctl_gemm_kr(tctl_ctx *ctx, int digits, int k, int ra, int rb, int n, double
 int tctl_expsum_fit(double alpha, double beta, double s_min, double s_max, double tol, double *t,
                     double *w, int cap, int *r, double *err);
 
-/* Learned preconditioner sums (SURVEY f-1; host buffers, no context).
+/* Learned preconditioner sums (host buffers, no context).
  * tctl_precond_fit: r free nodes theta (ascending) and weights p > 0 of
  * P(s) = s sum_k p_k exp(-theta_k s) ~ 1/F2(s) on [s_min, s_max]
  * (Levenberg-Marquardt on log parameters, Lawson reweighting; started from
