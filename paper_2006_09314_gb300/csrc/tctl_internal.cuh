@@ -11,6 +11,16 @@
 
 #include "../../include/tensorctl.h"
 
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define TCTL_HAVE_NVTX 1
+#endif
+#endif
+#ifndef TCTL_HAVE_NVTX
+#define TCTL_HAVE_NVTX 0
+#endif
+
 namespace tctl {
 
 // Errors are C++ exceptions inside the library; every extern "C" entry point
@@ -171,12 +181,24 @@ struct Ctx {
   } while (0)
 
 // Scoped algorithm phase for the per-kernel trace (names must be literals).
+// Each scope is also an NVTX range (no-op unless a profiler is attached), so
+// ncu / nsys can filter kernels by PCG step and phase (ncu --nvtx).
 struct PhaseScope {
   Ctx &c;
   const char *Ctx::*slot;
   const char *prev;
-  PhaseScope(Ctx &cc, const char *Ctx::*s, const char *p) : c(cc), slot(s), prev(cc.*s) { c.*s = p; }
-  ~PhaseScope() { c.*slot = prev; }
+  PhaseScope(Ctx &cc, const char *Ctx::*s, const char *p) : c(cc), slot(s), prev(cc.*s) {
+    c.*s = p;
+#if TCTL_HAVE_NVTX
+    nvtxRangePushA(p);
+#endif
+  }
+  ~PhaseScope() {
+#if TCTL_HAVE_NVTX
+    nvtxRangePop();
+#endif
+    c.*slot = prev;
+  }
 };
 #define TCTL_CAT2(a, b) a##b
 #define TCTL_CAT(a, b) TCTL_CAT2(a, b)
