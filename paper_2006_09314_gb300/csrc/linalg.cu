@@ -313,12 +313,14 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
           long long sC, int batch, int divA, int divB) {
   if (m <= 0 || n <= 0 || batch <= 0) return;
   if (k <= 0) {
-    // C = beta C
-    if (beta == 0.0) {
+    // C = beta C (an empty contraction)
+    if (beta != 1.0)
       for (int b = 0; b < batch; ++b)
-        for (int j = 0; j < n; ++j)
-          TCTL_CUDA(cudaMemsetAsync(C + b * sC + (long long)j * ldc, 0, sizeof(double) * m, c.st));
-    }
+        for (int j = 0; j < n; ++j) {
+          double *col = C + b * sC + (long long)j * ldc;
+          if (beta == 0.0) TCTL_CUDA(cudaMemsetAsync(col, 0, sizeof(double) * m, c.st));
+          else axpby(c, (size_t)m, beta, col, 0.0, col);  // col = beta col
+        }
     return;
   }
   if (batch == 1 && n <= 16 && m >= 64 && (long long)m * n * k >= (1 << 16)) {
