@@ -1,0 +1,62 @@
+"""Host logic of bench.py that runs without a GPU: the oracle-error status of
+the method variants (bound from the main solve, direct oracle check of the
+learned form's open cases, and a failed check leaving only the bound)."""
+import numpy as np
+import pytest
+
+import bench
+from oracle import formats as F
+from oracle import fullgrid as fg
+from oracle import operator as op
+from paper_2006_09314_gb300.inputs import make_problem
+
+
+def _exact_cp(p):
+    """The oracle's exact solution of problem p as a canonical tensor of rank n^2."""
+    lams, Vs = zip(*[op.eig(*op.assemble(p.coeffs[l])) for l in range(3)])
+    u = fg.solve_exact(F.cp_full(p.yw, p.yU), lams, Vs, p.alpha, p.beta)
+    n = p.n
+    U = [np.zeros((n, n * n)) for _ in range(3)]
+    for j in range(n):
+        for k in range(n):
+            c = j + n * k
+            U[0][:, c] = u[:, j, k]
+            U[1][j, c] = 1.0
+            U[2][k, c] = 1.0
+    return np.ones(n * n), U
+
+
+@pytest.fixture(scope="module")
+def pool():
+    p = bench._pool(2)
+    yield p
+    p.close()
+
+
+def test_verify_variants_bound_and_direct_check(pool):
+    probs = [make_problem(8, 0.5, 1e-2, 2, s) for s in (3, 4)]
+    sols = [_exact_cp(p) for p in probs]
+    errs = [5e-7, 5e-7]
+    variants = {"learned_pre": {"rel_diff_to_main": [2e-6, 1e-7], "solves_per_s": 10.0},
+                "fp64_sinc": {"rel_diff_to_main": [1e-7, 7e-7], "solves_per_s": 4.0}}
+    bench.verify_variants(variants, {"learned_pre": sols}, errs, probs, pool)
+    lp, sc = variants["learned_pre"], variants["fp64_sinc"]
+    assert list(lp["rel_err_vs_oracle_direct"]) == ["0"]          # only the open case
+    assert lp["rel_err_vs_oracle_direct"]["0"] < 1e-12            # exact solution
+    assert lp["verified_le_1e-6"] == 2 and lp["verified_solves_per_s"] == 10.0
+    assert sc["verified_le_1e-6"] == 1 and sc["verified_solves_per_s"] == 2.0
+    assert "rel_err_vs_oracle_direct" not in sc                   # bound only
+
+
+def test_verify_variants_wrong_solution_and_failed_check(pool):
+    probs = [make_problem(8, 0.5, 1e-2, 2, 5)]
+    w, U = _exact_cp(probs[0])
+    wrong = (1.01 * w, U)                                         # 1% off
+    v = {"learned_pre": {"rel_diff_to_main": [3e-6], "solves_per_s": 1.0}}
+    bench.verify_variants(v, {"learned_pre": [wrong]}, [5e-7], probs, pool)
+    assert abs(v["learned_pre"]["rel_err_vs_oracle_direct"]["0"] - 0.01) < 1e-9
+    assert v["learned_pre"]["verified_le_1e-6"] == 0
+    v = {"learned_pre": {"rel_diff_to_main": [3e-6], "solves_per_s": 1.0}}
+    bench.verify_variants(v, {"learned_pre": [None]}, [5e-7], probs, pool)
+    assert "direct_check_failed" in v["learned_pre"]
+    assert v["learned_pre"]["verified_le_1e-6"] == 0
