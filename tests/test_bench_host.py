@@ -60,3 +60,22 @@ def test_verify_variants_wrong_solution_and_failed_check(pool):
     bench.verify_variants(v, {"learned_pre": [None]}, [5e-7], probs, pool)
     assert "direct_check_failed" in v["learned_pre"]
     assert v["learned_pre"]["verified_le_1e-6"] == 0
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the oracle timed on the host) prints one JSON
+    line with the keys of the benchmark contract."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--n", "16"], cwd=root, capture_output=True,
+                         text=True, timeout=300, check=True).stdout.strip().splitlines()
+    line = json.loads(out[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
