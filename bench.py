@@ -208,6 +208,16 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, world, device):
+    """The largest value over the ranks (the job takes as long as its slowest rank)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _problems(n, rank, batch):
     """The (alpha, beta) grid of the n-point rank-structured configuration, seeded per problem."""
     from paper_2006_09314_gb300.inputs import make_problem, problem_seed
@@ -320,11 +330,7 @@ def ours_arm(args, rank, world):
         barrier()
     launches = sum(c.launch_count() for c in ctxs) - l0
     clk = clocks.stop()
-    total_ms = sum(times)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
+    total_ms_max = max_over_ranks(sum(times), world, "cuda")
     sols = [r[0] for r in results]
     stats = [r[1] for r in results]
 
