@@ -63,6 +63,22 @@ def test_inputs_generator_is_seeded():
     assert a.coeffs.min() >= 0.5 - 1e-15 and a.coeffs.max() <= 1.5 + 1e-15
 
 
+def test_uneven_batch_generator():
+    """The uneven batch: seeded, n from the choices, design rank 1..8,
+    alpha in [0.2, 0.8], log10 beta in [-4, 0]."""
+    import numpy as np
+    from paper_2006_09314_gb300.inputs import batch_problems
+    a = batch_problems(40, 11)
+    b = batch_problems(40, 11)
+    assert [p.n for p in a] == [p.n for p in b]
+    assert all(np.array_equal(x.coeffs, y.coeffs) for x, y in zip(a, b))
+    assert {p.n for p in a} <= set(range(64, 513, 32)) and len({p.n for p in a}) > 5
+    assert all(1 <= len(p.yw) <= 8 for p in a)
+    assert all(0.2 <= p.alpha <= 0.8 and 1e-4 <= p.beta <= 1.0 for p in a)
+    assert batch_problems(3, 12)[0].n != a[0].n or not np.array_equal(batch_problems(3, 12)[0].coeffs,
+                                                                       a[0].coeffs)
+
+
 def test_map_constants_without_gpu():
     """(beta_p, gamma) of Section 3.1 -> beta = gamma / beta_p^2, u_paper = u / beta_p."""
     from paper_2006_09314_gb300 import tensorctl as T
