@@ -69,10 +69,11 @@ typedef struct {
   int rank_cap;       /* maximal Tucker rank per mode inside the solver (default and
                          maximum 64)                                                  */
   int precision;      /* full-grid mode products: 0 = FP64 FMA (default); 1 = tensor
-                         cores, BF16 digit split (4 x 7-bit digits, shared row/column
-                         exponents, 10 products, FP32 accumulate; ~1e-7 relative per
-                         product; needs n % 128 == 0, n <= 1024). The rank-structured
-                         solver always runs in FP64.                                   */
+                         cores, BF16 digit split (5 x 7-bit digits, shared row/column
+                         exponents, 15 products, exact leading levels, FP32 storage
+                         between products; ~1e-7 relative per solve; needs
+                         n % 128 == 0, n <= 1024). The rank-structured solver's
+                         contractions are chosen by tc_gemm.                          */
   int basis;          /* 1 = PCG vectors kept in eigenbasis coordinates (default);
                          0 = paper form, mode products with V_l in every apply         */
   int expsum_src;     /* separable F2: 0 = sinc quadrature (Section 3.4); 1 = fitted
@@ -121,7 +122,8 @@ typedef struct {
   double t_setup_ms;     /* time of tctl_setup                                       */
   double t_solve_ms;     /* time of the last tctl_pcg_solve                          */
   int expsum_used;       /* representation of F2 in use: 0 sinc, 1 fitted             */
-  int pre_used;          /* preconditioner in use: 0 NNLS nodes, 1 fitted, 2 learned  */
+  int pre_used;          /* preconditioner in use: 0 NNLS nodes, 1 fitted, 2 learned,
+                            3 anisotropic Laplacian (case (A))                         */
   double pre_delta;      /* its measured max |P(s) F2(s) - 1| on [s_min, s_max]       */
   double ws_peak_mb;     /* peak use of the context's workspace arena so far (MiB)    */
   double ws_size_mb;     /* size of the arena (MiB)                                    */
@@ -133,8 +135,10 @@ int tctl_default_opts(tctl_opts *o);
 /* Builds the solver for one coefficient set (Sections 3.2-3.5):
  * assembles A_(l) from coeffs (HOST, 3 x (n+1) doubles, row l holds
  * a_l(x_{i-1/2}) for i = 1..n+1), computes the 1D eigenpairs on the GPU in
- * FP64, the spectral interval, the sinc exp-sum of F2 (Section 3.4) and the
- * preconditioner exp-sum (Section 3.5, case (B)), and their factor matrices.
+ * FP64, the spectral interval, the exponential sum of F2 (fitted by default,
+ * the sinc quadrature of Section 3.4 with expsum_src = 0 or as fallback) and
+ * the preconditioner sum (Section 3.5, case (B) by default, case (A) with
+ * pre_src = 3), and their factor matrices.
  * n >= 2, 0 < alpha <= 1, beta > 0, eps_trunc in (0, 1). opts may be NULL.
  * cuda_stream: a cudaStream_t (NULL = the calling host thread's default
  * stream: the library is built with per-thread default streams; pass
