@@ -153,7 +153,9 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha,
  * (TCTL_E_RANK_CAP otherwise, y then holds the first y->cap terms). */
 int tctl_apply_op(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y);
 
-/* y = trunc(P(A) x, eps_trunc), P ~ F2^-1 the preconditioner (Section 3.5 (B)). */
+/* y = trunc(P(A) x, eps_trunc), P ~ F2^-1 the preconditioner chosen by
+ * opts.pre_src (Section 3.5: case (B) in the operators' eigenbasis by
+ * default, case (A) in the sine basis with pre_src = 3). */
 int tctl_apply_precond(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y);
 
 /* State recovery (state equation "State" of Section 3.1 with beta_p = 1):
