@@ -110,6 +110,48 @@ def test_P3_dense_kronecker_sum(n, alpha, beta):
     assert np.allclose(op.stencil_apply(pr.coeffs, X).reshape(-1), K @ X.reshape(-1), rtol=1e-12)
 
 
+# ---------------------------------------------------------------- state equation pins
+@pytest.mark.parametrize("n", [10, 16])
+def test_state_alpha_one_inverts_the_stencil(n):
+    """State equation (Section 3.1) at alpha = 1: y = A^-1 u, so the 7-point stencil of y is u."""
+    pr = make_problem(n, 1.0, 1e-2, 3, 131)
+    lams, Vs = _eig3(pr)
+    U = F.cp_full(pr.yw, pr.yU)
+    Y = fg.state_exact(U, lams, Vs, 1.0)
+    assert np.linalg.norm(op.stencil_apply(pr.coeffs, Y) - U) / np.linalg.norm(U) < 1e-11
+    # beta_p scales the state linearly
+    Y3 = fg.state_exact(U, lams, Vs, 1.0, beta_state=3.0)
+    assert np.linalg.norm(Y3 - 3.0 * Y) <= 1e-14 * np.linalg.norm(Y3)
+
+
+def test_state_half_power_composes_to_the_inverse():
+    """A^-1/2 applied twice is A^-1: the stencil of the twice-applied state returns u."""
+    n = 12
+    pr = make_problem(n, 0.5, 1e-2, 3, 132)
+    lams, Vs = _eig3(pr)
+    U = F.cp_full(pr.yw, pr.yU)
+    Y2 = fg.state_exact(fg.state_exact(U, lams, Vs, 0.5), lams, Vs, 0.5)
+    assert np.linalg.norm(op.stencil_apply(pr.coeffs, Y2) - U) / np.linalg.norm(U) < 1e-11
+    # and the quarter power four times
+    Y4 = U
+    for _ in range(4):
+        Y4 = fg.state_exact(Y4, lams, Vs, 0.25)
+    assert np.linalg.norm(op.stencil_apply(pr.coeffs, Y4) - U) / np.linalg.norm(U) < 1e-11
+
+
+@pytest.mark.parametrize("n,alpha", [(4, 0.5), (5, 0.25), (6, 0.75)])
+def test_state_dense_kronecker_sum(n, alpha):
+    """n <= 6: A^-alpha u by eigh of the dense n^3 x n^3 Kronecker sum, mu^-alpha."""
+    pr = make_problem(n, alpha, 1e-2, 2, 133)
+    mats = [op.dense(*op.assemble(pr.coeffs[l])) for l in range(3)]
+    mu, Q = np.linalg.eigh(op.kron_sum_dense(mats))
+    U = F.cp_full(pr.yw, pr.yU)
+    ref = ((Q * (mu ** -alpha)[None, :]) @ (Q.T @ U.reshape(-1))).reshape(U.shape)
+    lams, Vs = _eig3(pr)
+    Y = fg.state_exact(U, lams, Vs, alpha)
+    assert np.linalg.norm(Y - ref) / np.linalg.norm(ref) < 1e-12
+
+
 # ---------------------------------------------------------------- P4 invariants
 def test_P4_invariants():
     n, alpha, beta = 12, 0.5, 1e-2
