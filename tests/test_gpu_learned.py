@@ -116,7 +116,7 @@ def test_learned_preconditioner_in_pcg(trained):
     u2, st2 = res[2]
     assert st2["pre_used"] == 2 and st2["pre_delta"] <= 0.5
     assert st2["pre_rank"] <= 3 * R < res[0][1]["pre_rank"]
-    assert np.linalg.norm(u2 - ustar) <= 1e-5 * np.linalg.norm(ustar)
+    assert np.linalg.norm(u2 - ustar) <= 1e-6 * np.linalg.norm(ustar)
     # a bound the learned sum cannot meet sends the context back to the K-node sum
     o = T.tctl_default_opts(pre_src=2, pre_r=R, pre_model=model.ctypes.data, pre_delta_max=1e-9)
     with T.Context(pr.coeffs, n, alpha, beta, 1e-6, opts=o) as ctx:

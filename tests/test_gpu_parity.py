@@ -8,7 +8,9 @@ Tolerances (derived from the arithmetic):
   * eigenvectors: angle <= eps ||A|| / gap (min relative gap ~6e-4 at n=2048) -> 5e-9;
   * full-grid solve (no truncation, FP64): 1e-10 relative L2;
   * single applies / truncation: eps_trunc (1e-6) + separable F2 error (1e-8);
-  * PCG: 1e-5 relative L2 (10 eps_trunc), and 1e-6 as the solve-quality target.
+  * PCG: 1e-6 relative L2 for the default form (fitted sums, digit-split tensor-core
+    contractions) and the precision / learned forms; 1e-5 (10 eps_trunc) for the
+    other FP64 forms.
 """
 import math
 
@@ -46,7 +48,7 @@ def _full_from_gpu(x: "T.CP"):
 
 
 # ------------------------------------------------------------------ eigenbasis
-@pytest.mark.parametrize("n", [8, 33, 257, 1024])
+@pytest.mark.parametrize("n", [8, 33, 257, 1024, 2048])
 def test_eigs_match_lapack(n):
     pr = make_problem(n, 0.5, 1e-2, 1, 200 + n)
     lams, Vs = _oracle_eigs(pr)
@@ -251,11 +253,39 @@ def test_pcg_small_config():
     assert launches > 0
 
 
+# the default form (fitted sums, digit-split tensor-core contractions) is held
+# to the 1e-6 of the precision and learned forms; the metric counts a solve
+# only at <= 1e-6
 @pytest.mark.parametrize("n,alpha,beta", [(33, 0.25, 1e-4), (40, 0.75, 1.0), (24, 1.0, 1e-2),
                                           (48, 0.1, 1.0)])
 def test_pcg_matches_exact(n, alpha, beta):
     err, st, _ = _pcg_case(n, alpha, beta, 5, 700 + n)
-    assert err <= 1e-5, (err, st)
+    assert err <= 1e-6, (err, st)
+
+
+@pytest.mark.parametrize("alpha,beta", [(0.5, 1e-2), (0.25, 1e-4)])
+def test_pcg_full_size_n256(alpha, beta):
+    """n = 256 (16.7M grid points), design rank 5: element-wise against the exact solve.
+
+    At this size the solve takes the paths small grids never reach: split-K
+    contractions over K = 256 in 256-deep chunks, sketch widths saturating at
+    64 columns, Jacobi eigenproblems of order ~60.
+    """
+    n = 256
+    pr = make_problem(n, alpha, beta, 5, 1000 + int(100 * alpha))
+    lams, Vs = _oracle_eigs(pr)
+    Y = np.einsum("j,ij,kj,lj->ikl", pr.yw, pr.yU[0], pr.yU[1], pr.yU[2], optimize=True)
+    ustar = fg.solve_exact(Y, lams, Vs, alpha, beta)
+    del Y
+    with T.Context(pr.coeffs, n, alpha, beta, 1e-6) as ctx:
+        x, st, code = ctx.pcg_solve(T.CP.from_numpy(pr.yw, pr.yU))
+    assert code == 0 and st["rel_res"] <= 1e-7
+    w, U = x.to_numpy()
+    u = np.einsum("j,ij,kj,lj->ikl", w, U[0], U[1], U[2], optimize=True)
+    err = np.linalg.norm(u - ustar) / np.linalg.norm(ustar)
+    assert err <= 1e-6, (err, st)
+    # no single grid point is off by more than the solution's own scale allows
+    assert np.max(np.abs(u - ustar)) <= 1e-5 * np.max(np.abs(ustar))
 
 
 def _solve_iters(pr, n, alpha, beta, **kw):
@@ -315,7 +345,7 @@ def test_pcg_fp64_and_tensor_core_contractions_agree():
             out.append(_full_from_gpu(x))
     nrm = np.linalg.norm(ustar)
     for u in out:
-        assert np.linalg.norm(u - ustar) <= 1e-5 * nrm
+        assert np.linalg.norm(u - ustar) <= 1e-6 * nrm
     assert np.linalg.norm(out[0] - out[1]) <= 2e-6 * nrm
 
 
