@@ -173,7 +173,12 @@ int tctl_apply_state(tctl_ctx *ctx, const tctl_cp *u, tctl_cp *y);
 int tctl_map_constants(double beta_p, double gamma, double *beta, double *u_scale);
 
 /* y = trunc(x, eps) (Appendix 1: canonical-to-Tucker by reduced HOSVD, core
- * truncation, Tucker-to-canonical). ||x - y|| <= eps ||x||. y may equal x. */
+ * truncation, Tucker-to-canonical). ||x - y|| <= eps ||x||. y may equal x.
+ * eps must lie in [TCTL_TRUNC_EPS_MIN, 1): the range of each mode is found
+ * from FP64 Gram matrices, which resolve directions down to about 1e-8 of the
+ * largest weighted column, so a smaller eps could not be guaranteed and is
+ * rejected with TCTL_E_ARG. */
+#define TCTL_TRUNC_EPS_MIN 1e-7
 int tctl_truncate(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, double eps);
 
 /* Solves (1) for b = y_Omega by Algorithm 1 (Appendix 2). x: output
@@ -329,10 +334,9 @@ long long tctl_launch_count(const tctl_ctx *ctx);
  * device memory: code running where cudaMalloc is not allowed or not wanted,
  * e.g. inside another library's memory pool, a stream-ordered pipeline whose
  * owner controls every allocation, or an embedded runtime with a fixed memory
- * budget. The paper has no counterpart of this entry point; it computes the
- * same eigenpairs as tctl_setup (the three A_(l) of Section 3.2 and their
- * eigendecompositions), so its outputs match tctl_get_eigs for the same
- * coefficients, without creating a context.
+ * budget. The paper has no counterpart of this entry point. It returns the
+ * same eigenpairs as tctl_setup / tctl_get_eigs for the same coefficients,
+ * without creating a context.
  *   coeffs: DEVICE, 3 x (n+1) doubles (row l = a_l(x_{i-1/2}), i = 1..n+1).
  *   lam:    DEVICE, 3 x n doubles, ascending per mode (output).
  *   V:      DEVICE, 3 x n x n doubles; mode l at V + l*n*n, column-major,
@@ -345,8 +349,11 @@ long long tctl_launch_count(const tctl_ctx *ctx);
  * TCTL_EIG_NOALLOC_MAX_N (about 3.2 MB, held by every device that loads the
  * library until the process exits); no cudaMalloc, cudaFree or allocating
  * library routine is called. The first call on a device looks up the array's
- * device address (one-time set-up); make that first call before any stream
- * capture. All calls on a device share the array: calls whose GPU work
+ * device address (one-time set-up). Every call synchronizes its stream (the
+ * coefficient check reads a status word back to the host), so no call may be
+ * made while the stream is being captured into a CUDA graph: the capture would
+ * be invalidated and the call returns TCTL_E_CUDA. All calls on a device share
+ * the array: calls whose GPU work
  * overlaps (different streams, or host threads without ordering) race and
  * corrupt each other's results; serialize them.
  * Errors: TCTL_E_ARG (NULL pointer, n < 2 or n > TCTL_EIG_NOALLOC_MAX_N),
@@ -355,6 +362,16 @@ long long tctl_launch_count(const tctl_ctx *ctx);
 #define TCTL_EIG_NOALLOC_MAX_N 256
 int tctl_eig1d_noalloc(const double *coeffs, int n, int paper_end_rows, double *lam,
                        double *V, void *cuda_stream);
+
+/* Failure-detection test hook (no counterpart in the paper): the next `count`
+ * tensor-core GEMM launches of this context withhold their operand copies, so
+ * the kernel's bounded wait for the first stage (a barrier nothing arrives on)
+ * runs out after about 1 ms instead of the normal 1 s limit. Such a launch
+ * leaves its output unwritten, frees its tensor memory and returns; the call
+ * that issued it returns TCTL_E_NUMERIC ("bounded mbarrier wait timed out"),
+ * and the context stays usable for the next call. Nothing faults, traps or
+ * hangs. count = 0 cancels. Errors: TCTL_E_ARG (NULL context, count < 0). */
+int tctl_inject_wait_timeout(tctl_ctx *ctx, int count);
 
 /* Per-kernel timing (tracing): when enabled, the context records a pair of
  * CUDA events on its stream around every kernel it launches. The report is a

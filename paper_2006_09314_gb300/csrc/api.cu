@@ -40,6 +40,15 @@ void check_cp(const Ctx &c, const tctl_cp *t, const char *name, bool need_terms)
     fail(TCTL_E_ARG, std::string(name) + ": NULL factor pointer");
 }
 
+// Restores the workspace's bump pointer when an entry point leaves, also by an
+// error, so that a failed call does not shrink the workspace of the next one.
+struct WsGuard {
+  Arena &a;
+  size_t m;
+  explicit WsGuard(Arena &ar) : a(ar), m(ar.mark()) {}
+  ~WsGuard() { a.reset(m); }
+};
+
 struct Timer {
   cudaEvent_t a, b;
   cudaStream_t st;
@@ -324,6 +333,7 @@ static int apply_common(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, int which) 
     check_cp(*c, x, "x", true);
     check_cp(*c, y, "y", false);
     if (which == 2) ensure_state_sep(*c);
+    WsGuard g(c->ws);
     size_t mk = c->ws.mark();
     Tucker tx, ty;
     tucker_alloc(*c, tx, kCap);
@@ -367,7 +377,10 @@ int tctl_truncate(tctl_ctx *ctx, const tctl_cp *x, tctl_cp *y, double eps) {
   try {
     check_cp(*c, x, "x", true);
     check_cp(*c, y, "y", false);
-    if (!(eps > 0.0 && eps < 1.0)) fail(TCTL_E_ARG, "eps must be in (0, 1)");
+    if (!(eps >= TCTL_TRUNC_EPS_MIN && eps < 1.0))
+      fail(TCTL_E_ARG, "eps must be in [1e-7, 1): smaller tolerances are below what the "
+                       "Gram-based range finding resolves");
+    WsGuard g(c->ws);
     size_t mk = c->ws.mark();
     Tucker t;
     tucker_alloc(*c, t, kCap);
@@ -386,7 +399,16 @@ int tctl_pcg_solve(tctl_ctx *ctx, const tctl_cp *b, tctl_cp *x, tctl_stats *st) 
   try {
     check_cp(*c, b, "b", true);
     check_cp(*c, x, "x", false);
-    return pcg_solve(*c, b, x, st);
+    WsGuard g(c->ws);
+    try {
+      return pcg_solve(*c, b, x, st);
+    } catch (const Error &e) {
+      // a tensor-core wait that ran out leaves unwritten outputs behind it;
+      // report the timeout rather than whatever it caused downstream
+      if (tcg_timed_out(*c))
+        throw Error{TCTL_E_NUMERIC, "tensor-core GEMM: bounded mbarrier wait timed out"};
+      throw;
+    }
   } catch (const Error &e) {
     return handle(c, e);
   }
@@ -542,6 +564,7 @@ int tctl_gemm(tctl_ctx *ctx, int digits, int trans_a, int trans_b, int m, int n,
     if (lda < std::max(1, trans_a ? k : m) || ldb < std::max(1, trans_b ? n : k) || ldc < std::max(1, m))
       fail(TCTL_E_ARG, "leading dimension too small");
     if (m == 0 || n == 0) return TCTL_OK;
+    WsGuard g(c->ws);
     if (digits == 0 || k == 0)
       gemm(*c, trans_a != 0, trans_b != 0, m, n, k, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0);
     else {
@@ -569,6 +592,7 @@ int tctl_gemm_kr(tctl_ctx *ctx, int digits, int k, int ra, int rb, int n, double
         ldc < std::max<long long>(1, m))
       fail(TCTL_E_ARG, "leading dimension too small");
     if (m == 0 || n == 0) return TCTL_OK;
+    WsGuard g(c->ws);
     if (digits == 0 || k == 0) {
       size_t mk = c->ws.mark();
       double *KR = c->ws.dbl((size_t)std::max(k, 1) * m);
@@ -583,6 +607,13 @@ int tctl_gemm_kr(tctl_ctx *ctx, int digits, int k, int ra, int rb, int n, double
   } catch (const Error &e) {
     return handle(c, e);
   }
+}
+
+int tctl_inject_wait_timeout(tctl_ctx *ctx, int count) {
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (!c || count < 0) return TCTL_E_ARG;
+  c->withhold_copies = count;
+  return TCTL_OK;
 }
 
 int tctl_expsum_fit(double alpha, double beta, double s_min, double s_max, double tol, double *t,
@@ -719,7 +750,7 @@ int tctl_profile_report(tctl_ctx *ctx, char *buf, int buflen) {
     struct Agg {
       std::string name;
       long long launches = 0;
-      double ms = 0, flops = 0;
+      double ms = 0, flops = 0, mma = 0, bytes = 0;
     };
     std::vector<Agg> agg;
     for (const ProfRec &r : c->prof_recs) {
@@ -739,12 +770,17 @@ int tctl_profile_report(tctl_ctx *ctx, char *buf, int buflen) {
       it->launches++;
       it->ms += ms;
       it->flops += r.flops;
+      it->mma += r.mma_flops;
+      it->bytes += r.bytes;
     }
     std::string js = "{";
     for (size_t i = 0; i < agg.size(); ++i) {
-      char tmp[512];
-      std::snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e}",
-                    i ? ", " : "", agg[i].name.c_str(), agg[i].launches, agg[i].ms, agg[i].flops);
+      char tmp[640];
+      std::snprintf(tmp, sizeof(tmp),
+                    "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e, \"mma_flops\": %.6e, "
+                    "\"bytes\": %.6e}",
+                    i ? ", " : "", agg[i].name.c_str(), agg[i].launches, agg[i].ms, agg[i].flops,
+                    agg[i].mma, agg[i].bytes);
       js += tmp;
     }
     js += "}";

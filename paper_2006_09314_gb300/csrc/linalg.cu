@@ -288,6 +288,7 @@ static void gemm_skinny(Ctx &c, bool ta, bool tb, int m, int n, int k, double al
   else if (NC == 8) skinny_launch<8>(c, ta, tb, m, n, k, A, lda, B, ldb, part, splits, kchunk, rowblocks);
   else skinny_launch<16>(c, ta, tb, m, n, k, A, lda, B, ldb, part, splits, kchunk, rowblocks);
   const long long total = (long long)m * n;
+  c.next_bytes = 8.0 * total * (splits + 1 + (beta != 0.0));
   LAUNCH(c, splitk_reduce, (unsigned)((total + 31) / 32), dim3(32, 8), 0, m, n, splits, 1, alpha, part,
          beta, C, ldc, 0ll);
   c.ws.reset(mk);
@@ -383,6 +384,8 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
     c.next_tag = c.intern(nm);
   }
   c.next_flops = 2.0 * m * n * (double)k * batch;
+  c.next_bytes = 8.0 * ((double)m * k * ((batch - 1) / divA + 1) + (double)k * n * ((batch - 1) / divB + 1) +
+                        (double)m * n * batch * (1 + (beta != 0.0)));
   if (small)
     gemm_launch<32, 32>(c, ta, tb, grid, m, n, k, alpha, A, lda, sA, divA, B, ldb, sB, divB, beta,
                         C, ldc, sC, splits, kchunk, part);
@@ -391,6 +394,7 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
                         C, ldc, sC, splits, kchunk, part);
   if (splits > 1) {
     const long long total = (long long)m * n * batch;
+    c.next_bytes = 8.0 * total * (splits + 1 + (beta != 0.0));
     LAUNCH(c, splitk_reduce, (unsigned)((total + 31) / 32), dim3(32, 8), 0, m, n, splits, batch, alpha,
            part, beta, C, ldc, sC);
   }
@@ -416,6 +420,7 @@ void khatri_rao(Ctx &c, int n, const double *A, int lda, int ra, const double *B
   const long long total = (long long)n * ra * rb;
   if (total == 0) return;
   const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+  c.next_bytes = 8.0 * ((double)total + (double)n * (ra + rb));
   LAUNCH(c, khatri_rao_kernel, blocks, 256, 0, n, A, lda, ra, B, ldb, rb, out, ldo);
 }
 

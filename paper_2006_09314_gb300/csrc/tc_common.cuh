@@ -1,5 +1,5 @@
 // Shared device helpers of the tcgen05 kernels: shared-memory matrix
-// descriptors for the SWIZZLE_NONE K-major core-matrix layout, bounded
+// descriptors for the SWIZZLE_NONE K-major core-matrix layout, time-bounded
 // mbarrier waits, powers of two.
 //
 // Operand tiles are stored as 8-row x 16-byte core matrices: element (r, k)
@@ -38,18 +38,33 @@ __device__ __forceinline__ uint32_t core_off(int r, int k) {
   return (uint32_t)((r >> 3) * SBO + (k >> 3) * LBO + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// Bounded wait on an mbarrier phase; false after ~4M polls (the caller
-// records an error and unwinds instead of hanging).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it) {
+// Bounded wait on an mbarrier phase: false once limit_ns nanoseconds (global
+// timer) have passed without the phase completing, or after 2^24 polls
+// whatever the timer says; the caller records an error and unwinds instead of
+// hanging. kWaitNs = 1 s, far above any wait of a working pipeline
+// (microseconds).
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs) {
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(bar), "r"(parity));
+    if (done) return true;
+    if (global_ns() - t0 > limit_ns) return false;
   }
-  return done != 0;
+  return false;
 }
 
 __device__ __forceinline__ float pow2f(int e) {

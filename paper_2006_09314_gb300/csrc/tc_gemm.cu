@@ -180,6 +180,10 @@ struct TcgArgs {
   int cd;
   double *part;  // nchunk > 1: FP64 partial sums, [(b * nchunk + ch) * N + j] * M + m
   int *err;
+  // failure-detection test: the producer withholds every copy, so the MMA
+  // thread's wait for the first stage runs out after wait_ns
+  int withhold;
+  unsigned long long wait_ns;
 };
 
 template <int D, int NST>
@@ -219,14 +223,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
+  int issued = 0;  // stages whose bulk copies the producer started
   if (warp == 0 && lane == 0) {
     // producer: one bulk copy of the A digit block and one of the B block per stage
     const __nv_bfloat16 *asrc = a.pa + (((long long)ia * a.Mt + mt) * a.nks + ks0) * D * PA;
     const __nv_bfloat16 *bsrc = a.pb + (((long long)ib * a.Nt + jt) * a.nks + ks0) * D * PB;
-    for (int s = 0; s < nst; ++s) {
+    for (int s = 0; s < (a.withhold ? 0 : nst); ++s) {
       const int st = s % NST;
       if (s >= NST) {
-        if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)(((s - NST) / NST) & 1))) {
+        if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)(((s - NST) / NST) & 1), a.wait_ns)) {
           atomicExch(abort_flag, 1);
           break;
         }
@@ -244,6 +249,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
               "r"(dst + A_BYTES),
           "l"(bsrc + (long long)s * D * PB), "r"(B_BYTES), "r"(bar)
           : "memory");
+      issued = s + 1;
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: kind::f16, BF16 x BF16 -> FP32, M = 128, N = 64
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
                            ((uint32_t)(TM >> 4) << 24);
     for (int s = 0; s < nst; ++s) {
       const int st = s % NST;
-      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((s / NST) & 1))) {
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((s / NST) & 1), a.wait_ns)) {
         atomicExch(abort_flag, 1);
         break;
       }
@@ -285,6 +291,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
   const bool fin = mbar_wait(smem_u32(done_bar), 0u);
   const bool ok = (__syncthreads_and(fin ? 1 : 0) != 0) && (*abort_flag == 0) && nst > 0;
   if (!ok && nst > 0 && tid == 0) atomicExch(a.err, 1);
+  if (!ok && warp == 0 && lane == 0) {
+    // after an abort, bulk copies into stages the MMA thread never consumed may
+    // still be landing: wait (bounded) for the last NST issued stages before the
+    // CTA releases its shared memory (earlier stages completed before their
+    // buffers were reissued)
+    for (int s = max(0, issued - NST); s < issued; ++s)
+      mbar_wait(smem_u32(&full[s % NST]), (uint32_t)((s / NST) & 1));
+  }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     // warp w: TMEM lanes 32 (w % 4) .. +31 (rows), columns 32 (w / 4) .. +31, 16 at a time
@@ -367,9 +381,15 @@ template <int D, int TR>
 void split_operand(Ctx &c, const TcOpnd &o, int R, int K, int items, int Rpad, int nks, int *e,
                    __nv_bfloat16 *planes) {
   TCTL_CUDA(cudaMemsetAsync(e, 0, sizeof(int) * (size_t)items * Rpad, c.st));
+  // algorithmic bytes: the operand's distinct elements once (a Khatri-Rao
+  // operand: its two factors), the exponents, and the digit planes written
+  const double in_bytes = o.q ? 8.0 * K * ((double)o.d + (double)R / o.d)
+                              : 8.0 * (double)R * K * items;
   dim3 ge((R + 31) / 32, (K + RE_K - 1) / RE_K, items);
+  c.next_bytes = in_bytes + 4.0 * items * Rpad;
   LAUNCH(c, row_exp_kernel, ge, 256, 0, o, R, K, Rpad, e);
   dim3 g(Rpad / TR, nks, items);
+  c.next_bytes = in_bytes + 4.0 * items * Rpad + 2.0 * D * (double)items * Rpad * nks * BK;
   LAUNCH(c, (split_kernel<D, TR>), g, 2 * TR, 0, o, R, K, Rpad, nks, e, planes);
 }
 
@@ -447,13 +467,24 @@ void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double 
   ar.cd = cd;
   ar.part = part;
   ar.err = c.tcg_err;
+  ar.withhold = 0;
+  ar.wait_ns = kWaitNs;
+  if (c.withhold_copies > 0) {
+    // host-injected failure (tctl_inject_wait_timeout): a 1 ms limit on a
+    // barrier nothing arrives on
+    ar.withhold = 1;
+    ar.wait_ns = 1000000ull;
+    --c.withhold_copies;
+  }
   dim3 grid(Mt, Nt, batch * nchunk);
   c.next_flops = 2.0 * M * (double)N * K * batch;
+  c.next_mma = (D * (D + 1) / 2) * c.next_flops;  // digit products with p + q <= D - 1
   constexpr int smem_bytes = tcg_smem<D, NST>();
   LAUNCH(c, (tcg_kernel<D, NST>), grid, NTHREADS, smem_bytes, ar);
   if (nchunk > 1) {
     const long long total = (long long)M * N * batch;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    c.next_bytes = 8.0 * total * (nchunk + 1 + (beta != 0.0));
     LAUNCH(c, tcg_reduce_kernel, blocks, 256, 0, M, N, batch, nchunk, part, alpha, beta, C, cm0, cm1,
            cd, cj, cb);
   }
@@ -534,14 +565,16 @@ void gemm_tc_kr(Ctx &c, int digits, int k, int ra, int rb, int n, double alpha, 
   gemm_tc(c, digits, m, n, k, 1, 1, 1, alpha, kr, opB, beta, C, 1, 0, 1 << 30, ldc, 0);
 }
 
-void tcg_check(Ctx &c) {
-  if (!c.tcg_err) return;
+bool tcg_timed_out(Ctx &c) {
+  if (!c.tcg_err) return false;
   int herr = 0;
   read_host(c, &herr, c.tcg_err, sizeof(int));
-  if (herr) {
-    TCTL_CUDA(cudaMemsetAsync(c.tcg_err, 0, sizeof(int), c.st));
-    fail(TCTL_E_NUMERIC, "tensor-core GEMM: bounded mbarrier wait timed out");
-  }
+  if (herr) TCTL_CUDA(cudaMemsetAsync(c.tcg_err, 0, sizeof(int), c.st));
+  return herr != 0;
+}
+
+void tcg_check(Ctx &c) {
+  if (tcg_timed_out(c)) fail(TCTL_E_NUMERIC, "tensor-core GEMM: bounded mbarrier wait timed out");
 }
 
 }  // namespace tctl

@@ -83,16 +83,25 @@ __device__ __forceinline__ uint32_t core_off(int r, int k) {
   return (uint32_t)((r >> 3) * SBO + (k >> 3) * LBO + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// Bounded wait on an mbarrier phase: false after 1 s (global timer) or 2^24
+// polls without the phase completing; the caller records an error instead of
+// hanging.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it) {
+  constexpr unsigned long long kLimitNs = 1000000000ull;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(bar), "r"(parity));
+    if (done) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > kLimitNs) return false;
   }
-  return done != 0;
+  return false;
 }
 
 // Five 7-bit digits (35-bit fixed point, truncated) of |x| / 2^f for |x| < 2^f,
@@ -305,6 +314,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
+  int issued = 0;  // stages whose bulk copies the producer started
   if (warp == 0 && lane == 0) {
     // producer: bulk copies of the W and X digit blocks of each stage
     const __nv_bfloat16 *wsrc = a.wplanes + (long long)mt * nks * NPLANE * PLANE_ELEMS;
@@ -332,6 +342,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
               "r"(dst + W_BYTES),
           "l"(xsrc + (long long)s * XPLANE * XPLANE_ELEMS), "r"(X_BYTES), "r"(bar)
           : "memory");
+      issued = s + 1;
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -380,6 +391,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_modeprod_kernel(TcArgs a) {
   const bool fin = mbar_wait(smem_u32(done_bar), 0u);
   const bool ok = (__syncthreads_and(fin ? 1 : 0) != 0) && (*abort_flag == 0);
   if (!ok && tid == 0) atomicExch(a.err, 1);
+  if (!ok && warp == 0 && lane == 0) {
+    // after an abort, wait (bounded) for the bulk copies of the last NSTAGE
+    // issued stages before the CTA releases its shared memory
+    for (int s = max(0, issued - NSTAGE); s < issued; ++s)
+      mbar_wait(smem_u32(&full[s % NSTAGE]), (uint32_t)((s / NSTAGE) & 1));
+  }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows m), columns (TN / 2) (w / 4) .. +
@@ -483,6 +500,7 @@ void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
   float *A = c.tc_x[0], *B = c.tc_x[1];
   {
     const int blocks = (int)std::min<long long>((n3 + 255) / 256, 152 * 64);
+    c.next_bytes = 12.0 * n3;
     LAUNCH(c, f64_to_f32_kernel, blocks, 256, 0, n3, y, A);
   }
   // strides of the three mode products (k = contracted index; j0, j1 the others)
@@ -493,9 +511,11 @@ void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
     const int idx = 2 * l + dir;
     const int cblocks = (sk[l] == 1) ? (int)std::min<long long>(n2 * 32 / 256, 152 * 64)
                                      : (int)std::min<long long>((n2 + 255) / 256, 152 * 64);
+    c.next_bytes = 4.0 * n3 + 4.0 * n2;
     LAUNCH(c, col_exp_kernel, cblocks, 256, 0, n, X, sk[l], sj0[l], sj1[l], c.tc_f);
     {
       dim3 g(n / (BK * XD_KS), (unsigned)(n2 / TN));
+      c.next_bytes = 4.0 * n3 + 4.0 * n2 + 2.0 * XPLANE * n3;  // FP32 in, 5 BF16 digit planes out
       LAUNCH(c, x_digits_kernel, g, 512, 0, n, X, sk[l], sj0[l], sj1[l], c.tc_f, c.tc_xd);
     }
     TcArgs ar;
@@ -519,6 +539,7 @@ void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
     ar.err = c.tc_err;
     dim3 grid(n / TM, (unsigned)(n2 / TN));
     c.next_flops = 2.0 * (double)n * (double)n2 * (double)n;  // one logical FP64-class GEMM
+    c.next_mma = 15.0 * c.next_flops;                         // digit pairs with p + q <= 4
     LAUNCH(c, tc_modeprod_kernel, grid, NTHREADS, SMEM_BYTES, ar);
   };
   pass(0, 0, A, B, 0);
@@ -529,6 +550,7 @@ void fullgrid_apply_tc(Ctx &c, const double *y, double *u, int which) {
   pass(2, 1, B, A, 0);
   {
     const int blocks = (int)std::min<long long>((n3 + 255) / 256, 152 * 64);
+    c.next_bytes = 12.0 * n3;
     LAUNCH(c, f32_to_f64_kernel, blocks, 256, 0, n3, A, u);
   }
   int herr = 0;

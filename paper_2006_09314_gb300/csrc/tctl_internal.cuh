@@ -77,7 +77,9 @@ struct ProfRec {
   const char *outer;
   const char *phase;
   cudaEvent_t a, b;
-  double flops;
+  double flops;      // algorithmic FP64-class flops (GEMMs)
+  double mma_flops;  // BF16 tensor-core flops of the digit products (2 MNK per product)
+  double bytes;      // algorithmic global-memory bytes (operands read once, results written once)
 };
 
 struct Ctx {
@@ -124,6 +126,7 @@ struct Ctx {
   uint64_t rng_counter = 0;
   std::vector<void *> owned;         // device allocations freed at destroy
   int *tcg_err = nullptr;            // tensor-core GEMM wait-timeout flag (device)
+  int withhold_copies = 0;           // failure-detection test: GEMM launches left to starve
   // digit planes of constant tensor-core operands (the operator's factor
   // matrices), keyed by the operand's address, strides and split geometry
   struct TcKept {
@@ -150,6 +153,8 @@ struct Ctx {
   std::vector<cudaEvent_t> prof_pool;
   size_t prof_used = 0;
   double next_flops = 0;             // algorithmic flops of the next launch (GEMMs)
+  double next_mma = 0;               // BF16 tensor-core flops of the next launch
+  double next_bytes = 0;             // algorithmic bytes of the next launch (memory-bound kernels)
   const char *next_tag = nullptr;    // profile name of the next launch (GEMM call site)
   const char *phase = nullptr;       // current algorithm phase (profile grouping)
   const char *outer = nullptr;       // current PCG step (profile grouping)
@@ -174,9 +179,12 @@ struct Ctx {
     if ((ctx).prof) {                                                             \
       ::tctl::check_cuda(cudaEventRecord(tctl_ev_b, (ctx).st), "cudaEventRecord"); \
       (ctx).prof_recs.push_back({(ctx).next_tag ? (ctx).next_tag : #kernel, (ctx).outer, (ctx).phase, \
-                                 tctl_ev_a, tctl_ev_b, (ctx).next_flops});        \
+                                 tctl_ev_a, tctl_ev_b, (ctx).next_flops, (ctx).next_mma,         \
+                                 (ctx).next_bytes});                              \
     }                                                                             \
     (ctx).next_flops = 0;                                                         \
+    (ctx).next_mma = 0;                                                           \
+    (ctx).next_bytes = 0;                                                         \
     (ctx).next_tag = nullptr;                                                     \
   } while (0)
 
@@ -244,6 +252,8 @@ void gemm_tc_cm(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, doubl
                 const double *A, int lda, const double *B, int ldb, double beta, double *C, int ldc);
 // Raises TCTL_E_NUMERIC if a tensor-core GEMM timed out on a wait (synchronizes).
 void tcg_check(Ctx &c);
+// Reads and clears the wait-timeout flag without raising (synchronizes).
+bool tcg_timed_out(Ctx &c);
 
 // ------------------------------------------------------------ linalg.cu
 // C = alpha op(A) op(B) + beta C, column-major, batched with element strides;

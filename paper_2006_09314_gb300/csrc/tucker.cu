@@ -560,6 +560,7 @@ static void sketch_mode(Ctx &c, const Sep &D, const Tucker &x, const double *Cl,
            uT + (size_t)r[l] * s0, r[l] * ls, 0, 0.0, W, n, 0, 1, 1, 1, true);
     const long long tot = (long long)n * ns;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+    c.next_bytes = 8.0 * n * ((double)r[l] * ns + r[l] + ns);
     LAUNCH(c, rowdot_kernel, blocks, 256, 0, n, r[l], ns, x.Q[l], n, W, n, Y + (size_t)n * s0, n);
   }
   c.ws.reset(mk);

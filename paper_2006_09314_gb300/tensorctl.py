@@ -37,7 +37,7 @@ EXPORTED = [
     "tctl_profile_enable", "tctl_profile_report", "tctl_eig1d_noalloc", "tctl_get_expsum",
     "tctl_expsum_fit", "tctl_gemm", "tctl_gemm_kr", "tctl_precond_fit", "tctl_precond_dataset",
     "tctl_mlp_model_size", "tctl_mlp_train", "tctl_mlp_grad", "tctl_mlp_forward",
-    "tctl_apply_state", "tctl_map_constants", "tctl_solve_batch",
+    "tctl_apply_state", "tctl_map_constants", "tctl_solve_batch", "tctl_inject_wait_timeout",
 ]
 
 ERRORS = {0: "OK", -1: "E_ARG", -2: "E_COEFF", -3: "E_CUDA", -4: "E_NOMEM",
@@ -146,6 +146,7 @@ def load(build_if_missing: bool = True):
         "tctl_apply_state": (I, [P, PCP, PCP]),
         "tctl_map_constants": (I, [D, D, P, P]),
         "tctl_solve_batch": (I, [P, I, D, P, I]),
+        "tctl_inject_wait_timeout": (I, [P, I]),
         "tctl_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -528,6 +529,11 @@ def tctl_eig1d_noalloc(coeffs_dev, n, lam_dev, V_dev, paper_end_rows=0, stream=N
                                      lam_dev.data_ptr(), V_dev.data_ptr(), ctypes.c_void_p(stream)))
 
 
+def tctl_inject_wait_timeout(ctx, count=1):
+    """The next `count` tensor-core GEMM launches of ctx starve a bounded wait (test hook)."""
+    _check(load().tctl_inject_wait_timeout(ctx, int(count)), ctx)
+
+
 def tctl_destroy(ctx):
     load().tctl_destroy(ctx)
 
@@ -604,3 +610,6 @@ class Context:
 
     def profile_report(self):
         return tctl_profile_report(self.handle)
+
+    def inject_wait_timeout(self, count=1):
+        tctl_inject_wait_timeout(self.handle, count)

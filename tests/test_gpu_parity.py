@@ -401,6 +401,10 @@ def test_edge_cases_and_errors():
         with pytest.raises(T.TctlError) as ei:
             ctx.apply_op(b, cap=1)
         assert ei.value.code == -5
+        # truncation tolerances below what the range finding resolves are rejected
+        with pytest.raises(T.TctlError) as ei:
+            ctx.truncate(b, 5e-8)
+        assert ei.value.code == -1
     o = T.tctl_default_opts(max_iter=1, pcg_rtol=1e-14, r_pre=2)
     with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6, opts=o) as ctx:
         x, st, code = ctx.pcg_solve(T.CP.from_numpy(pr.yw, pr.yU), check=False)
