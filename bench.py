@@ -63,6 +63,9 @@ def parse():
                     help="grid of the full-grid mode-product measurement (0: skip)")
     ap.add_argument("--fullgrid-only", action="store_true",
                     help="run only the full-grid mode-product measurement")
+    ap.add_argument("--single", action="store_true",
+                    help="one context and one solve per step (alpha = 0.5, beta = 1e-2), for "
+                         "profiler captures: one problem's memory, no checks")
     return ap.parse_args()
 
 
@@ -393,8 +396,9 @@ def ours_arm(args, rank, world):
     e2e_value = world * B / statistics.mean(e2e_times)
 
     # the same kernels traced on one solve alone (alpha = 0.5, beta = 1e-2): per-launch
-    # durations without the other streams' kernels interleaved
-    iso = None
+    # durations without the other streams' kernels interleaved; the roofline comes
+    # from this trace
+    iso, roofline = None, None
     if rank == 0:
         k_iso = min(range(B), key=lambda i: abs(probs[i].alpha - 0.5) + abs(math.log10(probs[i].beta) + 2))
         ctxs[k_iso].profile(True)
@@ -402,34 +406,12 @@ def ours_arm(args, rank, world):
             ctxs[k_iso].pcg_solve(bs[k_iso])
         rep = ctxs[k_iso].profile_report()
         ctxs[k_iso].profile(False)
-        tot_iso = sum(v["ms"] for v in rep.values())
-        iso = {"solve_ms": tot_iso, "kernels": {}}
-        for kname, v in sorted(rep.items(), key=lambda kv: -kv[1]["ms"])[:6]:
-            e = {"launches": v["launches"], "ms": round(v["ms"], 3), "share": round(v["ms"] / tot_iso, 3)}
-            if v["flops"] > 0:
-                tf = v["flops"] / (v["ms"] / 1000.0) / 1e12
-                e["fp64_class_tflops"] = round(tf, 3)
-                e["frac_of_fp64_peak"] = round(tf / FP64_PEAK_TFLOPS, 3)
-            iso["kernels"][kname] = e
-    # the roofline kernel: the largest share among kernels with an algorithmic
-    # flop count (the Jacobi eigensolver's sweeps are data-dependent; it is
-    # named in the note when it leads)
-    top_name, top = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    dname, d = max(((k, v) for k, v in prof.items() if v["flops"] > 0),
-                   key=lambda kv: kv[1]["ms"], default=(top_name, top))
-    tot_prof_ms = sum(v["ms"] for v in prof.values())
-    achieved = (d["flops"] / (d["ms"] / 1000.0) / 1e12) if d["flops"] > 0 else None
-    gemm_flops = sum(v["flops"] for v in prof.values())
-    roofline = {"bound": "alu", "kernel": dname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                "traffic": None, "share": d["ms"] / tot_prof_ms,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
-                               "(FP64 FMA probe measured 1.256 TFLOP/s)",
-                "note": "per-launch durations measured while the batch's solves run "
-                        "concurrently; aggregate GEMM rate over the step: "
-                        f"{gemm_flops / (total_ms_max / args.steps / 1000.0) / 1e12:.3f} TFLOP/s"
-                        + ("" if top_name == dname else
-                           f"; largest share: {top_name} ({top['ms'] / tot_prof_ms:.3f}, no flop model)")}
+        iso, roofline = roofline_from_trace(rep)
+        iso["problem"] = {"alpha": probs[k_iso].alpha, "beta": probs[k_iso].beta, "n": n}
+        roofline["note"] = (f"kernel with the largest share ({roofline['share']:.3f}) of one solve "
+                            f"traced alone (alpha={probs[k_iso].alpha}, beta={probs[k_iso].beta}), "
+                            "CUDA events around every launch on the solve's stream; "
+                            "achieved = algorithmic work per launch / mean launch time")
 
     cpu = None
     if not args.no_cpu:
@@ -452,6 +434,12 @@ def ours_arm(args, rank, world):
                                 f"eps={EPS}, fitted exp-sum F2 to 1e-8, tensor-core contractions; "
                                 f"one step = {B} concurrent solves"),
                    "n": n, "batch": B, "rank": RANK, "eps_trunc": EPS,
+                   "contractions": ("sketch and core-projection GEMMs of the truncated Hadamard "
+                                    "products: 6 signed 7-bit BF16 digits per operand (42-bit "
+                                    "fixed point under one exponent per row / column), 21 digit "
+                                    "products on tcgen05 with FP32 accumulators, exact low levels, "
+                                    "FP64 K-chunk sums; Gram, QR, Jacobi, basis changes, PCG "
+                                    "scalars and residual updates in FP64"),
                    "l2": "flushed between timed steps (256 MB write)",
                    "setup_ms_mean": statistics.mean(setup_ms),
                    "iters": [s["iters"] for s in stats],
@@ -473,12 +461,77 @@ def ours_arm(args, rank, world):
         "uneven_batch": batchsec,
         "gpu_launches": launches,
         "clocks": clk,
-        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
-                    sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+        "kernels_concurrent": {
+            "note": (f"one traced step of the {B} concurrent solves: event pairs also cover "
+                     "the other streams' kernels, so these times overlap and add up to more "
+                     "than the step"),
+            **{k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
+               sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]}},
     }
     print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
+
+
+def _pipe_peaks():
+    """Denominators: FP64 pipe (unit counts x max clock), BF16 tensor pipe and HBM (measured)."""
+    return {"alu": (FP64_PEAK_TFLOPS, "TFLOP/s",
+                    "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (no measured FP64 peak; "
+                    "an FP64 FMA probe reached 1.256 TFLOP/s)"),
+            "tensor": (_peak("bf16_tflops", 1900.0), "TFLOP/s",
+                       "measured: MEASURED_PEAKS.json bf16_tflops (cuBLAS burst; kernel timed alone)"
+                       if _peak("bf16_tflops", None) else "fallback 1.9 PFLOP/s bf16 burst"),
+            "hbm": (_peak("hbm_gbs", 6800.0), "GB/s",
+                    "measured: MEASURED_PEAKS.json hbm_gbs (copy)" if _peak("hbm_gbs", None)
+                    else "fallback 6.8 TB/s")}
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+# committed ncu summaries, keyed by kernel; None where no capture of the current
+# kernel exists
+TRAFFIC_PER_LAUNCH = {}
+
+
+def roofline_from_trace(rep):
+    """Per-kernel roofline of a traced solve and the roofline object of its largest kernel.
+
+    Each kernel is held against the pipe its work runs on: the digit-split
+    tensor-core GEMMs against the BF16 tensor peak (counting the BF16 digit
+    products, 2 MNK each), the FP64 GEMMs against the FP64 pipe, and kernels
+    with a byte model (digit splits, reductions, row contractions) against HBM.
+    """
+    peaks = _pipe_peaks()
+    tot = sum(v["ms"] for v in rep.values())
+    kern = {}
+    for name, v in rep.items():
+        e = {"launches": v["launches"], "ms": round(v["ms"], 4), "share": round(v["ms"] / tot, 4)}
+        sec = v["ms"] / 1000.0
+        if v.get("mma_flops", 0) > 0:
+            e["bound"], e["achieved"] = "tensor", v["mma_flops"] / sec / 1e12
+            e["fp64_class_tflops"] = v["flops"] / sec / 1e12
+        elif v.get("flops", 0) > 0:
+            e["bound"], e["achieved"] = "alu", v["flops"] / sec / 1e12
+        elif v.get("bytes", 0) > 0:
+            e["bound"], e["achieved"] = "hbm", v["bytes"] / sec / 1e9
+        if "bound" in e:
+            e["frac"] = round(e["achieved"] / peaks[e["bound"]][0], 4)
+            e["achieved"] = round(e["achieved"], 4)
+        kern[name] = e
+    iso = {"solve_kernel_ms": tot,
+           "kernels": dict(sorted(kern.items(), key=lambda kv: -kv[1]["ms"])[:12])}
+    modeled = [(k, e) for k, e in kern.items() if "bound" in e]
+    name, e = max(modeled, key=lambda kv: kv[1]["ms"])
+    v = rep[name]
+    peak, unit, src = peaks[e["bound"]]
+    per_launch = ((v["mma_flops"] if e["bound"] == "tensor" else v["flops"] if e["bound"] == "alu"
+                   else v["bytes"]) / v["launches"])
+    roofline = {"bound": e["bound"], "kernel": name, "achieved": e["achieved"], "peak": peak,
+                "unit": unit, "frac": e["achieved"] / peak,
+                "traffic": TRAFFIC_PER_LAUNCH.get(name), "share": e["share"],
+                "work_per_launch": per_launch, "launches": v["launches"],
+                "ms_per_launch": v["ms"] / v["launches"], "peak_source": src + " (of measured)"
+                if "measured" in src else src}
+    return iso, roofline
 
 
 def verify_variants(variants, variant_sols, errs, probs, pool):
@@ -675,6 +728,33 @@ def _peak(key, fallback):
         return fallback
 
 
+def single_arm(args):
+    """One n-point problem (alpha = 0.5, beta = 1e-2) solved W + K times on one stream."""
+    import torch
+    from paper_2006_09314_gb300 import tensorctl as T
+    from paper_2006_09314_gb300.inputs import make_problem, problem_seed
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    p = make_problem(args.n, ALPHA, BETA, RANK, problem_seed(CONFIG_ID, 4))
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st), T.Context(p.coeffs, args.n, p.alpha, p.beta, EPS,
+                                          stream=st.cuda_stream) as ctx:
+        b = T.CP.from_numpy(p.yw, p.yU)
+        for _ in range(args.warmup):
+            ctx.pcg_solve(b)
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            x, stats, _ = ctx.pcg_solve(b)
+            e1.record(st)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        print(json.dumps({"single": {"n": args.n, "alpha": p.alpha, "beta": p.beta,
+                                     "ms_per_solve": times, "iters": stats["iters"],
+                                     "rank_x": list(stats["rank_x"]),
+                                     "setup_ms": ctx.stats()["t_setup_ms"]}}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -688,6 +768,10 @@ def main():
         else:
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
             dist.init_process_group("nccl")
+    if args.single:
+        if rank == 0:
+            single_arm(args)
+        return
     if args.fullgrid_only:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))

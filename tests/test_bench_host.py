@@ -79,3 +79,28 @@ def test_reference_arm_prints_the_contract_line():
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_roofline_from_trace_divides_each_kernel_by_its_own_pipe():
+    """Tensor-core GEMMs against the BF16 peak (digit products), FP64 GEMMs against
+    the FP64 pipe, byte-modelled kernels against HBM; the largest modelled kernel
+    gives the roofline object, whose frac is its work / time / peak."""
+    rep = {"tcg_kernel": {"launches": 10, "ms": 5.0, "flops": 1e11, "mma_flops": 2.1e12, "bytes": 0.0},
+           "dgemm_kernel": {"launches": 100, "ms": 4.0, "flops": 4e8, "mma_flops": 0.0, "bytes": 1e8},
+           "split_kernel": {"launches": 20, "ms": 1.0, "flops": 0.0, "mma_flops": 0.0, "bytes": 3e9},
+           "jacobi_kernel": {"launches": 3, "ms": 9.0, "flops": 0.0, "mma_flops": 0.0, "bytes": 0.0}}
+    iso, roof = bench.roofline_from_trace(rep)
+    peaks = bench._pipe_peaks()
+    k = iso["kernels"]
+    assert k["tcg_kernel"]["bound"] == "tensor"
+    assert k["tcg_kernel"]["achieved"] == pytest.approx(2.1e12 / 5e-3 / 1e12, rel=1e-3)
+    assert k["dgemm_kernel"]["bound"] == "alu"
+    assert k["dgemm_kernel"]["frac"] == pytest.approx(4e8 / 4e-3 / 1e12 / peaks["alu"][0], rel=1e-3)
+    assert k["split_kernel"]["bound"] == "hbm"
+    assert k["split_kernel"]["achieved"] == pytest.approx(3e9 / 1e-3 / 1e9, rel=1e-3)
+    assert "bound" not in k["jacobi_kernel"] and k["jacobi_kernel"]["share"] == pytest.approx(0.4737, abs=1e-3)
+    # the jacobi kernel leads but has no work model: the roofline is the tensor-core GEMM
+    assert roof["kernel"] == "tcg_kernel" and roof["bound"] == "tensor"
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    assert roof["work_per_launch"] == pytest.approx(2.1e11)
+    assert roof["ms_per_launch"] == pytest.approx(0.5)
