@@ -489,7 +489,11 @@ def _pipe_peaks():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # committed ncu summaries, keyed by kernel; None where no capture of the current
 # kernel exists
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # profiles/dram_rank_structured_n2048_single_solve.md: 420 launches of the
+    # timed solve, 211.1 MB read + written in all
+    "dgemm_kernel": 503e3,
+}
 
 
 def roofline_from_trace(rep):
@@ -529,8 +533,12 @@ def roofline_from_trace(rep):
                 "unit": unit, "frac": e["achieved"] / peak,
                 "traffic": TRAFFIC_PER_LAUNCH.get(name), "share": e["share"],
                 "work_per_launch": per_launch, "launches": v["launches"],
-                "ms_per_launch": v["ms"] / v["launches"], "peak_source": src + " (of measured)"
-                if "measured" in src else src}
+                "ms_per_launch": v["ms"] / v["launches"],
+                "peak_source": src + (" (of derived)" if e["bound"] == "alu" else
+                                      " (of measured)" if src.startswith("measured") else
+                                      " (of fallback)")}
+    if v.get("bytes", 0) > 0:
+        roofline["algorithmic_bytes_per_launch"] = v["bytes"] / v["launches"]
     return iso, roofline
 
 

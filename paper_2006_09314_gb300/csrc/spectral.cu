@@ -92,52 +92,90 @@ void sinc_nodes(double g, const SincRule &s, std::vector<double> &t, std::vector
 }
 
 // Lawson-Hanson non-negative least squares min ||A x - b||, x >= 0.
-// A: M x K column-major. Dense Householder least squares on the passive set.
-std::vector<double> ls_solve(const std::vector<double> &A, int M, int K, const std::vector<int> &cols,
-                             const std::vector<double> &b) {
-  const int P = (int)cols.size();
-  std::vector<double> Q((size_t)M * P), rhs(b);
-  for (int j = 0; j < P; ++j)
-    for (int i = 0; i < M; ++i) Q[i + (size_t)j * M] = A[i + (size_t)cols[j] * M];
-  for (int j = 0; j < P; ++j) {
+// A: M x K column-major. The least-squares problem on the passive set is
+// solved from a Householder QR that grows by one column at a time: a column
+// entering the passive set is multiplied by the reflectors of the columns
+// before it and contributes one new reflector (O(M P) work, P passive
+// columns), and Q^T b is updated the same way. When coordinates leave the
+// passive set the factorization is rebuilt from the remaining columns, in
+// their order of entry.
+class IncQR {
+ public:
+  IncQR(const std::vector<double> &A, int M, const std::vector<double> &b)
+      : A_(A), M_(M), b_(b) { reset(); }
+
+  void reset() {
+    cols_.clear();
+    R_.clear();
+    V_.clear();
+    vn_.clear();
+    qb_ = b_;
+  }
+
+  // appends column j of A to the factorization
+  void add(int j) {
+    const int P = (int)cols_.size();
+    std::vector<double> c(A_.begin() + (size_t)j * M_, A_.begin() + (size_t)(j + 1) * M_);
+    for (int p = 0; p < P; ++p) reflect(p, c);
     double nrm = 0;
-    for (int i = j; i < M; ++i) nrm += Q[i + (size_t)j * M] * Q[i + (size_t)j * M];
+    for (int i = P; i < M_; ++i) nrm += c[i] * c[i];
     nrm = std::sqrt(nrm);
-    if (nrm == 0) continue;
-    const double a0 = Q[j + (size_t)j * M];
-    const double alpha = a0 > 0 ? -nrm : nrm;
-    std::vector<double> v(M, 0.0);
-    for (int i = j; i < M; ++i) v[i] = Q[i + (size_t)j * M];
-    v[j] -= alpha;
-    double vn = 0;
-    for (int i = j; i < M; ++i) vn += v[i] * v[i];
-    if (vn == 0) continue;
-    for (int k = j; k < P; ++k) {
-      double s = 0;
-      for (int i = j; i < M; ++i) s += v[i] * Q[i + (size_t)k * M];
-      s = 2 * s / vn;
-      for (int i = j; i < M; ++i) Q[i + (size_t)k * M] -= s * v[i];
+    std::vector<double> v(M_, 0.0);
+    double vn = 0.0, alpha = 0.0;
+    if (nrm > 0) {
+      alpha = c[P] > 0 ? -nrm : nrm;
+      for (int i = P; i < M_; ++i) v[i] = c[i];
+      v[P] -= alpha;
+      for (int i = P; i < M_; ++i) vn += v[i] * v[i];
     }
+    V_.push_back(v);
+    vn_.push_back(vn);
+    cols_.push_back(j);
+    // R column: c[0..P) above the diagonal, alpha on it
+    std::vector<double> rc(c.begin(), c.begin() + P);
+    rc.push_back(vn == 0 ? c[P] : alpha);
+    R_.push_back(rc);
+    reflect(P, qb_);
+  }
+
+  // least-squares coefficients of the passive columns (in order of entry)
+  std::vector<double> solve() const {
+    const int P = (int)cols_.size();
+    std::vector<double> x(P, 0.0);
+    for (int j = P - 1; j >= 0; --j) {
+      double s = qb_[j];
+      for (int k = j + 1; k < P; ++k) s -= R_[k][j] * x[k];
+      const double d = R_[j][j];
+      x[j] = d != 0 ? s / d : 0.0;
+    }
+    return x;
+  }
+
+  const std::vector<int> &cols() const { return cols_; }
+
+ private:
+  void reflect(int p, std::vector<double> &y) const {
+    if (vn_[p] == 0) return;
+    const std::vector<double> &v = V_[p];
     double s = 0;
-    for (int i = j; i < M; ++i) s += v[i] * rhs[i];
-    s = 2 * s / vn;
-    for (int i = j; i < M; ++i) rhs[i] -= s * v[i];
+    for (int i = p; i < M_; ++i) s += v[i] * y[i];
+    s = 2 * s / vn_[p];
+    for (int i = p; i < M_; ++i) y[i] -= s * v[i];
   }
-  std::vector<double> x(P, 0.0);
-  for (int j = P - 1; j >= 0; --j) {
-    double s = rhs[j];
-    for (int k = j + 1; k < P; ++k) s -= Q[j + (size_t)k * M] * x[k];
-    const double d = Q[j + (size_t)j * M];
-    x[j] = d != 0 ? s / d : 0.0;
-  }
-  (void)K;
-  return x;
-}
+
+  const std::vector<double> &A_;
+  int M_;
+  const std::vector<double> &b_;
+  std::vector<int> cols_;
+  std::vector<std::vector<double>> R_, V_;
+  std::vector<double> vn_, qb_;
+};
 
 std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::vector<double> &b) {
   std::vector<double> x(K, 0.0);
   std::vector<char> passive(K, 0), blocked(K, 0);
   const double tol = 1e-15;  // the duals of this ill-conditioned basis are tiny
+  IncQR qr(A, M, b);
   for (int outer = 0; outer < 3 * K; ++outer) {
     // dual w = A^T (b - A x); the most positive free, unblocked coordinate enters
     std::vector<double> res(b);
@@ -154,11 +192,10 @@ std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::
     }
     if (jmax < 0) break;
     passive[jmax] = 1;
+    qr.add(jmax);
     for (int inner = 0; inner < 3 * K; ++inner) {
-      std::vector<int> cols;
-      for (int k = 0; k < K; ++k)
-        if (passive[k]) cols.push_back(k);
-      const std::vector<double> z = ls_solve(A, M, K, cols, b);
+      const std::vector<int> cols = qr.cols();
+      const std::vector<double> z = qr.solve();
       bool allpos = true;
       for (double v : z) allpos = allpos && (v > 0);
       if (allpos) {
@@ -179,6 +216,10 @@ std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::
       x[imin] = 0.0;
       for (size_t j = 0; j < cols.size(); ++j)
         if (x[cols[j]] <= 0.0) { passive[cols[j]] = 0; x[cols[j]] = 0.0; }
+      // rebuild the factorization from the columns still passive (order of entry)
+      qr.reset();
+      for (int cj : cols)
+        if (passive[cj]) qr.add(cj);
       // the entering coordinate left at once: it cannot improve the fit now
       if (imin == jmax && amin == 0.0) { blocked[jmax] = 1; break; }
     }
