@@ -227,6 +227,279 @@ __global__ void twisted_kernel(int n, const double *d0, const double *d1, const 
   }
 }
 
+// ------------------------------------------------------------------ set-up eigensolver
+// The set-up path spends its FP64 work (GB300: 2 FP64 FMA per clock per SM)
+// on few inertia counts: per eigenvalue,
+//   1. an FP32 Sturm bisection inside the Courant-Fischer bracket gives a
+//      guess (the FP32 pipe is ~64x the FP64 one; its counts are only a guess);
+//   2. Rayleigh-quotient iteration on twisted factorizations in FP64: the
+//      factorization of T - sigma I with twist r gives (T - sigma I) z = gamma_r e_r
+//      (z_r = 1), so z^T (T - sigma I) z / z^T z = gamma_r / ||z||^2 and
+//      sigma + gamma_r / ||z||^2 is the Rayleigh quotient of z (cubic
+//      convergence); the inertia of the same factorization (signs of D+)
+//      shrinks a safeguarding bracket, and a step leaving it is a bisection;
+//   3. two FP64 inertia counts at lambda -+ tau confirm the index k; if they
+//      do not (or the iteration does not settle), the eigenvalue is bisected
+//      in FP64 from the Courant-Fischer bracket as before.
+// The eigenvector is the normalised z of the last factorization.
+
+// FP32 copies of d and e^2 (the guess phase), e^2 in FP64, the Weyl sign weights.
+__global__ void eig_prep_kernel(int n, const double *d0, const double *d1, const double *d2,
+                                const double *e0, const double *e1, const double *e2,
+                                float *__restrict__ d32, float *__restrict__ ee32,
+                                double *__restrict__ ee, double *__restrict__ g) {
+  const int l = blockIdx.y;
+  const double *d = l == 0 ? d0 : (l == 1 ? d1 : d2);
+  const double *e = l == 0 ? e0 : (l == 1 ? e1 : e2);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    d32[(size_t)l * n + i] = (float)d[i];
+    const double q = i < n - 1 ? e[i] * e[i] : 0.0;
+    ee[(size_t)l * n + i] = q;
+    ee32[(size_t)l * n + i] = (float)q;
+    if (l == 0) {
+      const double x = (double)(i + 1) * 0.6180339887498949;
+      g[i] = 2.0 * (x - floor(x)) - 1.0;
+    }
+  }
+}
+
+// FP64 reciprocal: the hardware approximation refined by two Newton-Raphson
+// steps r <- r + r (1 - q r), each of which doubles the number of correct bits.
+// The inertia counts need a quotient with a relative error of a few units in
+// the last place, not a correctly rounded one (Kahan's backward-error argument
+// for Sturm counts holds for any operation with a small relative error).
+// |q| >= pivmin > 0 is never subnormal here.
+__device__ __forceinline__ double rcp_nr(double q) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(q));
+  double t = fma(-q, r, 1.0);
+  r = fma(r, t, r);
+  t = fma(-q, r, 1.0);
+  return fma(r, t, r);
+}
+
+// number of eigenvalues below x, FP64 (ee = e^2)
+__device__ int count64(int n, const double *__restrict__ d, const double *__restrict__ ee, double x,
+                       double pivmin) {
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int cnt = q < 0.0;
+  for (int i = 1; i < n; ++i) {
+    q = fma(-ee[i - 1], rcp_nr(q), d[i] - x);
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+// the same in FP32: a guess only, never trusted for the index
+__device__ int count32(int n, const float *__restrict__ d, const float *__restrict__ ee, float x,
+                       float pivmin) {
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = q < 0.0f;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - __fdividef(ee[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0f;
+  }
+  return cnt;
+}
+
+struct Twist {
+  int cnt;      // eigenvalues below sigma (negative D+ pivots)
+  int r;        // twist index
+  double gam;   // gamma_r
+  double nrm2;  // ||z||^2 with z_r = 1
+};
+
+// Twisted factorization of T - sigma I. Forward multipliers L_i = e_i / D+_i and
+// backward ones U_i = e_i / D-_{i+1} go to L[i * ld], U[i * ld] (ld = n: the
+// threads of a warp, consecutive eigenvalues, touch consecutive words).
+__device__ Twist twisted64(int n, const double *__restrict__ d, const double *__restrict__ e,
+                           double sigma, double pivmin, double *__restrict__ L,
+                           double *__restrict__ U, int ld) {
+  Twist t;
+  double dplus = d[0] - sigma;
+  if (fabs(dplus) < pivmin) dplus = pivmin;
+  int cnt = dplus < 0.0;
+  for (int i = 0; i < n - 1; ++i) {
+    const double Li = e[i] * rcp_nr(dplus);
+    L[(size_t)i * ld] = Li;
+    dplus = fma(-Li, e[i], d[i + 1] - sigma);
+    if (fabs(dplus) < pivmin) dplus = pivmin;
+    cnt += dplus < 0.0;
+  }
+  t.cnt = cnt;
+  t.r = n - 1;
+  t.gam = dplus;  // gamma_{n-1} = D+_{n-1}
+  double gbest = fabs(dplus);
+  double dminus = d[n - 1] - sigma;
+  if (fabs(dminus) < pivmin) dminus = pivmin;
+  for (int i = n - 2; i >= 0; --i) {
+    const double Ui = e[i] * rcp_nr(dminus);
+    U[(size_t)i * ld] = Ui;
+    const double ci = d[i] - sigma;
+    dminus = fma(-Ui, e[i], ci);
+    if (fabs(dminus) < pivmin) dminus = pivmin;
+    // D+_i again, from the stored multiplier (same operations as the forward pass)
+    double dp = i == 0 ? ci : fma(-L[(size_t)(i - 1) * ld], e[i - 1], ci);
+    if (fabs(dp) < pivmin) dp = pivmin;
+    const double gam = dp + dminus - ci;
+    if (fabs(gam) < gbest) {
+      gbest = fabs(gam);
+      t.r = i;
+      t.gam = gam;
+    }
+  }
+  // ||z||^2: z_r = 1, z_i = -L_i z_{i+1} (i < r), z_{i+1} = -U_i z_i (i >= r)
+  double zi = 1.0, nrm2 = 1.0;
+  for (int i = t.r - 1; i >= 0; --i) {
+    zi = -L[(size_t)i * ld] * zi;
+    nrm2 = fma(zi, zi, nrm2);
+  }
+  zi = 1.0;
+  for (int i = t.r; i < n - 1; ++i) {
+    zi = -U[(size_t)i * ld] * zi;
+    nrm2 = fma(zi, zi, nrm2);
+  }
+  t.nrm2 = nrm2;
+  return t;
+}
+
+__global__ void eig_rqi_kernel(int n, const double *d0, const double *d1, const double *d2,
+                               const double *e0, const double *e1, const double *e2,
+                               const double *__restrict__ ee_all, const float *__restrict__ d32_all,
+                               const float *__restrict__ ee32_all, const double *__restrict__ g,
+                               const double *bounds, double *l0, double *l1, double *l2,
+                               double *V0, double *V1, double *V2, double *Lscr, double *Uscr,
+                               int *fallbacks) {
+  const int l = blockIdx.y;
+  const double *d = l == 0 ? d0 : (l == 1 ? d1 : d2);
+  const double *e = l == 0 ? e0 : (l == 1 ? e1 : e2);
+  const double *ee = ee_all + (size_t)l * n;
+  const float *d32 = d32_all + (size_t)l * n, *ee32 = ee32_all + (size_t)l * n;
+  double *lam = l == 0 ? l0 : (l == 1 ? l1 : l2);
+  double *V = l == 0 ? V0 : (l == 1 ? V1 : V2);
+  const double glo = bounds[4 * l], ghi = bounds[4 * l + 1], pivmin = bounds[4 * l + 2];
+  const double gnorm = fmax(fabs(glo), fabs(ghi));
+  const float pivmin32 = FLT_MIN * fmaxf(1.0f, (float)(pivmin / DBL_MIN));
+  const double h = 1.0 / (n + 1), h2 = h * h;
+  // coefficient range at the n + 1 half points (Courant-Fischer brackets)
+  __shared__ double s_min[64], s_max[64];
+  double amin = 1e300, amax = -1e300;
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+    double ai;
+    if (i == 0) ai = d[0] * h2 + e[0] * h2;
+    else if (i == n) ai = d[n - 1] * h2 + e[n - 2] * h2;
+    else ai = -e[i - 1] * h2;
+    amin = fmin(amin, ai);
+    amax = fmax(amax, ai);
+  }
+  s_min[threadIdx.x] = amin;
+  s_max[threadIdx.x] = amax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_min[threadIdx.x] = fmin(s_min[threadIdx.x], s_min[threadIdx.x + o]);
+      s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  amin = s_min[0];
+  amax = s_max[0];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double blo = glo, bhi = ghi;
+  if (amin > 0.0) {
+    const double sn = sin(0.5 * M_PI * h * (k + 1));
+    const double mu = 4.0 * sn * sn / h2;
+    const double a = fmax(glo, 0.99 * amin * mu), b = fmin(ghi, 1.01 * amax * mu);
+    if (a < b) {
+      blo = a;
+      bhi = b;
+    }
+  }
+  double *Lk = Lscr + (size_t)l * n * n + k;
+  double *Uk = Uscr + (size_t)l * n * n + k;
+  // 1. FP32 guess
+  float flo = (float)blo, fhi = (float)bhi;
+  for (int it = 0; it < 64; ++it) {
+    const float mid = 0.5f * (flo + fhi);
+    if (mid <= flo || mid >= fhi) break;
+    if (fhi - flo <= 4.0f * FLT_EPSILON * fmaxf(fabsf(flo), fabsf(fhi))) break;
+    if (count32(n, d32, ee32, mid, pivmin32) > k) fhi = mid; else flo = mid;
+  }
+  // 2. Rayleigh-quotient iteration, safeguarded by [lo, hi] (shrunk by every inertia)
+  double lo = blo, hi = bhi;
+  double sigma = fmin(fmax(0.5 * ((double)flo + (double)fhi), blo), bhi);
+  double lamk = 0.0;
+  Twist t{};
+  bool ok = false;
+  for (int it = 0; it < 10; ++it) {
+    t = twisted64(n, d, e, sigma, pivmin, Lk, Uk, n);
+    if (t.cnt <= k) lo = fmax(lo, sigma); else hi = fmin(hi, sigma);
+    const double delta = t.gam / t.nrm2;
+    if (fabs(delta) <= 2.0 * DBL_EPSILON * fabs(sigma) + 8.0 * DBL_EPSILON * gnorm) {
+      lamk = sigma + delta;
+      ok = true;
+      break;
+    }
+    double sn = sigma + delta;
+    if (!(sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+    sigma = sn;
+  }
+  // 3. the index: exactly k eigenvalues below lambda - tau, k + 1 below lambda + tau
+  if (ok) {
+    const double tau = 64.0 * DBL_EPSILON * gnorm + 4.0 * DBL_EPSILON * fabs(lamk);
+    ok = count64(n, d, ee, lamk - tau, pivmin) <= k && count64(n, d, ee, lamk + tau, pivmin) > k;
+  }
+  if (!ok) {
+    // FP64 bisection from the Courant-Fischer bracket (Gershgorin if it fails)
+    lo = blo;
+    hi = bhi;
+    if (!(count64(n, d, ee, lo, pivmin) <= k && count64(n, d, ee, hi, pivmin) > k)) {
+      lo = glo;
+      hi = ghi;
+    }
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
+      if (count64(n, d, ee, mid, pivmin) > k) hi = mid; else lo = mid;
+    }
+    lamk = 0.5 * (lo + hi);
+    t = twisted64(n, d, e, lamk, pivmin, Lk, Uk, n);
+    atomicAdd(fallbacks, 1);
+  }
+  lam[k] = lamk;
+  // eigenvector: z of the last factorization, unit norm, sum_i z_i g_i > 0
+  double dot = 0.0, zi = 1.0;
+  for (int i = t.r - 1; i >= 0; --i) {
+    zi = -Lk[(size_t)i * n] * zi;
+    dot = fma(zi, g[i], dot);
+  }
+  dot = fma(1.0, g[t.r], dot);
+  zi = 1.0;
+  for (int i = t.r; i < n - 1; ++i) {
+    zi = -Uk[(size_t)i * n] * zi;
+    dot = fma(zi, g[i + 1], dot);
+  }
+  const double sc = (dot < 0.0 ? -1.0 : 1.0) / sqrt(t.nrm2);
+  double *z = V + (size_t)k * n;
+  zi = 1.0;
+  for (int i = t.r - 1; i >= 0; --i) {
+    zi = -Lk[(size_t)i * n] * zi;
+    z[i] = zi * sc;
+  }
+  z[t.r] = sc;
+  zi = 1.0;
+  for (int i = t.r; i < n - 1; ++i) {
+    zi = -Uk[(size_t)i * n] * zi;
+    z[i + 1] = zi * sc;
+  }
+}
+
 void setup_eigs(Ctx &c) {
   const int n = c.n;
   for (int l = 0; l < 3; ++l) {
@@ -241,22 +514,29 @@ void setup_eigs(Ctx &c) {
   size_t mk = c.ws.mark();
   double *bounds = c.ws.dbl(12);
   LAUNCH(c, gersh_kernel, 3, 256, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds);
-  dim3 gb((n + 63) / 64, 3);
-  // one warp per block spreads the 3n eigenvalues over all SMs (the inertia
-  // counts are bound by the FP64 pipe of the SMs they run on)
-  dim3 gbis((n + 31) / 32, 3);
+  double *ee = c.ws.dbl((size_t)3 * n), *g = c.ws.dbl(n);
+  float *d32 = reinterpret_cast<float *>(c.ws.dbl(((size_t)3 * n + 1) / 2));
+  float *ee32 = reinterpret_cast<float *>(c.ws.dbl(((size_t)3 * n + 1) / 2));
+  int *fallbacks = c.ws.i32(1);
+  TCTL_CUDA(cudaMemsetAsync(fallbacks, 0, sizeof(int), c.st));
+  LAUNCH(c, eig_prep_kernel, ga, 256, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], d32, ee32,
+         ee, g);
+  double *Lscr = c.ws.dbl((size_t)3 * n * n);
+  double *Uscr = c.ws.dbl((size_t)3 * n * n);
+  // one warp per block spreads the 3n eigenpairs over all SMs (their FP64 work is
+  // bound by the FP64 pipe of the SMs they run on)
+  dim3 geig((n + 31) / 32, 3);
   const auto tb0 = std::chrono::steady_clock::now();
-  LAUNCH(c, bisect_kernel, gbis, 32, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds,
-         c.lam[0], c.lam[1], c.lam[2]);
+  LAUNCH(c, eig_rqi_kernel, geig, 32, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], ee, d32,
+         ee32, g, bounds, c.lam[0], c.lam[1], c.lam[2], c.V[0], c.V[1], c.V[2], Lscr, Uscr,
+         fallbacks);
   if (c.trace) {
-    TCTL_CUDA(cudaStreamSynchronize(c.st));
-    std::fprintf(stderr, "[tctl] bisection %.1f ms\n",
-                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tb0).count());
+    int nf = 0;
+    read_host(c, &nf, fallbacks, sizeof(int));
+    std::fprintf(stderr, "[tctl] eigenpairs %.1f ms (%d of %d by bisection)\n",
+                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tb0).count(),
+                 nf, 3 * n);
   }
-  double *Dp = c.ws.dbl((size_t)3 * n * n);
-  double *Um = c.ws.dbl((size_t)3 * n * n);
-  LAUNCH(c, twisted_kernel, gb, 64, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], bounds,
-         c.lam[0], c.lam[1], c.lam[2], c.V[0], c.V[1], c.V[2], Dp, Um);
   for (int l = 0; l < 3; ++l) {
     c.lam_host[l].resize(n);
     to_host(c, c.lam_host[l].data(), c.lam[l], n);
