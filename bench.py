@@ -489,11 +489,7 @@ def _pipe_peaks():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # committed ncu summaries, keyed by kernel; None where no capture of the current
 # kernel exists
-TRAFFIC_PER_LAUNCH = {
-    # profiles/dram_rank_structured_n2048_single_solve.md: 420 launches of the
-    # timed solve, 211.1 MB read + written in all
-    "dgemm_kernel": 503e3,
-}
+TRAFFIC_PER_LAUNCH = {}
 
 
 def roofline_from_trace(rep):
@@ -750,6 +746,7 @@ def single_arm(args):
         for _ in range(args.warmup):
             ctx.pcg_solve(b)
         times = []
+        l0 = ctx.launch_count()
         for _ in range(args.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
@@ -757,8 +754,10 @@ def single_arm(args):
             e1.record(st)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+        launches = (ctx.launch_count() - l0) / max(1, args.steps)
         print(json.dumps({"single": {"n": args.n, "alpha": p.alpha, "beta": p.beta,
-                                     "ms_per_solve": times, "iters": stats["iters"],
+                                     "ms_per_solve": times, "launches_per_solve": launches,
+                                     "iters": stats["iters"],
                                      "rank_x": list(stats["rank_x"]),
                                      "setup_ms": ctx.stats()["t_setup_ms"]}}), flush=True)
 

@@ -401,6 +401,210 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
   c.ws.reset(mk);
 }
 
+// ------------------------------------------------------------------ grouped GEMM
+// Up to kGroupMax independent GEMMs of the same transposition in one launch
+// (the three modes' Gram matrices and projections of a Tucker step): each
+// item keeps its own shape, pointers and K-split; the launch's CTAs are dealt
+// out to the items in order (item i owns CTAs [cta0_i, cta0_{i+1})), and one
+// grouped reduction adds the split-K partial sums of all items. 32 x 32 tiles:
+// these products have a dimension of at most 64 (ranks), so larger tiles
+// would leave most of their lanes idle.
+constexpr int kGroupMax = 8;
+
+struct GItem {
+  const double *A, *B;
+  double *C, *part;
+  double alpha, beta;
+  int m, n, k, lda, ldb, ldc, splits, kchunk, gx, cta0;
+  long long out0;  // first output of this item in the grouped reduction
+};
+
+struct GArgs {
+  int count;
+  GItem it[kGroupMax];
+};
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) dgemm_group_kernel(GArgs g) {
+  constexpr int BM = 32, BN = 32, TM = BM / 16, TN = BN / 16;
+  __shared__ double As[GEMM_BK][BM + 1];
+  __shared__ double Bs[GEMM_BK][BN + 1];
+  int item = 0;
+  while (item + 1 < g.count && (int)blockIdx.x >= g.it[item + 1].cta0) ++item;
+  const GItem &it = g.it[item];
+  const int local = blockIdx.x - it.cta0;
+  const int split = local % it.splits, tile = local / it.splits;
+  const int row0 = (tile % it.gx) * BM, col0 = (tile / it.gx) * BN;
+  const int m = it.m, n = it.n, k = it.k, lda = it.lda, ldb = it.ldb;
+  const double *__restrict__ A = it.A;
+  const double *__restrict__ B = it.B;
+  const int k0 = split * it.kchunk;
+  const int k1 = min(k, k0 + it.kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+  for (int kb = k0; kb < k1; kb += GEMM_BK) {
+    for (int e = threadIdx.x; e < BM * GEMM_BK; e += 256) {
+      int i, kk;
+      if (!TA) { i = e % BM; kk = e / BM; } else { kk = e % GEMM_BK; i = e / GEMM_BK; }
+      const int gi = row0 + i, gk = kb + kk;
+      double v = 0.0;
+      if (gi < m && gk < k1) v = TA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda];
+      As[kk][i] = v;
+    }
+    for (int e = threadIdx.x; e < BN * GEMM_BK; e += 256) {
+      int j, kk;
+      if (!TB) { kk = e % GEMM_BK; j = e / GEMM_BK; } else { j = e % BN; kk = e / BN; }
+      const int gj = col0 + j, gk = kb + kk;
+      double v = 0.0;
+      if (gj < n && gk < k1) v = TB ? B[gj + (long long)gk * ldb] : B[gk + (long long)gj * ldb];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GEMM_BK; ++kk) {
+      double a[TM], bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gi = row0 + ty + 16 * i, gj = col0 + tx + 16 * j;
+      if (gi >= m || gj >= n) continue;
+      if (it.splits == 1) {
+        double *p = it.C + gi + (long long)gj * it.ldc;
+        *p = (it.beta == 0.0) ? it.alpha * acc[i][j] : fma(it.alpha, acc[i][j], it.beta * *p);
+      } else {
+        it.part[(long long)split * m * n + gi + (long long)gj * m] = acc[i][j];
+      }
+    }
+}
+
+// C_i = alpha_i sum_q part_i,q + beta_i C_i for the items with split K, in the
+// fixed order of splitk_reduce (8 groups of splits, then the groups in order).
+__global__ void __launch_bounds__(256) splitk_reduce_group(GArgs g, long long total) {
+  __shared__ double red[8][33];
+  const long long t = blockIdx.x * 32ll + threadIdx.x;
+  int item = 0;
+  if (t < total)
+    while (item + 1 < g.count && t >= g.it[item + 1].out0) ++item;
+  const GItem &it = g.it[item];
+  const long long mn = (long long)it.m * it.n;
+  const long long r = t - it.out0;
+  double s = 0.0;
+  if (t < total && it.splits > 1) {
+    const double *p = it.part + r;
+#pragma unroll 4
+    for (int q = threadIdx.y; q < it.splits; q += 8) s += p[q * mn];
+  }
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && t < total && it.splits > 1) {
+    for (int q = 1; q < 8; ++q) s += red[q][threadIdx.x];
+    const int i = (int)(r % it.m), j = (int)(r / it.m);
+    double *out = it.C + i + (long long)j * it.ldc;
+    *out = (it.beta == 0.0) ? it.alpha * s : fma(it.alpha, s, it.beta * *out);
+  }
+}
+
+void gemm_group(Ctx &c, int count, const GemmSpec *spec) {
+  // items of one transposition pair go together; empty products are done alone
+  std::vector<int> todo;
+  for (int i = 0; i < count; ++i) {
+    const GemmSpec &q = spec[i];
+    if (q.m <= 0 || q.n <= 0) continue;
+    if (q.k <= 0) {
+      gemm(c, q.ta, q.tb, q.m, q.n, q.k, q.alpha, q.A, q.lda, 0, q.B, q.ldb, 0, q.beta, q.C, q.ldc, 0);
+      continue;
+    }
+    todo.push_back(i);
+  }
+  while (!todo.empty()) {
+    const bool ta = spec[todo[0]].ta, tb = spec[todo[0]].tb;
+    std::vector<int> grp, rest;
+    for (int i : todo) {
+      if (spec[i].ta == ta && spec[i].tb == tb && (int)grp.size() < kGroupMax) grp.push_back(i);
+      else rest.push_back(i);
+    }
+    todo.swap(rest);
+    GArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.count = (int)grp.size();
+    int ctas = 0;
+    long long outs = 0, part_total = 0;
+    double flops = 0, bytes = 0;
+    for (int t = 0; t < g.count; ++t) {
+      const GemmSpec &q = spec[grp[t]];
+      GItem &it = g.it[t];
+      it.A = q.A;
+      it.B = q.B;
+      it.C = q.C;
+      it.alpha = q.alpha;
+      it.beta = q.beta;
+      it.m = q.m;
+      it.n = q.n;
+      it.k = q.k;
+      it.lda = q.lda;
+      it.ldb = q.ldb;
+      it.ldc = q.ldc;
+      it.gx = (q.m + 31) / 32;
+      const int tiles = it.gx * ((q.n + 31) / 32);
+      // the group as a whole aims at about two CTAs per SM; a CTA contracts at
+      // least 4 k-steps of 16, so its fixed costs stay small against its work
+      const int target = (2 * 152 + g.count - 1) / g.count;
+      int splits = 1;
+      if (tiles < target && q.k >= 8 * GEMM_BK)
+        splits = std::min((target + tiles - 1) / tiles, q.k / (4 * GEMM_BK));
+      splits = std::max(1, std::min(splits, 256));
+      int kchunk = (q.k + splits - 1) / splits;
+      kchunk = ((kchunk + GEMM_BK - 1) / GEMM_BK) * GEMM_BK;
+      it.splits = (q.k + kchunk - 1) / kchunk;
+      it.kchunk = kchunk;
+      it.cta0 = ctas;
+      ctas += tiles * it.splits;
+      it.out0 = outs;
+      outs += (long long)q.m * q.n;
+      if (it.splits > 1) part_total += (long long)it.splits * q.m * q.n;
+      flops += 2.0 * q.m * q.n * (double)q.k;
+      bytes += 8.0 * ((double)q.m * q.k + (double)q.k * q.n + (double)q.m * q.n * (1 + (q.beta != 0.0)));
+    }
+    size_t mk = c.ws.mark();
+    double *part = part_total > 0 ? c.ws.dbl((size_t)part_total) : nullptr;
+    long long off = 0;
+    for (int t = 0; t < g.count; ++t)
+      if (g.it[t].splits > 1) {
+        g.it[t].part = part + off;
+        off += (long long)g.it[t].splits * g.it[t].m * g.it[t].n;
+      }
+    c.next_flops = flops;
+    c.next_bytes = bytes;
+#define TCTL_GG(TA_, TB_) LAUNCH(c, (dgemm_group_kernel<TA_, TB_>), ctas, 256, 0, g)
+    if (!ta && !tb) TCTL_GG(false, false);
+    else if (!ta && tb) TCTL_GG(false, true);
+    else if (ta && !tb) TCTL_GG(true, false);
+    else TCTL_GG(true, true);
+#undef TCTL_GG
+    if (part_total > 0) {
+      c.next_bytes = 8.0 * (double)(part_total + outs);
+      LAUNCH(c, splitk_reduce_group, (unsigned)((outs + 31) / 32), dim3(32, 8), 0, g, outs);
+    }
+    c.ws.reset(mk);
+  }
+}
+
 // ------------------------------------------------------------------ elementwise
 __global__ void khatri_rao_kernel(int n, const double *__restrict__ A, int lda, int ra,
                                   const double *__restrict__ B, int ldb, int rb, double *out,
@@ -497,6 +701,47 @@ void fill_zero(Ctx &c, double *x, size_t count) {
 void copy_d(Ctx &c, double *dst, const double *src, size_t count) {
   if (count && dst != src)
     TCTL_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+}
+
+// Up to kCopyMax device-to-device copies in one launch.
+constexpr int kCopyMax = 8;
+struct CopyArgs {
+  int count;
+  double *dst[kCopyMax];
+  const double *src[kCopyMax];
+  long long off[kCopyMax + 1];  // prefix of the element counts
+};
+
+__global__ void copy_multi_kernel(CopyArgs a) {
+  const long long total = a.off[a.count];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i = 0;
+    while (i + 1 < a.count && t >= a.off[i + 1]) ++i;
+    const long long r = t - a.off[i];
+    a.dst[i][r] = a.src[i][r];
+  }
+}
+
+void copy_multi(Ctx &c, int count, double *const *dst, const double *const *src, const size_t *n) {
+  for (int b = 0; b < count; b += kCopyMax) {
+    CopyArgs a;
+    std::memset(&a, 0, sizeof(a));
+    long long tot = 0;
+    for (int i = b; i < std::min(count, b + kCopyMax); ++i) {
+      if (!n[i] || dst[i] == src[i]) continue;
+      a.dst[a.count] = dst[i];
+      a.src[a.count] = src[i];
+      a.off[a.count] = tot;
+      tot += (long long)n[i];
+      ++a.count;
+    }
+    if (!a.count) continue;
+    a.off[a.count] = tot;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 152 * 8);
+    c.next_bytes = 16.0 * tot;
+    LAUNCH(c, copy_multi_kernel, blocks, 256, 0, a);
+  }
 }
 
 __global__ void axpby_kernel(size_t count, double a, const double *x, double b, double *y) {

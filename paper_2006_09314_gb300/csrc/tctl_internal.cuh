@@ -262,6 +262,22 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha,
           const double *A, int lda, long long sA, const double *B, int ldb,
           long long sB, double beta, double *C, int ldc, long long sC,
           int batch = 1, int divA = 1, int divB = 1);
+// One GEMM of a group: C = alpha op(A) op(B) + beta C, column-major.
+struct GemmSpec {
+  bool ta, tb;
+  int m, n, k;
+  double alpha;
+  const double *A;
+  int lda;
+  const double *B;
+  int ldb;
+  double beta;
+  double *C;
+  int ldc;
+};
+// Independent GEMMs in as few launches as their transpositions allow (one
+// launch plus one split-K reduction per transposition pair, up to 8 items).
+void gemm_group(Ctx &c, int count, const GemmSpec *spec);
 // out[:, a + ra*b] = A[:, a] .* B[:, b]   (n rows, Khatri-Rao of columns)
 void khatri_rao(Ctx &c, int n, const double *A, int lda, int ra, const double *B,
                 int ldb, int rb, double *out, int ldo);
@@ -287,6 +303,8 @@ void scale_cols(Ctx &c, int n, int m, double *A, int lda, const double *s, bool 
 void fill_gaussian(Ctx &c, double *x, size_t count, uint64_t seed);
 void fill_zero(Ctx &c, double *x, size_t count);
 void copy_d(Ctx &c, double *dst, const double *src, size_t count);
+// Several device-to-device copies (dst[i] <- src[i], n[i] doubles) in one launch.
+void copy_multi(Ctx &c, int count, double *const *dst, const double *const *src, const size_t *n);
 void axpby(Ctx &c, size_t count, double a, const double *x, double b, double *y);
 // Host copies. to_host / read_host return once the data is on the host (the
 // context stream is synchronised); to_dev / write_dev are stream-ordered and

@@ -225,20 +225,23 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
   size_t mk = c.ws.mark();
   const int r[3] = {x.r[0], x.r[1], x.r[2]};
   const long long sz = (long long)r[0] * r[1] * r[2];
-  double *perm = c.ws.dbl(sz);
+  double *perm1 = c.ws.dbl(sz), *perm2 = c.ws.dbl(sz);
   double *G[3], *lam[3], *U[3];
   std::vector<double> lh[3];
   double *lam_all = c.ws.dbl((size_t)r[0] + r[1] + r[2]);  // one read-back for the three modes
-  for (int l = 0; l < 3; ++l) {
-    G[l] = c.ws.dbl((size_t)r[l] * r[l]);
-    lam[l] = lam_all + (l == 0 ? 0 : l == 1 ? r[0] : r[0] + r[1]);
-    U[l] = c.ws.dbl((size_t)r[l] * r[l]);
-    const double *src = x.core;
-    if (l == 1) { permute3(c, r, x.core, 1, 0, 2, perm); src = perm; }
-    if (l == 2) { permute3(c, r, x.core, 2, 0, 1, perm); src = perm; }
-    // mode-l unfolding (r_l x rest), column-major with ld r_l
-    gemm(c, false, true, r[l], r[l], (int)(sz / r[l]), 1.0, src, r[l], 0, src, r[l], 0, 0.0, G[l],
-         r[l], 0);
+  permute3(c, r, x.core, 1, 0, 2, perm1);
+  permute3(c, r, x.core, 2, 0, 1, perm2);
+  {
+    // Gram matrices of the three mode-l unfoldings (r_l x rest, ld r_l) in one launch
+    const double *src[3] = {x.core, perm1, perm2};
+    GemmSpec g[3];
+    for (int l = 0; l < 3; ++l) {
+      G[l] = c.ws.dbl((size_t)r[l] * r[l]);
+      lam[l] = lam_all + (l == 0 ? 0 : l == 1 ? r[0] : r[0] + r[1]);
+      U[l] = c.ws.dbl((size_t)r[l] * r[l]);
+      g[l] = {false, true, r[l], r[l], (int)(sz / r[l]), 1.0, src[l], r[l], src[l], r[l], 0.0, G[l], r[l]};
+    }
+    gemm_group(c, 3, g);
   }
   sym_eig_multi(c, 3, r, G, lam, U);
   double tot = 0.0;
@@ -271,12 +274,22 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
   ttm(c, rc, t1, U[1], r[1], true, rn[1], 1, t2);
   rc[1] = rn[1];
   ttm(c, rc, t2, U[2], r[2], true, rn[2], 2, x.core);
-  // new factors Q_l U_l[:, :rn]
-  double *Qt = c.ws.dbl((size_t)n * kMaxRank);
-  for (int l = 0; l < 3; ++l) {
-    gemm(c, false, false, n, rn[l], r[l], 1.0, x.Q[l], n, 0, U[l], r[l], 0, 0.0, Qt, n, 0);
-    copy_d(c, x.Q[l], Qt, (size_t)n * rn[l]);
-    x.r[l] = rn[l];
+  // new factors Q_l U_l[:, :rn], the three modes in one launch
+  {
+    GemmSpec g[3];
+    double *dst[3];
+    const double *srcq[3];
+    size_t cnt[3];
+    for (int l = 0; l < 3; ++l) {
+      double *Qt = c.ws.dbl((size_t)n * rn[l]);
+      g[l] = {false, false, n, rn[l], r[l], 1.0, x.Q[l], n, U[l], r[l], 0.0, Qt, n};
+      dst[l] = x.Q[l];
+      srcq[l] = Qt;
+      cnt[l] = (size_t)n * rn[l];
+    }
+    gemm_group(c, 3, g);
+    copy_multi(c, 3, dst, srcq, cnt);
+    for (int l = 0; l < 3; ++l) x.r[l] = rn[l];
   }
   c.ws.reset(mk);
 }
@@ -287,9 +300,13 @@ double tucker_inner(Ctx &c, const Tucker &x, const Tucker &y) {
   const int n = c.n;
   size_t mk = c.ws.mark();
   double *M[3];
-  for (int l = 0; l < 3; ++l) {
-    M[l] = c.ws.dbl((size_t)x.r[l] * y.r[l]);
-    gemm(c, true, false, x.r[l], y.r[l], n, 1.0, x.Q[l], n, 0, y.Q[l], n, 0, 0.0, M[l], x.r[l], 0);
+  {
+    GemmSpec g[3];
+    for (int l = 0; l < 3; ++l) {
+      M[l] = c.ws.dbl((size_t)x.r[l] * y.r[l]);
+      g[l] = {true, false, x.r[l], y.r[l], n, 1.0, x.Q[l], n, y.Q[l], n, 0.0, M[l], x.r[l]};
+    }
+    gemm_group(c, 3, g);
   }
   const long long big = (long long)std::max(x.r[0], y.r[0]) * std::max(x.r[1], y.r[1]) *
                         std::max(x.r[2], y.r[2]);
@@ -333,21 +350,40 @@ void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucke
   size_t mk = c.ws.mark();
   double *My[3];
   int rz[3];
-  double *Qz[3], *Wl[3];
+  double *Qz[3], *Wl[3], *C1[3], *C2[3];
   for (int l = 0; l < 3; ++l) {
-    const int rx = x.r[l], ry = y.r[l];
-    double *C1 = c.ws.dbl((size_t)rx * ry);
-    double *W = c.ws.dbl((size_t)n * ry);
-    // W = Q_y - Q_x (Q_x^T Q_y), twice (block classical Gram-Schmidt with reorthogonalisation)
-    gemm(c, true, false, rx, ry, n, 1.0, x.Q[l], n, 0, y.Q[l], n, 0, 0.0, C1, rx, 0);
-    copy_d(c, W, y.Q[l], (size_t)n * ry);
-    gemm(c, false, false, n, ry, rx, -1.0, x.Q[l], n, 0, C1, rx, 0, 1.0, W, n, 0);
-    double *C2 = c.ws.dbl((size_t)rx * ry);
-    gemm(c, true, false, rx, ry, n, 1.0, x.Q[l], n, 0, W, n, 0, 0.0, C2, rx, 0);
-    gemm(c, false, false, n, ry, rx, -1.0, x.Q[l], n, 0, C2, rx, 0, 1.0, W, n, 0);
+    C1[l] = c.ws.dbl((size_t)x.r[l] * y.r[l]);
+    C2[l] = c.ws.dbl((size_t)x.r[l] * y.r[l]);
+    Wl[l] = c.ws.dbl((size_t)n * y.r[l]);
     Qz[l] = c.ws.dbl((size_t)n * kMaxRank);
-    copy_d(c, Qz[l], x.Q[l], (size_t)n * rx);
-    Wl[l] = W;
+  }
+  // W = Q_y - Q_x (Q_x^T Q_y), twice (block classical Gram-Schmidt with
+  // reorthogonalisation), the three modes in one launch per step
+  {
+    GemmSpec g[3];
+    double *dst[6];
+    const double *src[6];
+    size_t cnt[6];
+    for (int l = 0; l < 3; ++l) {
+      g[l] = {true, false, x.r[l], y.r[l], n, 1.0, x.Q[l], n, y.Q[l], n, 0.0, C1[l], x.r[l]};
+      dst[l] = Wl[l];
+      src[l] = y.Q[l];
+      cnt[l] = (size_t)n * y.r[l];
+      dst[3 + l] = Qz[l];
+      src[3 + l] = x.Q[l];
+      cnt[3 + l] = (size_t)n * x.r[l];
+    }
+    gemm_group(c, 3, g);
+    copy_multi(c, 6, dst, src, cnt);
+    for (int l = 0; l < 3; ++l)
+      g[l] = {false, false, n, y.r[l], x.r[l], -1.0, x.Q[l], n, C1[l], x.r[l], 1.0, Wl[l], n};
+    gemm_group(c, 3, g);
+    for (int l = 0; l < 3; ++l)
+      g[l] = {true, false, x.r[l], y.r[l], n, 1.0, x.Q[l], n, Wl[l], n, 0.0, C2[l], x.r[l]};
+    gemm_group(c, 3, g);
+    for (int l = 0; l < 3; ++l)
+      g[l] = {false, false, n, y.r[l], x.r[l], -1.0, x.Q[l], n, C2[l], x.r[l], 1.0, Wl[l], n};
+    gemm_group(c, 3, g);
   }
   // orthonormal complements of the three modes in one batched call
   {
@@ -362,11 +398,14 @@ void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucke
     orth_multi(c, 3, n, ms, Wl, lds, 1e-8, false, caps, Qw, rw);
     for (int l = 0; l < 3; ++l) rz[l] = x.r[l] + rw[l];
   }
-  for (int l = 0; l < 3; ++l) {
+  {
     // coordinates of Q_y in [Q_x | Q_w]: [C1 + C2 ; Q_w^T Q_y]
-    const int ry = y.r[l];
-    My[l] = c.ws.dbl((size_t)rz[l] * ry);
-    gemm(c, true, false, rz[l], ry, n, 1.0, Qz[l], n, 0, y.Q[l], n, 0, 0.0, My[l], rz[l], 0);
+    GemmSpec g[3];
+    for (int l = 0; l < 3; ++l) {
+      My[l] = c.ws.dbl((size_t)rz[l] * y.r[l]);
+      g[l] = {true, false, rz[l], y.r[l], n, 1.0, Qz[l], n, y.Q[l], n, 0.0, My[l], rz[l]};
+    }
+    gemm_group(c, 3, g);
   }
   const long long szz = (long long)rz[0] * rz[1] * rz[2];
   double *core = c.ws.dbl(szz);
@@ -383,11 +422,13 @@ void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucke
   rc[1] = rz[1];
   ttm(c, rc, t2, My[2], rz[2], false, rz[2], 2, t3);
   axpby(c, (size_t)szz, b, t3, 1.0, core);
-  for (int l = 0; l < 3; ++l) {
-    z.r[l] = rz[l];
-    copy_d(c, z.Q[l], Qz[l], (size_t)n * rz[l]);
+  {
+    double *dst[4] = {z.Q[0], z.Q[1], z.Q[2], z.core};
+    const double *src[4] = {Qz[0], Qz[1], Qz[2], core};
+    size_t cnt[4] = {(size_t)n * rz[0], (size_t)n * rz[1], (size_t)n * rz[2], (size_t)szz};
+    for (int l = 0; l < 3; ++l) z.r[l] = rz[l];
+    copy_multi(c, 4, dst, src, cnt);
   }
-  copy_d(c, z.core, core, (size_t)szz);
   c.ws.reset(mk);
   finish();
 }
