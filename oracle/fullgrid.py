@@ -31,13 +31,16 @@ __all__ = [
     "solve_exact",
     "state_exact",
     "streamed_rel_error",
+    "streamed_rel_errors",
 ]
 
 
 def F2(s, alpha: float, beta: float):
-    """F2(s) = s^-alpha + beta s^alpha (the symbol of the control equation)."""
-    s = np.asarray(s, dtype=np.float64)
-    return s ** (-alpha) + beta * s ** alpha
+    """F2(s) = s^-alpha + beta s^alpha (the symbol of the control equation).
+
+    s^alpha is evaluated once and s^-alpha as its reciprocal."""
+    t = np.asarray(s, dtype=np.float64) ** alpha
+    return 1.0 / t + beta * t
 
 
 def spectral_sum(lams) -> np.ndarray:
@@ -85,32 +88,57 @@ def state_exact(U: np.ndarray, lams, Vs, alpha: float, beta_state: float = 1.0) 
     return beta_state * from_eigenbasis(to_eigenbasis(U, Vs) * S ** (-alpha), Vs)
 
 
-def _slab_terms(args):
-    (l1, l2, l3c, Yh1, Yh2, yw3, Uh1, Uh2, uw3, alpha, beta) = args
-    S = l1[:, None] + l2[None, :] + l3c
-    ystar = (Yh1 * yw3[None, :]) @ Yh2.T / F2(S, alpha, beta)
-    uh = (Uh1 * uw3[None, :]) @ Uh2.T
-    d = ystar - uh
-    return float(np.sum(d * d)), float(np.sum(ystar * ystar))
+def _slab_range_terms(args):
+    """||u*_hat||^2 and ||u*_hat - u_hat_m||^2 summed over the i3-slabs c0 <= c < c1."""
+    (l1, l2, l3, c0, c1, Yh1, Yh2, y3, sols, alpha, beta) = args
+    n1, blk = l1.shape[0], 256  # rows of a slab at a time (cache-sized temporaries)
+    den = 0.0
+    num = [0.0] * len(sols)
+    for c in range(c0, c1):
+        Yw = Yh1 * y3[c][None, :]
+        Us = [(Uh1 * u3[c][None, :], Uh2) for Uh1, Uh2, u3 in sols]
+        for i0 in range(0, n1, blk):
+            S = l1[i0:i0 + blk, None] + l2[None, :] + l3[c]
+            ystar = Yw[i0:i0 + blk] @ Yh2.T
+            np.divide(ystar, F2(S, alpha, beta), out=ystar)
+            yv = ystar.ravel()
+            den += float(yv @ yv)
+            for m, (A1, Uh2) in enumerate(Us):
+                d = A1[i0:i0 + blk] @ Uh2.T
+                np.subtract(ystar, d, out=d)
+                dv = d.ravel()
+                num[m] += float(dv @ dv)
+    return den, num
+
+
+def streamed_rel_errors(lams, yw, yU_hat, sols, alpha, beta, pool=None):
+    """||u* - u_m|| / ||u*|| for several canonical u_m of one problem, one pass.
+
+    Both tensors are given in the eigenbasis as canonical factors:
+    y_hat = sum_j yw_j (x_l yU_hat[l][:, j]), u_hat = sum_k uw_k (x_l uU_hat[l][:, k]);
+    sols is a list of (uw, uU_hat). The tensor eigenbasis is orthogonal, so the
+    error there equals the error on the grid. u*_hat = y_hat ./ F2(S) is formed
+    one i3-slab at a time (never the n^3 array), once for all the solutions;
+    a pool, if given, takes contiguous ranges of slabs.
+    """
+    l1, l2, l3 = lams
+    n3 = l3.shape[0]
+    y3 = yU_hat[2] * yw[None, :]
+    s3 = [(uU[0], uU[1], uU[2] * uw[None, :]) for uw, uU in sols]
+    parts = 1 if pool is None else min(n3, 4 * getattr(pool, "_processes", 4))
+    bounds = [round(i * n3 / parts) for i in range(parts + 1)]
+    jobs = [(l1, l2, l3, bounds[i], bounds[i + 1], yU_hat[0], yU_hat[1], y3, s3, alpha, beta)
+            for i in range(parts) if bounds[i + 1] > bounds[i]]
+    res = pool.map(_slab_range_terms, jobs, chunksize=1) if pool is not None else map(_slab_range_terms, jobs)
+    den = 0.0
+    num = [0.0] * len(sols)
+    for d, nm in res:
+        den += d
+        for m in range(len(sols)):
+            num[m] += nm[m]
+    return [float(np.sqrt(v / den)) for v in num]
 
 
 def streamed_rel_error(lams, yw, yU_hat, uw, uU_hat, alpha, beta, pool=None):
-    """||u* - u|| / ||u*|| without forming n^3 arrays.
-
-    Both tensors are given in the eigenbasis as canonical factors:
-    y_hat = sum_j yw_j (x_l yU_hat[l][:, j]), u_hat = sum_k uw_k (x_l uU_hat[l][:, k]).
-    The tensor eigenbasis is orthogonal, so the error there equals the error
-    on the grid. u*_hat = y_hat ./ F2(S) is formed one i3-slab at a time.
-    """
-    l1, l2, l3 = lams
-    jobs = []
-    for c in range(l3.shape[0]):
-        jobs.append((l1, l2, l3[c], yU_hat[0], yU_hat[1], yw * yU_hat[2][c, :],
-                     uU_hat[0], uU_hat[1], uw * uU_hat[2][c, :], alpha, beta))
-    res = pool.map(_slab_terms, jobs, chunksize=16) if pool is not None else map(_slab_terms, jobs)
-    num = 0.0
-    den = 0.0
-    for a, b in res:
-        num += a
-        den += b
-    return float(np.sqrt(num / den))
+    """||u* - u|| / ||u*|| without forming n^3 arrays (one solution of streamed_rel_errors)."""
+    return streamed_rel_errors(lams, yw, yU_hat, [(uw, uU_hat)], alpha, beta, pool=pool)[0]

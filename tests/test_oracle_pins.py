@@ -240,6 +240,13 @@ def test_streamed_error_matches_full():
     streamed = fg.streamed_rel_error(lams, yw, yUh, vw, vUh, alpha, beta)
     assert streamed == pytest.approx(full, rel=1e-10)
     assert u.shape == Y.shape
+    # several solutions in one pass: each against the error of its full expansion
+    w2, U2 = _rand_cp(rng, n, 3)
+    w2 = 3e-2 * w2
+    vw2, vU2h = F.cp_to_eigenbasis(w2, U2, Vs)
+    full2 = np.linalg.norm(F.cp_full(w2, U2) - ustar) / np.linalg.norm(ustar)
+    many = fg.streamed_rel_errors(lams, yw, yUh, [(vw, vUh), (vw2, vU2h)], alpha, beta)
+    assert many[0] == pytest.approx(full, rel=1e-10) and many[1] == pytest.approx(full2, rel=1e-10)
 
 
 # ---------------------------------------------------------------- sinc exp-sums (Section 3.4)
