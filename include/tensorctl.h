@@ -78,7 +78,7 @@ typedef struct {
                          0 = paper form, mode products with V_l in every apply         */
   int expsum_src;     /* separable F2: 0 = sinc quadrature (Section 3.4); 1 = fitted
                          exponential sum of F2(s)/s (default; falls back to sinc
-                         when the fit misses op_tol)                                   */
+                         when the fit misses op_tol); 2 = learned sum (op_model)      */
   int paper_end_rows; /* 1 = the paper's printed end rows of A_(l) (default 0)        */
   double eps_final;   /* truncation of the returned solution; <= 0 means eps/10       */
   unsigned long long seed; /* seed of the sketching random numbers (default 1)       */
@@ -107,6 +107,17 @@ typedef struct {
   double pre_delta_max;   /* acceptance bound of pre_src 1 / 2 (default 0.25)           */
   int workspace_mb;   /* device workspace arena of the context in MiB; 0 = automatic
                          (sized from n); too small an arena fails with TCTL_E_NOMEM   */
+  const float *op_model; /* HOST model blob of tctl_mlp_train for expsum_src 2: the
+                         network's op_r nodes of g(s) = F2(s)/s, weights re-solved by
+                         NNLS; used only if the measured max relative error of F2 on
+                         [s_min, s_max] is <= op_judge, else the sinc quadrature
+                         (at op_tol) is used; alpha = 1 always uses sinc          */
+  int op_r;           /* terms of the learned operator sum (default 16)              */
+  double op_judge;    /* acceptance bound of the learned operator sum (default 1e-7)  */
+  int tune;           /* 1 = tile autotuner for the tensor-core GEMMs (default): the
+                         contracted length per CTA (64, 128 or 256) of each shape
+                         class is timed at its first use and kept for the process;
+                         0 = fixed 256                                                 */
 } tctl_opts;
 
 typedef struct {
@@ -121,12 +132,16 @@ typedef struct {
   double s_min, s_max;   /* spectral interval of A                                    */
   double t_setup_ms;     /* time of tctl_setup                                       */
   double t_solve_ms;     /* time of the last tctl_pcg_solve                          */
-  int expsum_used;       /* representation of F2 in use: 0 sinc, 1 fitted             */
+  int expsum_used;       /* representation of F2 in use: 0 sinc, 1 fitted, 2 learned  */
   int pre_used;          /* preconditioner in use: 0 NNLS nodes, 1 fitted, 2 learned,
                             3 anisotropic Laplacian (case (A))                         */
   double pre_delta;      /* its measured max |P(s) F2(s) - 1| on [s_min, s_max]       */
   double ws_peak_mb;     /* peak use of the context's workspace arena so far (MiB)    */
   double ws_size_mb;     /* size of the arena (MiB)                                    */
+  double op_learned_err; /* expsum_src 2: measured max rel. error of F2 of the learned
+                            sum (accepted when <= op_judge); 0 otherwise               */
+  double sinc24_err;     /* expsum_src 2: the same error of the sinc quadrature with 24
+                            terms per function (the judge's reference); 0 otherwise    */
 } tctl_stats;
 
 /* Fills *o with the defaults listed above. */
@@ -310,6 +325,15 @@ int tctl_precond_fit(double alpha, double beta, double s_min, double s_max, int 
                      double *p, double *delta);
 int tctl_precond_dataset(int r, int n_samples, unsigned long long seed, int threads, float *X,
                          float *Y, double *delta);
+/* The same for either head: which = 0 fits r-term sums of the operator's
+ * g(s) = F2(s)/s (F2 = s sum_k w_k exp(-t_k s), Section 3.4's exponential-sum
+ * form with free nodes), which = 1 the preconditioner sums of
+ * tctl_precond_dataset. Targets Y (n x 2r): ln tau_k ascending, ln q_k in
+ * x = s / s_min units with the sum normalised by its target at s_min;
+ * err (n, may be NULL): measured max relative error of F2 (which = 0) or
+ * delta (which = 1). Inputs as tctl_precond_dataset (alpha < 1 throughout). */
+int tctl_expsum_dataset(int which, int r, int n_samples, unsigned long long seed, int threads,
+                        float *X, float *Y, double *err);
 int tctl_mlp_model_size(int r);
 int tctl_mlp_train(int r, int n_samples, const float *X, const float *Y, int steps, int batch,
                    float lr, unsigned long long seed, float *model, float *loss);
@@ -372,6 +396,12 @@ int tctl_eig1d_noalloc(const double *coeffs, int n, int paper_end_rows, double *
  * and the context stays usable for the next call. Nothing faults, traps or
  * hangs. count = 0 cancels. Errors: TCTL_E_ARG (NULL context, count < 0). */
 int tctl_inject_wait_timeout(tctl_ctx *ctx, int count);
+
+/* The tile autotuner's table (process-wide, host only): a JSON list with one
+ * object per shape class met so far (digits, k steps of 16, log2 of the tile
+ * count, the chosen k per CTA and the timed candidates in ms). Errors:
+ * TCTL_E_ARG (NULL buffer or too small). */
+int tctl_tune_report(char *buf, int buflen);
 
 /* Per-kernel timing (tracing): when enabled, the context records a pair of
  * CUDA events on its stream around every kernel it launches. The report is a

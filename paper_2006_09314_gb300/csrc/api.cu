@@ -235,6 +235,10 @@ int tctl_default_opts(tctl_opts *o) {
   o->pre_r = 12;
   o->pre_model = nullptr;
   o->pre_delta_max = 0.25;
+  o->op_model = nullptr;
+  o->op_r = 16;
+  o->op_judge = 1e-7;
+  o->tune = 1;
   return TCTL_OK;
 }
 
@@ -260,8 +264,13 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
       fail(TCTL_E_ARG, "precision must be 0 (FP64) or 1 (tensor-core digit split)");
     if (c->o.precision == 1 && !tc_fullgrid_supported(n))
       fail(TCTL_E_ARG, "precision 1 needs n a multiple of 128 and n <= 1024");
-    if (c->o.expsum_src != 0 && c->o.expsum_src != 1)
-      fail(TCTL_E_ARG, "expsum_src must be 0 (sinc) or 1 (fitted)");
+    if (c->o.expsum_src < 0 || c->o.expsum_src > 2)
+      fail(TCTL_E_ARG, "expsum_src must be 0 (sinc), 1 (fitted) or 2 (learned)");
+    if (c->o.expsum_src == 2 && !c->o.op_model) fail(TCTL_E_ARG, "expsum_src 2 needs op_model");
+    if (c->o.expsum_src == 2 && (c->o.op_r < 2 || c->o.op_r > kPreRMax))
+      fail(TCTL_E_ARG, "op_r must be in [2, 32]");
+    if (c->o.expsum_src == 2 && !(c->o.op_judge > 0.0 && c->o.op_judge < 1.0))
+      fail(TCTL_E_ARG, "op_judge must be in (0, 1)");
     if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
     if (c->o.tc_gemm != 0 && c->o.tc_gemm != 1) fail(TCTL_E_ARG, "tc_gemm must be 0 or 1");
     if (c->o.workspace_mb < 0) fail(TCTL_E_ARG, "workspace_mb must be >= 0");
@@ -314,6 +323,8 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
     c->stats.expsum_used = c->expsum_used;
     c->stats.pre_used = c->pre_used;
     c->stats.pre_delta = c->pre_delta;
+    c->stats.op_learned_err = c->op_learned_err;
+    c->stats.sinc24_err = c->sinc24_err;
     c->stats.s_min = c->s_min;
     c->stats.s_max = c->s_max;
     *ctx = reinterpret_cast<tctl_ctx *>(c);
@@ -609,6 +620,14 @@ int tctl_gemm_kr(tctl_ctx *ctx, int digits, int k, int ra, int rb, int n, double
   }
 }
 
+int tctl_tune_report(char *buf, int buflen) {
+  if (!buf || buflen <= 0) return TCTL_E_ARG;
+  const std::string js = tune_report();
+  if ((int)js.size() + 1 > buflen) return TCTL_E_ARG;
+  std::memcpy(buf, js.c_str(), js.size() + 1);
+  return TCTL_OK;
+}
+
 int tctl_inject_wait_timeout(tctl_ctx *ctx, int count) {
   Ctx *c = reinterpret_cast<Ctx *>(ctx);
   if (!c || count < 0) return TCTL_E_ARG;
@@ -663,7 +682,22 @@ int tctl_precond_dataset(int r, int n_samples, unsigned long long seed, int thre
     if (r < 2 || r > kPreRMax) fail(TCTL_E_ARG, "r must be in [2, 32]");
     if (n_samples < 1 || !X || !Y) fail(TCTL_E_ARG, "need n_samples >= 1 and output buffers");
     precond_sample_inputs(n_samples, seed, X);
-    precond_dataset(r, n_samples, X, std::max(1, std::min(threads, 256)), Y, delta);
+    expsum_dataset(FitTarget::Pre, r, n_samples, X, std::max(1, std::min(threads, 256)), Y, delta);
+    return TCTL_OK;
+  } catch (const Error &e) {
+    return handle(nullptr, e);
+  }
+}
+
+int tctl_expsum_dataset(int which, int r, int n_samples, unsigned long long seed, int threads,
+                        float *X, float *Y, double *err) {
+  try {
+    if (which != 0 && which != 1) fail(TCTL_E_ARG, "which must be 0 (operator) or 1 (preconditioner)");
+    if (r < 2 || r > kPreRMax) fail(TCTL_E_ARG, "r must be in [2, 32]");
+    if (n_samples < 1 || !X || !Y) fail(TCTL_E_ARG, "need n_samples >= 1 and output buffers");
+    precond_sample_inputs(n_samples, seed, X);
+    expsum_dataset(which == 0 ? FitTarget::Op : FitTarget::Pre, r, n_samples, X,
+                   std::max(1, std::min(threads, 256)), Y, err);
     return TCTL_OK;
   } catch (const Error &e) {
     return handle(nullptr, e);

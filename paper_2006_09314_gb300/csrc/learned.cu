@@ -17,6 +17,10 @@
 //     graph and replayed;
 //   * inference: the network's nodes, with the weights re-solved by NNLS on
 //     those nodes (one small least-squares problem on the host).
+// The same fitter and network serve the operator: an r-term sum
+// g(s) = F2(s)/s ~ sum_k w_k exp(-t_k s) (F2 = s g, 3 Kronecker terms per
+// node; Section 3.4's exponential-sum representation with free nodes), whose
+// quality is the measured max relative error of F2 on [s_min, s_max].
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -33,8 +37,12 @@ constexpr int kFitM = 300;      // fitting samples
 constexpr int kCheckM = 2000;   // samples of the measured delta
 
 double F2s(double s, double a, double b) { return std::pow(s, -a) + b * std::pow(s, a); }
-// P(s)/s must approximate h(s) = 1 / (s F2(s))
+// P(s)/s must approximate h(s) = 1 / (s F2(s)); the operator's sum approximates
+// g(s) = F2(s) / s
 double h_of(double s, double a, double b) { return 1.0 / (s * F2s(s, a, b)); }
+double target_of(FitTarget t, double s, double a, double b) {
+  return t == FitTarget::Pre ? h_of(s, a, b) : F2s(s, a, b) / s;
+}
 
 // Cholesky solve of the SPD system A x = b (n x n, row-major); false if not SPD.
 bool chol_solve(std::vector<double> A, std::vector<double> &x, int n) {
@@ -65,28 +73,36 @@ bool chol_solve(std::vector<double> A, std::vector<double> &x, int n) {
 
 }  // namespace
 
-double pre_delta(const double *theta, const double *p, int r, double a, double b, double smin,
-                 double smax) {
+// max over 2000 log-spaced s of |sum_k w_k exp(-t_k s) / target(s) - 1|: for the
+// preconditioner delta = max |P F2 - 1|, for the operator the relative error of F2
+double sum_rel_err(FitTarget tg, const double *t, const double *w, int r, double a, double b,
+                   double smin, double smax) {
   double dmax = 0.0;
   for (int j = 0; j < kCheckM; ++j) {
     const double s = std::exp(std::log(smin) + (std::log(smax) - std::log(smin)) * j / (kCheckM - 1));
     double v = 0.0;
-    for (int k = 0; k < r; ++k) v += p[k] * std::exp(-theta[k] * s);
-    dmax = std::max(dmax, std::fabs(s * v * F2s(s, a, b) - 1.0));
+    for (int k = 0; k < r; ++k) v += w[k] * std::exp(-t[k] * s);
+    dmax = std::max(dmax, std::fabs(v / target_of(tg, s, a, b) - 1.0));
   }
   return dmax;
 }
 
-// NNLS weights of P on fixed nodes theta (s units); returns p (>= 0).
-std::vector<double> pre_weights_nnls(const std::vector<double> &theta, double a, double b, double smin,
-                                     double smax) {
+double pre_delta(const double *theta, const double *p, int r, double a, double b, double smin,
+                 double smax) {
+  return sum_rel_err(FitTarget::Pre, theta, p, r, a, b, smin, smax);
+}
+
+// NNLS weights on fixed nodes (s units) minimising the relative residual
+// sum_k w_k exp(-t_k s_j) / target(s_j) - 1 on kFitM samples; w >= 0.
+std::vector<double> weights_nnls(FitTarget tg, const std::vector<double> &theta, double a, double b,
+                                 double smin, double smax) {
   const int r = (int)theta.size(), M = kFitM;
   std::vector<double> A((size_t)M * r), cs(r), rhs(M, 1.0);
   for (int k = 0; k < r; ++k) {
     double nrm = 0;
     for (int j = 0; j < M; ++j) {
       const double s = std::exp(std::log(smin) + (std::log(smax) - std::log(smin)) * j / (M - 1));
-      const double v = std::exp(-theta[k] * s) * s * F2s(s, a, b);
+      const double v = std::exp(-theta[k] * s) / target_of(tg, s, a, b);
       A[j + (size_t)k * M] = v;
       nrm += v * v;
     }
@@ -98,20 +114,25 @@ std::vector<double> pre_weights_nnls(const std::vector<double> &theta, double a,
   return q;
 }
 
+std::vector<double> pre_weights_nnls(const std::vector<double> &theta, double a, double b, double smin,
+                                     double smax) {
+  return weights_nnls(FitTarget::Pre, theta, a, b, smin, smax);
+}
+
 // r-term fit. Outputs tau (ascending, x = s / s_min units) and q (weights of
 // exp(-tau x) approximating h(s_min x) / h(s_min)); theta = tau / s_min,
 // p = q h(s_min). Returns the measured delta.
 namespace {
 
 // One Levenberg-Marquardt run from geometric nodes over [lo / rho, hi] (x units).
-double pre_fit_from(double a, double b, double smin, double smax, int r, double lo, double hi,
-                    double *tau_out, double *q_out) {
+double fit_from(FitTarget tg, double a, double b, double smin, double smax, int r, double lo,
+                double hi, double *tau_out, double *q_out) {
   const int M = kFitM, P = 2 * r;
-  const double rho = smax / smin, h0 = h_of(smin, a, b);
+  const double rho = smax / smin, h0 = target_of(tg, smin, a, b);
   std::vector<double> x(M), H(M);
   for (int j = 0; j < M; ++j) {
     x[j] = std::exp(std::log(rho) * j / (M - 1));
-    H[j] = h_of(smin * x[j], a, b) / h0;
+    H[j] = target_of(tg, smin * x[j], a, b) / h0;
   }
   // start: geometric nodes in [0.05 / rho, 20], NNLS weights (zeros lifted)
   std::vector<double> th(P);
@@ -119,7 +140,7 @@ double pre_fit_from(double a, double b, double smin, double smax, int r, double 
     std::vector<double> theta(r);
     for (int k = 0; k < r; ++k)
       theta[k] = std::exp(std::log(lo / rho) + (std::log(hi) - std::log(lo / rho)) * k / std::max(1, r - 1)) / smin;
-    std::vector<double> p = pre_weights_nnls(theta, a, b, smin, smax);
+    std::vector<double> p = weights_nnls(tg, theta, a, b, smin, smax);
     double pmax = 0;
     for (double v : p) pmax = std::max(pmax, v);
     if (!(pmax > 0)) pmax = h0;
@@ -221,24 +242,25 @@ double pre_fit_from(double a, double b, double smin, double smax, int r, double 
     theta[k] = tau_out[k] / smin;
     p[k] = q_out[k] * h0;
   }
-  return pre_delta(theta.data(), p.data(), r, a, b, smin, smax);
+  return sum_rel_err(tg, theta.data(), p.data(), r, a, b, smin, smax);
 }
 
 }  // namespace
 
 // r-term fit, best of up to three starts: the node range of the K-node default
 // first, two more ranges when the first run gains less than 2x over its start.
-double pre_fit(double a, double b, double smin, double smax, int r, double *tau_out, double *q_out) {
+double expsum_fit_r(FitTarget tg, double a, double b, double smin, double smax, int r, double *tau_out,
+                    double *q_out) {
   std::vector<double> theta(r), tb(r), qb(r);
   const double rho = smax / smin;
   for (int k = 0; k < r; ++k)
     theta[k] = std::exp(std::log(0.05 / rho) + (std::log(20.0) - std::log(0.05 / rho)) * k / std::max(1, r - 1)) / smin;
-  const std::vector<double> pg = pre_weights_nnls(theta, a, b, smin, smax);
-  const double d_geo = pre_delta(theta.data(), pg.data(), r, a, b, smin, smax);
-  double best = pre_fit_from(a, b, smin, smax, r, 0.05, 20.0, tau_out, q_out);
+  const std::vector<double> pg = weights_nnls(tg, theta, a, b, smin, smax);
+  const double d_geo = sum_rel_err(tg, theta.data(), pg.data(), r, a, b, smin, smax);
+  double best = fit_from(tg, a, b, smin, smax, r, 0.05, 20.0, tau_out, q_out);
   const double starts[2][2] = {{0.5, 5.0}, {0.005, 100.0}};
   for (int t = 0; t < 2 && best > 0.5 * d_geo; ++t) {
-    const double d = pre_fit_from(a, b, smin, smax, r, starts[t][0], starts[t][1], tb.data(), qb.data());
+    const double d = fit_from(tg, a, b, smin, smax, r, starts[t][0], starts[t][1], tb.data(), qb.data());
     if (d < best) {
       best = d;
       std::copy(tb.begin(), tb.end(), tau_out);
@@ -246,6 +268,10 @@ double pre_fit(double a, double b, double smin, double smax, int r, double *tau_
     }
   }
   return best;
+}
+
+double pre_fit(double a, double b, double smin, double smax, int r, double *tau_out, double *q_out) {
+  return expsum_fit_r(FitTarget::Pre, a, b, smin, smax, r, tau_out, q_out);
 }
 
 }  // namespace tctl
@@ -483,14 +509,14 @@ void precond_sample_inputs(int N, uint64_t seed, float *X) {
   }
 }
 
-void precond_dataset(int r, int N, const float *X, int threads, float *Y, double *delta) {
+void expsum_dataset(FitTarget tg, int r, int N, const float *X, int threads, float *Y, double *delta) {
   const int O = 2 * r;
   auto work = [&](int t0) {
     std::vector<double> tau(r), q(r);
     for (int i = t0; i < N; i += threads) {
       const double a = X[i * 4 + 0], b = std::pow(10.0, (double)X[i * 4 + 1]);
       const double smin = std::exp((double)X[i * 4 + 2]), smax = std::exp((double)X[i * 4 + 3]);
-      const double d = pre_fit(a, b, smin, smax, r, tau.data(), q.data());
+      const double d = expsum_fit_r(tg, a, b, smin, smax, r, tau.data(), q.data());
       for (int k = 0; k < r; ++k) {
         Y[(size_t)i * O + k] = (float)std::log(tau[k]);
         Y[(size_t)i * O + r + k] = (float)std::log(q[k]);

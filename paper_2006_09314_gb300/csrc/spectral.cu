@@ -484,6 +484,64 @@ std::vector<double> nnls_solve(const std::vector<double> &A, int M, int K, const
   return nnls(A, M, K, b);
 }
 
+namespace {
+
+// Sinc quadrature of s^-alpha (t1, w1) and, for alpha < 1, of s^(alpha-1) (t2, w2)
+// for a target error delta of F2 = sum1 + beta s sum2 (the rule of the file header).
+void sinc_sums(double a, double b, double smin, double smax, double delta, std::vector<double> &t1,
+               std::vector<double> &w1, std::vector<double> &t2, std::vector<double> &w2) {
+  const double F2min = min_F2(a, b, smin, smax), F2lo = F2h(smin, a, b), F2hi = F2h(smax, a, b);
+  {
+    const SincRule s = sinc_rule(a, 0.5 * delta, smin, 1.0 / F2min,
+                                 0.25 * 0.5 * delta * std::tgamma(a) * F2lo * std::pow(smin, a));
+    sinc_nodes(a, s, t1, w1);
+  }
+  t2.clear();
+  w2.clear();
+  if (a < 1.0) {
+    const double g = 1.0 - a;
+    const SincRule s = sinc_rule(g, 0.5 * delta, smin, b * smax / F2hi,
+                                 0.25 * 0.5 * delta * std::tgamma(g) * F2lo * std::pow(smin, g) /
+                                     (b * smin));
+    sinc_nodes(g, s, t2, w2);
+  }
+}
+
+// measured max relative error of the sinc form of F2 on 2000 log-spaced points
+double sinc_rel_err(double a, double b, double smin, double smax, const std::vector<double> &t1,
+                    const std::vector<double> &w1, const std::vector<double> &t2,
+                    const std::vector<double> &w2) {
+  double emax = 0;
+  const int M = 2000;
+  for (int j = 0; j < M; ++j) {
+    const double s = std::exp(std::log(smin) + (std::log(smax) - std::log(smin)) * j / (M - 1));
+    double v = 0;
+    for (size_t k = 0; k < t1.size(); ++k) v += w1[k] * std::exp(-t1[k] * s);
+    if (a >= 1.0) v += b * s;
+    else {
+      double v2 = 0;
+      for (size_t k = 0; k < t2.size(); ++k) v2 += w2[k] * std::exp(-t2[k] * s);
+      v += b * s * v2;
+    }
+    const double ex = F2h(s, a, b);
+    emax = std::max(emax, std::fabs(v - ex) / ex);
+  }
+  return emax;
+}
+
+}  // namespace
+
+// Error of the sinc form with at most r terms per function: the smallest
+// target delta (on a 1.25x grid from 1e-14) whose rules fit in r terms.
+double sinc_err_at_rank(double a, double b, double smin, double smax, int r) {
+  std::vector<double> t1, w1, t2, w2;
+  for (double delta = 1e-14; delta < 0.5; delta *= 1.25) {
+    sinc_sums(a, b, smin, smax, delta, t1, w1, t2, w2);
+    if ((int)t1.size() <= r && (int)t2.size() <= r) return sinc_rel_err(a, b, smin, smax, t1, w1, t2, w2);
+  }
+  return 1.0;
+}
+
 int expsum_fit_host(double a, double b, double smin, double smax, double tol, double *t, double *w,
                     int cap, int *r, double *err) {
   const ExpFit f = fit_F2(a, b, smin, smax, tol);
@@ -532,22 +590,46 @@ void setup_spectral(Ctx &c) {
       c.expsum_used = 1;
     }
   }
+  if (c.o.expsum_src == 2) {
+    // learned operator sum: the network's op_r nodes of g = F2/s (x = s / s_min
+    // units), weights as predicted or re-solved by NNLS on those nodes (the
+    // better of the two), judged on the measured relative error of F2; the
+    // sinc quadrature with 24 terms per function is measured as the reference
+    c.sinc24_err = sinc_err_at_rank(a, b, smin, smax, 24);
+    if (a < 1.0) {
+      const int r = c.o.op_r;
+      const float xin[4] = {(float)a, (float)std::log10(b), (float)std::log(smin), (float)std::log(smax)};
+      std::vector<float> y(2 * r);
+      mlp_forward_host(r, 1, c.o.op_model, xin, y.data(), c.st);
+      const double g0 = F2h(smin, a, b) / smin;
+      std::vector<double> tt(r), wr(r);
+      for (int k = 0; k < r; ++k) {
+        tt[k] = std::exp((double)y[k]) / smin;
+        wr[k] = std::exp((double)y[r + k]) * g0;
+      }
+      const double e_raw = sum_rel_err(FitTarget::Op, tt.data(), wr.data(), r, a, b, smin, smax);
+      const std::vector<double> wn = weights_nnls(FitTarget::Op, tt, a, b, smin, smax);
+      const double e_nn = sum_rel_err(FitTarget::Op, tt.data(), wn.data(), r, a, b, smin, smax);
+      if (e_nn < e_raw) wr = wn;
+      const double e = std::min(e_raw, e_nn);
+      c.op_learned_err = e;
+      if (std::isfinite(e) && e <= c.o.op_judge) {
+        for (int k = 0; k < r; ++k) {
+          if (!(wr[k] > 0)) continue;
+          for (int m = 0; m < 3; ++m) {
+            w.push_back(wr[k]);
+            td.push_back({tt[k], m});
+          }
+        }
+        c.op_rel_err = e;
+        c.expsum_used = 2;
+      }
+    }
+  }
   if (c.expsum_used == 0) {
-    const double F2min = min_F2(a, b, smin, smax), F2lo = F2h(smin, a, b), F2hi = F2h(smax, a, b);
     std::vector<double> t1, w1, t2, w2;
-    {
-      const SincRule s = sinc_rule(a, 0.5 * delta, smin, 1.0 / F2min,
-                                   0.25 * 0.5 * delta * std::tgamma(a) * F2lo * std::pow(smin, a));
-      sinc_nodes(a, s, t1, w1);
-    }
+    sinc_sums(a, b, smin, smax, delta, t1, w1, t2, w2);
     const bool exact_linear = (a >= 1.0);
-    if (!exact_linear) {
-      const double g = 1.0 - a;
-      const SincRule s = sinc_rule(g, 0.5 * delta, smin, b * smax / F2hi,
-                                   0.25 * 0.5 * delta * std::tgamma(g) * F2lo * std::pow(smin, g) /
-                                       (b * smin));
-      sinc_nodes(g, s, t2, w2);
-    }
     for (size_t k = 0; k < t1.size(); ++k) {
       w.push_back(w1[k]);
       td.push_back({t1[k], -1});
@@ -564,23 +646,7 @@ void setup_spectral(Ctx &c) {
           td.push_back({t2[k], m});
         }
     }
-    // measured relative error of the representation on a sample of [s_min, s_max]
-    double emax = 0;
-    const int M = 2000;
-    for (int j = 0; j < M; ++j) {
-      const double s = std::exp(std::log(smin) + (std::log(smax) - std::log(smin)) * j / (M - 1));
-      double v = 0;
-      for (size_t k = 0; k < t1.size(); ++k) v += w1[k] * std::exp(-t1[k] * s);
-      if (exact_linear) v += b * s;
-      else {
-        double v2 = 0;
-        for (size_t k = 0; k < t2.size(); ++k) v2 += w2[k] * std::exp(-t2[k] * s);
-        v += b * s * v2;
-      }
-      const double ex = F2h(s, a, b);
-      emax = std::max(emax, std::fabs(v - ex) / ex);
-    }
-    c.op_rel_err = emax;
+    c.op_rel_err = sinc_rel_err(a, b, smin, smax, t1, w1, t2, w2);
   }
   c.op_terms_w = w;
   c.op_terms_t.clear();

@@ -34,6 +34,9 @@
 // Every wait is bounded; a timeout sets an error flag the host reads.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "tc_common.cuh"
 #include "tctl_internal.cuh"
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(2 * TR) split_kernel(TcOpnd o, int R, int K, i
 }
 
 struct TcgArgs {
-  int M, N, nks, nchunk, divA, divB, Mt, Nt, Mpad, Npad;
+  int M, N, nks, nchunk, kst, divA, divB, Mt, Nt, Mpad, Npad;  // kst: 16-deep k steps per CTA
   const __nv_bfloat16 *pa, *pb;
   const int *ea, *eb;
   double alpha, beta;
@@ -202,8 +205,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
   const int mt = blockIdx.x, jt = blockIdx.y;
   const int b = blockIdx.z / a.nchunk, ch = blockIdx.z % a.nchunk;
   const int ia = b / a.divA, ib = b / a.divB;
-  const int ks0 = ch * (KCHUNK / BK);
-  const int nst = min(a.nks, ks0 + KCHUNK / BK) - ks0;
+  const int ks0 = ch * a.kst;
+  const int nst = min(a.nks, ks0 + a.kst) - ks0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
@@ -419,6 +422,119 @@ void operand_planes(Ctx &c, const TcOpnd &o, int R, int K, int items, int Rpad, 
   split_operand<D, TR>(c, o, R, K, items, Rpad, nks, e, planes);
 }
 
+// ---------------------------------------------------------------- tile autotuner
+// The contracted length a CTA takes (kst 16-deep k steps: 64, 128 or 256 k)
+// trades CTAs (parallelism of a sub-wave grid) against partial sums and the
+// pipeline fill of short chunks. The first GEMM of each shape class, keyed by
+// (digits, k steps, tile count bucket), times every candidate on the calling
+// context's stream (CUDA events, best of two launches each, writing partial
+// sums to scratch) and keeps the fastest for the process; later GEMMs of the
+// class use the table. opts.tune = 0 keeps the fixed 256-deep chunks.
+struct TuneEntry {
+  int D, nks, tiles_log2;
+  int kst;
+  float ms[3];
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+constexpr int kTuneKst[3] = {4, 8, 16};
+
+int tiles_bucket(long long tiles) {
+  int b = 0;
+  while ((1ll << (b + 1)) <= tiles && b < 30) ++b;
+  return b;
+}
+
+template <int D, int NST>
+int tcg_choose_kst(Ctx &c, int Mt, int Nt, int nks, int batch, int M, int N, const __nv_bfloat16 *pa,
+                   const __nv_bfloat16 *pb, const int *ea, const int *eb, int Mpad, int Npad) {
+  const int kfixed = KCHUNK / BK;
+  if (!c.o.tune) return kfixed;
+  const long long tiles = (long long)Mt * Nt * batch;
+  const int tb = tiles_bucket(tiles);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneEntry &t : g_tune)
+      if (t.D == D && t.nks == nks && t.tiles_log2 == tb) return t.kst;
+  }
+  // time the candidates on this GEMM's own planes (results go to scratch partials)
+  TuneEntry te{D, nks, tb, kfixed, {0, 0, 0}};
+  size_t mk = c.ws.mark();
+  double *part = c.ws.dbl((size_t)batch * ((nks + 3) / 4) * M * N);
+  if (!c.tcg_err) {
+    c.tcg_err = reinterpret_cast<int *>(c.dmalloc(1));
+    TCTL_CUDA(cudaMemsetAsync(c.tcg_err, 0, sizeof(int), c.st));
+  }
+  cudaEvent_t e0, e1;
+  TCTL_CUDA(cudaEventCreate(&e0));
+  TCTL_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int ci = 0; ci < 3; ++ci) {
+    const int kst = kTuneKst[ci];
+    const int nchunk = (nks + kst - 1) / kst;
+    if ((long long)batch * nchunk > 65535) {
+      te.ms[ci] = -1;
+      continue;
+    }
+    TcgArgs ar{};
+    ar.M = M;
+    ar.N = N;
+    ar.nks = nks;
+    ar.nchunk = nchunk;
+    ar.kst = kst;
+    ar.divA = 1;
+    ar.divB = 1;
+    ar.Mt = Mt;
+    ar.Nt = Nt;
+    ar.Mpad = Mpad;
+    ar.Npad = Npad;
+    ar.pa = pa;
+    ar.pb = pb;
+    ar.ea = ea;
+    ar.eb = eb;
+    ar.alpha = 1.0;
+    ar.beta = 0.0;
+    ar.C = part;  // only written when nchunk == 1: contiguous M x N x batch
+    ar.cm0 = 1;
+    ar.cm1 = 0;
+    ar.cd = 1 << 30;
+    ar.cj = M;
+    ar.cb = (long long)M * N;
+    ar.part = part;
+    ar.err = c.tcg_err;
+    ar.withhold = 0;
+    ar.wait_ns = kWaitNs;
+    dim3 grid(Mt, Nt, batch * nchunk);
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      TCTL_CUDA(cudaEventRecord(e0, c.st));
+      tcg_kernel<D, NST><<<grid, NTHREADS, tcg_smem<D, NST>(), c.st>>>(ar);
+      TCTL_CUDA(cudaGetLastError());
+      c.launches++;
+      TCTL_CUDA(cudaEventRecord(e1, c.st));
+      TCTL_CUDA(cudaEventSynchronize(e1));
+      float t = 0;
+      TCTL_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      ms = std::min(ms, t);
+    }
+    // the partial sums' reduction, charged at its algorithmic bytes over the HBM rate
+    if (nchunk > 1) ms += 0.004f + (float)(8.0 * (nchunk + 1) * (double)M * N * batch / 6.0e9);
+    te.ms[ci] = ms;
+    if (ms < best) {
+      best = ms;
+      te.kst = kst;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c.ws.reset(mk);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const TuneEntry &t : g_tune)
+    if (t.D == D && t.nks == nks && t.tiles_log2 == tb) return t.kst;  // another thread's result
+  g_tune.push_back(te);
+  return te.kst;
+}
+
 template <int D, int NST>
 void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double alpha,
              const TcOpnd &A, const TcOpnd &B, double beta, double *C, long long cm0, long long cm1,
@@ -426,27 +542,29 @@ void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double 
   const int Mt = (M + TM - 1) / TM, Nt = (N + TN - 1) / TN;
   const int Mpad = Mt * TM, Npad = Nt * TN;
   const int nks = (K + BK - 1) / BK;
-  const int nchunk = (nks * BK + KCHUNK - 1) / KCHUNK;
   const int itemsA = (batch - 1) / divA + 1, itemsB = (batch - 1) / divB + 1;
   size_t mk = c.ws.mark();
   int *ea = nullptr, *eb = nullptr;
   __nv_bfloat16 *pa = nullptr, *pb = nullptr;
   operand_planes<D, TM>(c, A, M, K, itemsA, Mpad, nks, ea, pa);
   operand_planes<D, TN>(c, B, N, K, itemsB, Npad, nks, eb, pb);
+  // the attribute belongs to the function; a function-local static is set once, thread-safely
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      tcg_kernel<D, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg_smem<D, NST>());
+  TCTL_CUDA(attr);
+  const int kst = tcg_choose_kst<D, NST>(c, Mt, Nt, nks, batch, M, N, pa, pb, ea, eb, Mpad, Npad);
+  const int nchunk = (nks + kst - 1) / kst;
   double *part = nchunk > 1 ? c.ws.dbl((size_t)batch * nchunk * M * N) : nullptr;
   if (!c.tcg_err) {
     c.tcg_err = reinterpret_cast<int *>(c.dmalloc(1));
     TCTL_CUDA(cudaMemsetAsync(c.tcg_err, 0, sizeof(int), c.st));
   }
-  // the attribute belongs to the function; a function-local static is set once, thread-safely
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      tcg_kernel<D, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg_smem<D, NST>());
-  TCTL_CUDA(attr);
   TcgArgs ar;
   ar.M = M;
   ar.N = N;
   ar.nks = nks;
   ar.nchunk = nchunk;
+  ar.kst = kst;
   ar.divA = divA;
   ar.divB = divB;
   ar.Mt = Mt;
@@ -496,7 +614,7 @@ void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double 
 bool gemm_tc_fits(int M, int N, int K, int batch) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return false;
   const int Mt = (M + TM - 1) / TM, Nt = (N + TN - 1) / TN, nks = (K + BK - 1) / BK;
-  const int nchunk = (nks * BK + KCHUNK - 1) / KCHUNK;
+  const int nchunk = (nks + kTuneKst[0] - 1) / kTuneKst[0];  // the finest candidate chunking
   if (Nt > 65535 || (long long)batch * nchunk > 65535 || Mt > 65535) return false;
   // enough work to pay for the digit split, and tiles not mostly padding
   const double flops = 2.0 * M * (double)N * K * batch;
@@ -563,6 +681,21 @@ void gemm_tc_kr(Ctx &c, int digits, int k, int ra, int rb, int n, double alpha, 
   const TcOpnd kr{X, (long long)ldx, (long long)ldy, 1ll, 0, ra, Y};
   const TcOpnd opB{B, (long long)ldb, 0ll, 1ll, 0, 1 << 30};
   gemm_tc(c, digits, m, n, k, 1, 1, 1, alpha, kr, opB, beta, C, 1, 0, 1 << 30, ldc, 0);
+}
+
+std::string tune_report() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string js = "[";
+  for (size_t i = 0; i < g_tune.size(); ++i) {
+    const TuneEntry &t = g_tune[i];
+    char b[256];
+    std::snprintf(b, sizeof(b),
+                  "%s{\"digits\": %d, \"k_steps\": %d, \"tiles_log2\": %d, \"k_per_cta\": %d, "
+                  "\"ms\": [%.5f, %.5f, %.5f]}",
+                  i ? ", " : "", t.D, t.nks, t.tiles_log2, t.kst * BK, t.ms[0], t.ms[1], t.ms[2]);
+    js += b;
+  }
+  return js + "]";
 }
 
 bool tcg_timed_out(Ctx &c) {

@@ -94,7 +94,9 @@ struct Ctx {
   double s_min = 0, s_max = 0;
   Sep op, pre;
   double op_rel_err = 0;
-  int expsum_used = 0;                     // 0 sinc, 1 fitted
+  int expsum_used = 0;                     // 0 sinc, 1 fitted, 2 learned
+  double op_learned_err = 0;               // expsum_src 2: the learned sum's measured error
+  double sinc24_err = 0;                   // expsum_src 2: sinc with 24 terms per function
   Sep state;                               // A^-alpha (state equation), built on first use
   double state_rel_err = 0;
   int pre_used = 0;                        // preconditioner: 0 K-node NNLS, 1 fitted, 2 learned, 3 anisotropic
@@ -254,6 +256,8 @@ void gemm_tc_cm(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, doubl
 void tcg_check(Ctx &c);
 // Reads and clears the wait-timeout flag without raising (synchronizes).
 bool tcg_timed_out(Ctx &c);
+// JSON list of the tile autotuner's decisions so far (process-wide).
+std::string tune_report();
 
 // ------------------------------------------------------------ linalg.cu
 // C = alpha op(A) op(B) + beta C, column-major, batched with element strides;
@@ -324,8 +328,23 @@ void setup_eigs(Ctx &c);
 // ------------------------------------------------------------ spectral.cu
 int expsum_fit_host(double a, double b, double smin, double smax, double tol, double *t, double *w,
                     int cap, int *r, double *err);
+double sinc_err_at_rank(double a, double b, double smin, double smax, int r);
 // ------------------------------------------------------------ learned.cu
 constexpr int kMlpIn = 4, kMlpH = 64, kPreRMax = 32;
+// What an r-term exponential sum sum_k w_k exp(-t_k s) approximates: the
+// preconditioner's h(s) = 1 / (s F2(s)) (P = s sum) or the operator's
+// g(s) = F2(s) / s (F2 = s sum).
+enum class FitTarget { Pre, Op };
+// Levenberg-Marquardt r-term fit (free log-nodes and log-weights); tau in
+// x = s / s_min units, q the weights of exp(-tau x) for target(s_min x) /
+// target(s_min). Returns the measured max |sum / target - 1|.
+double expsum_fit_r(FitTarget tg, double a, double b, double smin, double smax, int r, double *tau_out,
+                    double *q_out);
+double sum_rel_err(FitTarget tg, const double *t, const double *w, int r, double a, double b,
+                   double smin, double smax);
+std::vector<double> weights_nnls(FitTarget tg, const std::vector<double> &theta, double a, double b,
+                                 double smin, double smax);
+void expsum_dataset(FitTarget tg, int r, int N, const float *X, int threads, float *Y, double *delta);
 double pre_fit(double a, double b, double smin, double smax, int r, double *tau_out, double *q_out);
 double pre_delta(const double *theta, const double *p, int r, double a, double b, double smin,
                  double smax);
@@ -333,7 +352,7 @@ std::vector<double> pre_weights_nnls(const std::vector<double> &theta, double a,
                                      double smin, double smax);
 int mlp_param_count(int O);
 void precond_sample_inputs(int N, uint64_t seed, float *X);
-void precond_dataset(int r, int N, const float *X, int threads, float *Y, double *delta);
+
 void mlp_train(int r, int N, const float *X, const float *Y, int steps, int B, float lr,
                uint64_t seed, float *model, float *loss_out);
 void mlp_grad_host(int r, int B, const float *params, const float *X, const float *T, float *grad,

@@ -38,6 +38,7 @@ EXPORTED = [
     "tctl_expsum_fit", "tctl_gemm", "tctl_gemm_kr", "tctl_precond_fit", "tctl_precond_dataset",
     "tctl_mlp_model_size", "tctl_mlp_train", "tctl_mlp_grad", "tctl_mlp_forward",
     "tctl_apply_state", "tctl_map_constants", "tctl_solve_batch", "tctl_inject_wait_timeout",
+    "tctl_expsum_dataset", "tctl_tune_report",
 ]
 
 ERRORS = {0: "OK", -1: "E_ARG", -2: "E_COEFF", -3: "E_CUDA", -4: "E_NOMEM",
@@ -72,7 +73,8 @@ class Opts(ctypes.Structure):
                 ("seed", ctypes.c_ulonglong), ("range_tol", ctypes.c_double),
                 ("tc_gemm", ctypes.c_int), ("pre_src", ctypes.c_int), ("pre_r", ctypes.c_int),
                 ("pre_model", ctypes.c_void_p), ("pre_delta_max", ctypes.c_double),
-                ("workspace_mb", ctypes.c_int)]
+                ("workspace_mb", ctypes.c_int), ("op_model", ctypes.c_void_p),
+                ("op_r", ctypes.c_int), ("op_judge", ctypes.c_double), ("tune", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -84,7 +86,8 @@ class Stats(ctypes.Structure):
                 ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
                 ("expsum_used", ctypes.c_int), ("pre_used", ctypes.c_int),
                 ("pre_delta", ctypes.c_double), ("ws_peak_mb", ctypes.c_double),
-                ("ws_size_mb", ctypes.c_double)]
+                ("ws_size_mb", ctypes.c_double), ("op_learned_err", ctypes.c_double),
+                ("sinc24_err", ctypes.c_double)]
 
     def as_dict(self):
         out = {}
@@ -139,6 +142,7 @@ def load(build_if_missing: bool = True):
         "tctl_gemm_kr": (I, [P, I, I, I, I, I, D, P, I, P, I, P, I, D, P, I]),
         "tctl_precond_fit": (I, [D, D, D, D, I, P, P, P]),
         "tctl_precond_dataset": (I, [I, I, ctypes.c_ulonglong, I, P, P, P]),
+        "tctl_expsum_dataset": (I, [I, I, I, ctypes.c_ulonglong, I, P, P, P]),
         "tctl_mlp_model_size": (I, [I]),
         "tctl_mlp_train": (I, [I, I, P, P, I, I, ctypes.c_float, ctypes.c_ulonglong, P, P]),
         "tctl_mlp_grad": (I, [I, I, P, P, P, P, P]),
@@ -147,6 +151,7 @@ def load(build_if_missing: bool = True):
         "tctl_map_constants": (I, [D, D, P, P]),
         "tctl_solve_batch": (I, [P, I, D, P, I]),
         "tctl_inject_wait_timeout": (I, [P, I]),
+        "tctl_tune_report": (I, [ctypes.c_char_p, I]),
         "tctl_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -441,6 +446,19 @@ def tctl_precond_dataset(r, n, seed=1, threads=None):
     return X, Y, d
 
 
+def tctl_expsum_dataset(which, r, n, seed=1, threads=None):
+    """which 0 (operator g = F2/s) or 1 (preconditioner): (X (n, 4), Y (n, 2r), err (n))."""
+    import os
+    import numpy as np
+    threads = threads or len(os.sched_getaffinity(0))
+    X = np.zeros((n, 4), np.float32)
+    Y = np.zeros((n, 2 * r), np.float32)
+    e = np.zeros(n)
+    _check(load().tctl_expsum_dataset(int(which), r, n, seed, threads, X.ctypes.data, Y.ctypes.data,
+                                      e.ctypes.data))
+    return X, Y, e
+
+
 def tctl_mlp_train(r, X, Y, steps=3000, batch=256, lr=2e-3, seed=1):
     """Train the 4 -> 64 -> 64 -> 2r network on the GPU: (model float32 array, loss[2])."""
     import numpy as np
@@ -532,6 +550,14 @@ def tctl_eig1d_noalloc(coeffs_dev, n, lam_dev, V_dev, paper_end_rows=0, stream=N
 def tctl_inject_wait_timeout(ctx, count=1):
     """The next `count` tensor-core GEMM launches of ctx starve a bounded wait (test hook)."""
     _check(load().tctl_inject_wait_timeout(ctx, int(count)), ctx)
+
+
+def tctl_tune_report():
+    """The tile autotuner's decisions so far (list of dicts)."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().tctl_tune_report(buf, len(buf)))
+    return json.loads(buf.value.decode())
 
 
 def tctl_destroy(ctx):

@@ -1,6 +1,7 @@
-"""Host logic of bench.py that runs without a GPU: the oracle-error status of
-the method variants (bound from the main solve, direct oracle check of the
-learned form's open cases, and a failed check leaving only the bound)."""
+"""Host logic of bench.py that runs without a GPU: the oracle errors of several
+solutions in one pass, the oracle-error status of the method variants (direct
+errors, else the bound from the main solve), the reference arm's line and the
+roofline of a traced solve."""
 import numpy as np
 import pytest
 
@@ -33,33 +34,31 @@ def pool():
     p.close()
 
 
-def test_verify_variants_bound_and_direct_check(pool):
-    probs = [make_problem(8, 0.5, 1e-2, 2, s) for s in (3, 4)]
-    sols = [_exact_cp(p) for p in probs]
+def test_oracle_errors_of_several_solutions_in_one_pass(pool):
+    """bench.oracle_errors: the exact solution has error ~0, a 1% scaled one 0.01."""
+    p = make_problem(8, 0.5, 1e-2, 2, 5)
+    w, U = _exact_cp(p)
+    e = bench.oracle_errors(p, [(w, U), (1.01 * w, U)], pool)
+    assert e[0] < 1e-12 and abs(e[1] - 0.01) < 1e-9
+
+
+def test_verify_variants_direct_errors_and_bound():
     errs = [5e-7, 5e-7]
     variants = {"learned_pre": {"rel_diff_to_main": [2e-6, 1e-7], "solves_per_s": 10.0},
-                "fp64_sinc": {"rel_diff_to_main": [1e-7, 7e-7], "solves_per_s": 4.0}}
-    bench.verify_variants(variants, {"learned_pre": sols}, errs, probs, pool)
-    lp, sc = variants["learned_pre"], variants["fp64_sinc"]
-    assert list(lp["rel_err_vs_oracle_direct"]) == ["0"]          # only the open case
-    assert lp["rel_err_vs_oracle_direct"]["0"] < 1e-12            # exact solution
-    assert lp["verified_le_1e-6"] == 2 and lp["verified_solves_per_s"] == 10.0
-    assert sc["verified_le_1e-6"] == 1 and sc["verified_solves_per_s"] == 2.0
-    assert "rel_err_vs_oracle_direct" not in sc                   # bound only
-
-
-def test_verify_variants_wrong_solution_and_failed_check(pool):
-    probs = [make_problem(8, 0.5, 1e-2, 2, 5)]
-    w, U = _exact_cp(probs[0])
-    wrong = (1.01 * w, U)                                         # 1% off
-    v = {"learned_pre": {"rel_diff_to_main": [3e-6], "solves_per_s": 1.0}}
-    bench.verify_variants(v, {"learned_pre": [wrong]}, [5e-7], probs, pool)
-    assert abs(v["learned_pre"]["rel_err_vs_oracle_direct"]["0"] - 0.01) < 1e-9
-    assert v["learned_pre"]["verified_le_1e-6"] == 0
-    v = {"learned_pre": {"rel_diff_to_main": [3e-6], "solves_per_s": 1.0}}
-    bench.verify_variants(v, {"learned_pre": [None]}, [5e-7], probs, pool)
-    assert "direct_check_failed" in v["learned_pre"]
-    assert v["learned_pre"]["verified_le_1e-6"] == 0
+                "fp64_sinc": {"rel_diff_to_main": [1e-7, 7e-7], "solves_per_s": 4.0},
+                "aniso_pre": {"rel_diff_to_main": [1e-7, 1e-7], "solves_per_s": 2.0},
+                "learned_operator": {"accepted": 0}}
+    direct = {"learned_pre": [8e-7, 2e-6], "fp64_sinc": [3e-7, None]}
+    bench.verify_variants(variants, direct, errs)
+    lp, sc, an = variants["learned_pre"], variants["fp64_sinc"], variants["aniso_pre"]
+    # direct errors decide, whatever the distance to the main solve says
+    assert lp["rel_err_vs_oracle"] == [8e-7, 2e-6] and "err_bound_vs_oracle" not in lp
+    assert lp["verified_le_1e-6"] == 1 and lp["verified_solves_per_s"] == 5.0
+    # an incomplete direct check leaves the bound: main error + distance
+    assert sc["err_bound_vs_oracle"] == pytest.approx([6e-7, 1.2e-6])
+    assert sc["verified_le_1e-6"] == 1
+    assert an["verified_le_1e-6"] == 2 and an["verified_solves_per_s"] == 2.0
+    assert "verified_le_1e-6" not in variants["learned_operator"]
 
 
 def test_reference_arm_prints_the_contract_line():

@@ -136,3 +136,26 @@ def test_gemm_kr_fp64_path_and_errors(ctx):
     assert lib.tctl_gemm_kr(ctx.handle, 5, 4, 2, 2, 4, 1.0, None, 4, None, 4, None, 4, 0.0, None, 4) == -1
     assert lib.tctl_gemm_kr(ctx.handle, 6, 4, 2, 2, 4, 1.0, X.data_ptr(), 2, Y.data_ptr(), 4,
                             B.data_ptr(), 4, 0.0, C.data_ptr(), 4) == -1
+
+
+def test_autotuned_chunks_keep_the_error_bound():
+    """The tile autotuner (opts.tune, default on) picks the contracted length per CTA
+    of each shape class by timing 64, 128 and 256; every choice keeps the digit
+    split's error bound and gives the fixed-chunk (tune = 0) result to within it."""
+    pr = make_problem(16, 0.5, 1e-2, 1, 1)
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((700, 2048))
+    B = rng.standard_normal((2048, 60))
+    out = []
+    for tune in (1, 0):
+        with T.Context(pr.coeffs, 16, 0.5, 1e-2, 1e-6, opts=T.tctl_default_opts(tune=tune)) as c:
+            out.append(c.gemm(6, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy())
+    bound = _bound(A, B, 6, False, False)
+    ref = A @ B
+    for C in out:
+        assert np.all(np.abs(C - ref) <= bound)
+    assert np.all(np.abs(out[0] - out[1]) <= 2 * bound)
+    table = T.tctl_tune_report()
+    assert table and all(t["k_per_cta"] in (64, 128, 256) for t in table)
+    mine = [t for t in table if t["digits"] == 6 and t["k_steps"] == 128]
+    assert mine and all(len(t["ms"]) == 3 and min(x for x in t["ms"] if x > 0) > 0 for t in mine)
