@@ -67,8 +67,8 @@ def parse():
                     help="run only the full-grid mode-product measurement")
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the rank-structured solves at n = 256, 512, 1024")
-    ap.add_argument("--no-tune", action="store_true",
-                    help="--single only: fixed tensor-core GEMM chunks instead of the autotuner")
+    ap.add_argument("--tune", action="store_true",
+                    help="--single only: the tensor-core GEMM autotuner instead of fixed chunks")
     ap.add_argument("--single", action="store_true",
                     help="one context and one solve per step (alpha = 0.5, beta = 1e-2), for "
                          "profiler captures: one problem's memory, no checks")
@@ -868,7 +868,7 @@ def single_arm(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     p = make_problem(args.n, ALPHA, BETA, RANK, problem_seed(CONFIG_ID, 4))
     st = torch.cuda.Stream()
-    opts = T.tctl_default_opts(tune=0 if args.no_tune else 1)
+    opts = T.tctl_default_opts(tune=1 if args.tune else 0)
     with torch.cuda.stream(st), T.Context(p.coeffs, args.n, p.alpha, p.beta, EPS, opts=opts,
                                           stream=st.cuda_stream) as ctx:
         b = T.CP.from_numpy(p.yw, p.yU)

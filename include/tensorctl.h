@@ -114,10 +114,11 @@ typedef struct {
                          (at op_tol) is used; alpha = 1 always uses sinc          */
   int op_r;           /* terms of the learned operator sum (default 16)              */
   double op_judge;    /* acceptance bound of the learned operator sum (default 1e-7)  */
-  int tune;           /* 1 = tile autotuner for the tensor-core GEMMs (default): the
-                         contracted length per CTA (64, 128 or 256) of each shape
-                         class is timed at its first use and kept for the process;
-                         0 = fixed 256                                                 */
+  int tune;           /* 1 = tile autotuner for the tensor-core GEMMs: the contracted
+                         length per CTA (64, 128 or 256) of each shape class is timed
+                         at its first use and kept for the process; 0 = fixed 256
+                         (default: timed while other contexts share the GPU, the
+                         choices were measured to slow the concurrent solves)         */
 } tctl_opts;
 
 typedef struct {

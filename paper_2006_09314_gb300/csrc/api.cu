@@ -238,7 +238,7 @@ int tctl_default_opts(tctl_opts *o) {
   o->op_model = nullptr;
   o->op_r = 16;
   o->op_judge = 1e-7;
-  o->tune = 1;
+  o->tune = 0;
   return TCTL_OK;
 }
 

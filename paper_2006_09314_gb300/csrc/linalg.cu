@@ -54,6 +54,14 @@ cudaEvent_t Ctx::prof_event() {
 
 // ------------------------------------------------------------------ GEMM
 constexpr int GEMM_BK = 16;
+// CTAs a split-K FP64 GEMM aims at (the contracted dimension is split until the
+// grid has about this many): two per SM fill the GPU for one solve alone; with
+// many solves on concurrent streams fewer, longer CTAs spend less time in
+// per-CTA prologues, partial-sum writes and reductions.
+#ifndef TCTL_SPLIT_TARGET
+#define TCTL_SPLIT_TARGET (2 * 152)
+#endif
+constexpr int kSplitTarget = TCTL_SPLIT_TARGET;
 
 template <int BM, int BN, bool TA, bool TB>
 __global__ void __launch_bounds__(256)
@@ -276,7 +284,7 @@ static void gemm_skinny(Ctx &c, bool ta, bool tb, int m, int n, int k, double al
   const int NC = n <= 1 ? 1 : n <= 4 ? 4 : n <= 8 ? 8 : 16;
   const int rows_per_block = ta ? 8 * (NC >= 8 ? 2 : 4) : 256;
   const int rowblocks = (m + rows_per_block - 1) / rows_per_block;
-  int splits = std::max(1, std::min((2 * 152 + rowblocks - 1) / rowblocks, (k + 63) / 64));
+  int splits = std::max(1, std::min((kSplitTarget + rowblocks - 1) / rowblocks, (k + 63) / 64));
   splits = std::min(splits, 256);
   const int kchunk = (k + splits - 1) / splits;
   splits = (k + kchunk - 1) / kchunk;
@@ -333,7 +341,7 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
   const int gx = (m + BM - 1) / BM, gy = (n + BN - 1) / BN;
   const long long tiles = (long long)gx * gy * batch;
   int splits = 1;
-  const int target = 2 * 152;
+  const int target = kSplitTarget;
   if (tiles < target && k >= 4 * GEMM_BK) {
     // tall-skinny products (Gram matrices, projections with K = n): split K so that
     // about two CTAs per SM run; chunks down to one 16-deep tile.
@@ -564,7 +572,7 @@ void gemm_group(Ctx &c, int count, const GemmSpec *spec) {
       const int tiles = it.gx * ((q.n + 31) / 32);
       // the group as a whole aims at about two CTAs per SM; a CTA contracts at
       // least 4 k-steps of 16, so its fixed costs stay small against its work
-      const int target = (2 * 152 + g.count - 1) / g.count;
+      const int target = (kSplitTarget + g.count - 1) / g.count;
       int splits = 1;
       if (tiles < target && q.k >= 8 * GEMM_BK)
         splits = std::min((target + tiles - 1) / tiles, q.k / (4 * GEMM_BK));

@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -85,9 +86,9 @@ __device__ __forceinline__ int exp_code(double v) {
   return e + E_BIAS;
 }
 
-__global__ void row_exp_kernel(TcOpnd o, int R, int K, int Rpad, int *__restrict__ e_out) {
-  const int item = blockIdx.z;
-  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * RE_K;
+__device__ __forceinline__ void row_exp_body(const TcOpnd &o, int R, int K, int Rpad,
+                                             int *__restrict__ e_out, int bx, int by, int item) {
+  const int r0 = bx * 32, k0 = by * RE_K;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 8 warps
   const bool kr = o.q != nullptr;
   const int kend = min(K, k0 + RE_K);
@@ -121,13 +122,17 @@ __global__ void row_exp_kernel(TcOpnd o, int R, int K, int Rpad, int *__restrict
   }
 }
 
+__global__ void row_exp_kernel(TcOpnd o, int R, int K, int Rpad, int *__restrict__ e_out) {
+  row_exp_body(o, R, K, Rpad, e_out, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // Digit planes of one (row tile, 16-k slice) block: 2 TR threads, each cuts the
 // D digits of 8 consecutive k of one row (one 16-byte core-matrix row per plane).
 template <int D, int TR>
-__global__ void __launch_bounds__(2 * TR) split_kernel(TcOpnd o, int R, int K, int Rpad, int nks,
-                                                       const int *__restrict__ e_in,
-                                                       __nv_bfloat16 *__restrict__ planes) {
-  const int rt = blockIdx.x, ks = blockIdx.y, item = blockIdx.z;
+__device__ __forceinline__ void split_body(const TcOpnd &o, int R, int K, int Rpad, int nks,
+                                           const int *__restrict__ e_in,
+                                           __nv_bfloat16 *__restrict__ planes, int rt, int ks,
+                                           int item) {
   const int t = threadIdx.x;
   int rl, kh;
   if (o.sk == 1) {
@@ -173,6 +178,45 @@ __global__ void __launch_bounds__(2 * TR) split_kernel(TcOpnd o, int R, int K, i
     *reinterpret_cast<uint4 *>(blk + p * (TR * BK) + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
+template <int D, int TR>
+__global__ void __launch_bounds__(2 * TR) split_kernel(TcOpnd o, int R, int K, int Rpad, int nks,
+                                                       const int *__restrict__ e_in,
+                                                       __nv_bfloat16 *__restrict__ planes) {
+  split_body<D, TR>(o, R, K, Rpad, nks, e_in, planes, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Several operands' exponents / digit planes in one launch: operand i owns the
+// blocks [b0[i], b0[i + 1]) of a one-dimensional grid, in (x, y) order.
+constexpr int kSplitGroupMax = 4;
+struct SplitItem {
+  TcOpnd o;
+  int R, K, Rpad, nks;
+  int *e;
+  __nv_bfloat16 *planes;
+};
+struct SplitGroup {
+  int count;
+  int b0[kSplitGroupMax + 1];
+  SplitItem it[kSplitGroupMax];
+};
+
+__global__ void row_exp_group_kernel(SplitGroup g) {
+  int i = 0;
+  while (i + 1 < g.count && (int)blockIdx.x >= g.b0[i + 1]) ++i;
+  const SplitItem &q = g.it[i];
+  const int local = blockIdx.x - g.b0[i], gx = (q.R + 31) / 32;
+  row_exp_body(q.o, q.R, q.K, q.Rpad, q.e, local % gx, local / gx, 0);
+}
+
+template <int D, int TR>
+__global__ void __launch_bounds__(2 * TR) split_group_kernel(SplitGroup g) {
+  int i = 0;
+  while (i + 1 < g.count && (int)blockIdx.x >= g.b0[i + 1]) ++i;
+  const SplitItem &q = g.it[i];
+  const int local = blockIdx.x - g.b0[i], gx = q.Rpad / TR;
+  split_body<D, TR>(q.o, q.R, q.K, q.Rpad, q.nks, q.e, q.planes, local % gx, local / gx, 0);
+}
+
 struct TcgArgs {
   int M, N, nks, nchunk, kst, divA, divB, Mt, Nt, Mpad, Npad;  // kst: 16-deep k steps per CTA
   const __nv_bfloat16 *pa, *pb;
@@ -189,8 +233,9 @@ struct TcgArgs {
   unsigned long long wait_ns;
 };
 
+// One CTA of a digit-split GEMM: output tile (mt, jt) of batch item / K chunk bz.
 template <int D, int NST>
-__global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
+__device__ __forceinline__ void tcg_body(const TcgArgs &a, int mt, int jt, int bz) {
   constexpr int PA = TM * BK, PB = TN * BK;          // elements of one digit plane
   constexpr int A_BYTES = D * PA * 2, B_BYTES = D * PB * 2, STAGE = A_BYTES + B_BYTES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -202,8 +247,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done_bar + 1);
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mt = blockIdx.x, jt = blockIdx.y;
-  const int b = blockIdx.z / a.nchunk, ch = blockIdx.z % a.nchunk;
+  const int b = bz / a.nchunk, ch = bz % a.nchunk;
   const int ia = b / a.divA, ib = b / a.divB;
   const int ks0 = ch * a.kst;
   const int nst = min(a.nks, ks0 + a.kst) - ks0;
@@ -357,6 +401,30 @@ __global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+template <int D, int NST>
+__global__ void __launch_bounds__(NTHREADS, 2) tcg_kernel(TcgArgs a) {
+  tcg_body<D, NST>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Several independent digit-split GEMMs in one launch: item i owns the CTAs
+// [cta0[i], cta0[i + 1]) of a one-dimensional grid, in (mt, jt, bz) order.
+constexpr int kTcgGroupMax = 4;
+struct TcgGroup {
+  int count;
+  int cta0[kTcgGroupMax + 1];
+  TcgArgs it[kTcgGroupMax];
+};
+
+template <int D, int NST>
+__global__ void __launch_bounds__(NTHREADS, 2) tcg_group_kernel(TcgGroup g) {
+  int item = 0;
+  while (item + 1 < g.count && (int)blockIdx.x >= g.cta0[item + 1]) ++item;
+  const TcgArgs &a = g.it[item];
+  const int local = blockIdx.x - g.cta0[item];
+  const int mt = local % a.Mt, rest = local / a.Mt;
+  tcg_body<D, NST>(a, mt, rest % a.Nt, rest / a.Nt);
+}
+
 __global__ void tcg_reduce_kernel(int M, int N, int batch, int nchunk, const double *__restrict__ part,
                                   double alpha, double beta, double *C, long long cm0, long long cm1,
                                   int cd, long long cj, long long cb) {
@@ -372,6 +440,34 @@ __global__ void tcg_reduce_kernel(int M, int N, int batch, int nchunk, const dou
     double *out = C + (long long)b * cb + (long long)(m % cd) * cm0 + (long long)(m / cd) * cm1 +
                   (long long)j * cj;
     *out = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *out);
+  }
+}
+
+// the partial sums of the items of a group with K chunks (nchunk > 1)
+struct TcgRedGroup {
+  int count;
+  long long out0[kTcgGroupMax + 1];
+  const TcgArgs *dummy;
+  TcgArgs it[kTcgGroupMax];
+};
+
+__global__ void tcg_reduce_group_kernel(TcgRedGroup g) {
+  const long long total = g.out0[g.count];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int item = 0;
+    while (item + 1 < g.count && t >= g.out0[item + 1]) ++item;
+    const TcgArgs &a = g.it[item];
+    const long long r = t - g.out0[item];
+    const int m = (int)(r % a.M);
+    const int j = (int)((r / a.M) % a.N);
+    const int b = (int)(r / ((long long)a.M * a.N));
+    double sum = 0.0;
+#pragma unroll 8
+    for (int ch = 0; ch < a.nchunk; ++ch) sum += a.part[((long long)(b * a.nchunk + ch) * a.N + j) * a.M + m];
+    double *out = a.C + (long long)b * a.cb + (long long)(m % a.cd) * a.cm0 + (long long)(m / a.cd) * a.cm1 +
+                  (long long)j * a.cj;
+    *out = (a.beta == 0.0) ? a.alpha * sum : fma(a.alpha, sum, a.beta * *out);
   }
 }
 
@@ -609,7 +705,203 @@ void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double 
   c.ws.reset(mk);
 }
 
+template <int D, int NST>
+void run_tcg_group(Ctx &c, int count, const TcItem *items) {
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      tcg_group_kernel<D, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg_smem<D, NST>());
+  TCTL_CUDA(attr);
+  static const cudaError_t attr1 = cudaFuncSetAttribute(
+      tcg_kernel<D, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg_smem<D, NST>());
+  TCTL_CUDA(attr1);
+  if (!c.tcg_err) {
+    c.tcg_err = reinterpret_cast<int *>(c.dmalloc(1));
+    TCTL_CUDA(cudaMemsetAsync(c.tcg_err, 0, sizeof(int), c.st));
+  }
+  size_t mk = c.ws.mark();
+  TcgGroup g;
+  std::memset(&g, 0, sizeof(g));
+  TcgRedGroup rg;
+  std::memset(&rg, 0, sizeof(rg));
+  g.count = count;
+  int ctas = 0;
+  double flops = 0;
+  // digit planes: kept operands from the context's store (cut alone on first use),
+  // the others collected and cut together: exponents zeroed by one memset, one
+  // row-exponent launch, one split launch per tile height
+  int *ea_[kTcgGroupMax], *eb_[kTcgGroupMax];
+  __nv_bfloat16 *pa_[kTcgGroupMax], *pb_[kTcgGroupMax];
+  std::vector<SplitItem> pend[2];  // [0]: TM-row tiles (A), [1]: TN-row tiles (B)
+  auto prep = [&](const TcOpnd &o, int R, int K, int Rpad, int nks, bool isA, int *&e,
+                  __nv_bfloat16 *&pl) {
+    if (o.keep && !o.q) {
+      if (isA) operand_planes<D, TM>(c, o, R, K, 1, Rpad, nks, e, pl);
+      else operand_planes<D, TN>(c, o, R, K, 1, Rpad, nks, e, pl);
+      return;
+    }
+    const size_t nplane = (size_t)Rpad * nks * D * BK;
+    pl = reinterpret_cast<__nv_bfloat16 *>(c.ws.dbl((nplane * 2 + 7) / 8));
+    e = nullptr;  // assigned below from one zeroed block
+    pend[isA ? 0 : 1].push_back(SplitItem{o, R, K, Rpad, nks, nullptr, pl});
+  };
+  auto cut_pending = [&]() {
+    size_t etot = 0;
+    for (auto &v : pend)
+      for (const SplitItem &q : v) etot += (size_t)q.Rpad;
+    if (!etot) return;
+    int *eblk = c.ws.i32(etot);
+    TCTL_CUDA(cudaMemsetAsync(eblk, 0, sizeof(int) * etot, c.st));
+    size_t off = 0;
+    for (auto &v : pend)
+      for (SplitItem &q : v) {
+        q.e = eblk + off;
+        off += (size_t)q.Rpad;
+      }
+    // hand the exponent arrays back to the items (matched by their plane buffers)
+    for (int i = 0; i < count; ++i)
+      for (auto &v : pend)
+        for (const SplitItem &q : v) {
+          if (q.planes == pa_[i]) ea_[i] = q.e;
+          if (q.planes == pb_[i]) eb_[i] = q.e;
+        }
+    std::vector<SplitItem> all(pend[0]);
+    all.insert(all.end(), pend[1].begin(), pend[1].end());
+    for (size_t b = 0; b < all.size(); b += kSplitGroupMax) {
+      SplitGroup sg;
+      std::memset(&sg, 0, sizeof(sg));
+      int blocks = 0;
+      double bytes = 0;
+      for (size_t i = b; i < std::min(all.size(), b + kSplitGroupMax); ++i) {
+        const SplitItem &q = all[i];
+        sg.it[sg.count] = q;
+        sg.b0[sg.count] = blocks;
+        blocks += ((q.R + 31) / 32) * ((q.K + RE_K - 1) / RE_K);
+        bytes += (q.o.q ? 8.0 * q.K * ((double)q.o.d + (double)q.R / q.o.d) : 8.0 * (double)q.R * q.K) +
+                 4.0 * q.Rpad;
+        ++sg.count;
+      }
+      sg.b0[sg.count] = blocks;
+      c.next_bytes = bytes;
+      LAUNCH(c, row_exp_group_kernel, blocks, 256, 0, sg);
+    }
+    for (int h = 0; h < 2; ++h)
+      for (size_t b = 0; b < pend[h].size(); b += kSplitGroupMax) {
+        SplitGroup sg;
+        std::memset(&sg, 0, sizeof(sg));
+        int blocks = 0;
+        double bytes = 0;
+        const int TR = h == 0 ? TM : TN;
+        for (size_t i = b; i < std::min(pend[h].size(), b + kSplitGroupMax); ++i) {
+          const SplitItem &q = pend[h][i];
+          sg.it[sg.count] = q;
+          sg.b0[sg.count] = blocks;
+          blocks += (q.Rpad / TR) * q.nks;
+          bytes += (q.o.q ? 8.0 * q.K * ((double)q.o.d + (double)q.R / q.o.d) : 8.0 * (double)q.R * q.K) +
+                   4.0 * q.Rpad + 2.0 * D * (double)q.Rpad * q.nks * BK;
+          ++sg.count;
+        }
+        sg.b0[sg.count] = blocks;
+        c.next_bytes = bytes;
+        if (h == 0) LAUNCH(c, (split_group_kernel<D, TM>), blocks, 2 * TM, 0, sg);
+        else LAUNCH(c, (split_group_kernel<D, TN>), blocks, 2 * TN, 0, sg);
+      }
+  };
+  for (int i = 0; i < count; ++i) {
+    const TcItem &q = items[i];
+    const int Mt = (q.M + TM - 1) / TM, Nt = (q.N + TN - 1) / TN;
+    const int Mpad = Mt * TM, Npad = Nt * TN, nks = (q.K + BK - 1) / BK;
+    int *ea = nullptr, *eb = nullptr;
+    __nv_bfloat16 *pa = nullptr, *pb = nullptr;
+    prep(q.A, q.M, q.K, Mpad, nks, true, ea, pa);
+    prep(q.B, q.N, q.K, Npad, nks, false, eb, pb);
+    ea_[i] = ea;
+    eb_[i] = eb;
+    pa_[i] = pa;
+    pb_[i] = pb;
+  }
+  cut_pending();
+  for (int i = 0; i < count; ++i) {
+    const TcItem &q = items[i];
+    TcgArgs &ar = g.it[i];
+    const int Mt = (q.M + TM - 1) / TM, Nt = (q.N + TN - 1) / TN;
+    const int Mpad = Mt * TM, Npad = Nt * TN, nks = (q.K + BK - 1) / BK;
+    int *ea = ea_[i], *eb = eb_[i];
+    __nv_bfloat16 *pa = pa_[i], *pb = pb_[i];
+    const int kst = tcg_choose_kst<D, NST>(c, Mt, Nt, nks, 1, q.M, q.N, pa, pb, ea, eb, Mpad, Npad);
+    ar.M = q.M;
+    ar.N = q.N;
+    ar.nks = nks;
+    ar.kst = kst;
+    ar.nchunk = (nks + kst - 1) / kst;
+    ar.divA = ar.divB = 1;
+    ar.Mt = Mt;
+    ar.Nt = Nt;
+    ar.Mpad = Mpad;
+    ar.Npad = Npad;
+    ar.pa = pa;
+    ar.pb = pb;
+    ar.ea = ea;
+    ar.eb = eb;
+    ar.alpha = q.alpha;
+    ar.beta = q.beta;
+    ar.C = q.C;
+    ar.cm0 = q.cm0;
+    ar.cm1 = q.cm1;
+    ar.cd = q.cd;
+    ar.cj = q.cj;
+    ar.cb = 0;
+    ar.part = ar.nchunk > 1 ? c.ws.dbl((size_t)ar.nchunk * q.M * q.N) : nullptr;
+    ar.err = c.tcg_err;
+    ar.withhold = 0;
+    ar.wait_ns = kWaitNs;
+    if (c.withhold_copies > 0) {
+      ar.withhold = 1;
+      ar.wait_ns = 1000000ull;
+      --c.withhold_copies;
+    }
+    g.cta0[i] = ctas;
+    ctas += Mt * Nt * ar.nchunk;
+    flops += 2.0 * q.M * (double)q.N * q.K;
+  }
+  g.cta0[count] = ctas;
+  c.next_flops = flops;
+  c.next_mma = (D * (D + 1) / 2) * flops;
+  constexpr int smem_bytes = tcg_smem<D, NST>();
+  LAUNCH(c, (tcg_group_kernel<D, NST>), ctas, NTHREADS, smem_bytes, g);
+  long long outs = 0;
+  for (int i = 0; i < count; ++i)
+    if (g.it[i].nchunk > 1) {
+      rg.it[rg.count] = g.it[i];
+      rg.out0[rg.count] = outs;
+      outs += (long long)g.it[i].M * g.it[i].N;
+      ++rg.count;
+    }
+  if (rg.count > 0) {
+    rg.out0[rg.count] = outs;
+    double bytes = 0;
+    for (int i = 0; i < rg.count; ++i)
+      bytes += 8.0 * rg.it[i].M * (double)rg.it[i].N * (rg.it[i].nchunk + 1 + (rg.it[i].beta != 0.0));
+    c.next_bytes = bytes;
+    const int blocks = (int)std::min<long long>((outs + 255) / 256, 4096);
+    LAUNCH(c, tcg_reduce_group_kernel, blocks, 256, 0, rg);
+  }
+  c.ws.reset(mk);
+}
+
 }  // namespace
+
+void gemm_tc_group(Ctx &c, int digits, int count, const TcItem *items) {
+  for (int b = 0; b < count; b += kTcgGroupMax) {
+    const int cnt = std::min(kTcgGroupMax, count - b);
+    for (int i = b; i < b + cnt; ++i) {
+      const TcItem &q = items[i];
+      if (q.M <= 0 || q.N <= 0 || q.K <= 0) fail(TCTL_E_ARG, "gemm_tc_group: empty item");
+      if ((q.M + TM - 1) / TM > 65535 || (q.N + TN - 1) / TN > 65535)
+        fail(TCTL_E_ARG, "gemm_tc_group: item too large");
+    }
+    if (digits <= 4) run_tcg_group<4, 4>(c, cnt, items + b);
+    else run_tcg_group<6, 3>(c, cnt, items + b);
+  }
+}
 
 bool gemm_tc_fits(int M, int N, int K, int batch) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return false;

@@ -239,6 +239,20 @@ void gemm_tc(Ctx &c, int digits, int M, int N, int K, int batch, int divA, int d
              double alpha, const TcOpnd &A, const TcOpnd &B, double beta, double *C,
              long long cm0, long long cm1, int cd, long long cj, long long cb);
 bool gemm_tc_fits(int M, int N, int K, int batch);
+// One GEMM of a grouped tensor-core launch (no batch):
+// C[(m % cd) cm0 + (m / cd) cm1 + j cj] = alpha sum_k A(m, k) B(j, k) + beta C.
+struct TcItem {
+  int M, N, K;
+  TcOpnd A, B;
+  double alpha, beta;
+  double *C;
+  long long cm0, cm1;
+  int cd;
+  long long cj;
+};
+// Independent digit-split GEMMs in one launch (up to 4 per launch) plus one
+// grouped reduction of their K-chunk partial sums; digits as gemm_tc.
+void gemm_tc_group(Ctx &c, int digits, int count, const TcItem *items);
 // gemm() semantics; the tensor cores when opts.tc_gemm and the shape pays, FP64 otherwise
 void gemm_x(Ctx &c, int digits, bool ta, bool tb, int m, int n, int k, double alpha,
             const double *A, int lda, long long sA, const double *B, int ldb, long long sB,

@@ -532,6 +532,46 @@ static void kr_t_gemm(Ctx &c, int n, const double *X, int ldx, int ra, const dou
   c.ws.reset(mk);
 }
 
+// The same for several independent products (the three modes of one step):
+// on the tensor cores in one grouped launch when every item fits, else one by one.
+struct KrSpec {
+  const double *X;
+  int ldx, ra;
+  const double *Y;
+  int ldy, rb;
+  const double *E;
+  int lde, N;
+  double *out;
+  int ldo;
+};
+
+static void kr_t_gemm_group(Ctx &c, int n, int count, const KrSpec *sp) {
+  bool tc = c.o.tc_gemm != 0;
+  for (int i = 0; i < count && tc; ++i) {
+    const int M = sp[i].ra * sp[i].rb;
+    tc = M > 0 && sp[i].N > 0 && gemm_tc_fits(std::max(M, sp[i].N), std::min(M, sp[i].N), n, 1);
+  }
+  if (!tc) {
+    for (int i = 0; i < count; ++i)
+      kr_t_gemm(c, n, sp[i].X, sp[i].ldx, sp[i].ra, sp[i].Y, sp[i].ldy, sp[i].rb, sp[i].E, sp[i].lde,
+                sp[i].N, sp[i].out, sp[i].ldo);
+    return;
+  }
+  std::vector<TcItem> items(count);
+  for (int i = 0; i < count; ++i) {
+    const KrSpec &q = sp[i];
+    const int M = q.ra * q.rb;
+    const TcOpnd kr{q.X, (long long)q.ldx, (long long)q.ldy, 1, 0, q.ra, q.Y};
+    TcOpnd e{q.E, (long long)q.lde, 0, 1, 0, 1 << 30};
+    e.keep = true;  // a factor matrix of the context's operator
+    if (M >= q.N)
+      items[i] = TcItem{M, q.N, n, kr, e, 1.0, 0.0, q.out, 1, 0, 1 << 30, (long long)q.ldo};
+    else
+      items[i] = TcItem{q.N, M, n, e, kr, 1.0, 0.0, q.out, (long long)q.ldo, 0, 1 << 30, 1};
+  }
+  gemm_tc_group(c, kDigits, count, items.data());
+}
+
 // Probe factor of mode m for the Khatri-Rao sketches: with Om (n x ls) a fresh
 // Gaussian matrix, P_m[(a,s),k] = sum_i Q_m[i,a] Om[i,s] E_m[i,k]
 // = (KR(Q_m, Om)^T B_m) Z_m, an (r_m ls) x R matrix in the workspace. The same
@@ -661,7 +701,21 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
     bool todo[3] = {true, true, true};
     for (int attempt = 0; attempt < 2; ++attempt) {
       size_t mkp = c.ws.mark();
-      for (int m = 0; m < 3; ++m) P[m] = sketch_factor(c, D, x, m, ls);
+      if (!D.Z[0] && !D.Z[1] && !D.Z[2]) {
+        // uncompressed operator (tensor-core path): P_m = KR(Q_m, Om_m)^T E_m, the
+        // three modes in one grouped launch (probes drawn in mode order as below)
+        double *Om[3];
+        KrSpec sp[3];
+        for (int m = 0; m < 3; ++m) P[m] = c.ws.dbl((size_t)x.r[m] * ls * R);
+        for (int m = 0; m < 3; ++m) {
+          Om[m] = c.ws.dbl((size_t)n * ls);
+          fill_gaussian(c, Om[m], (size_t)n * ls, c.o.seed * 0x9E3779B97F4A7C15ull + (c.rng_counter++));
+          sp[m] = KrSpec{x.Q[m], n, x.r[m], Om[m], n, ls, D.B[m], n, D.rD[m], P[m], x.r[m] * ls};
+        }
+        kr_t_gemm_group(c, n, 3, sp);
+      } else {
+        for (int m = 0; m < 3; ++m) P[m] = sketch_factor(c, D, x, m, ls);
+      }
       int cnt = 0, ms[3], lds[3], caps[3], rr[3], idx[3];
       double *Ys[3], *Qs[3];
       for (int l = 0; l < 3; ++l) {
@@ -691,16 +745,24 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
   // ---------------- core of D .* X in the new bases
   TCTL_PHASE(c, "sep_core");
   double *M[3];
-  for (int l = 0; l < 3; ++l) {
-    // N_l[(a',b), p] = sum_i Qn[i,a'] Q[i,b] B[i,p];  M_l = N_l Z_l : (rn r) x R
-    double *N = c.ws.dbl((size_t)rn[l] * r[l] * D.rD[l]);
-    kr_t_gemm(c, n, Qn[l], n, rn[l], x.Q[l], n, r[l], D.B[l], n, D.rD[l], N, rn[l] * r[l]);
-    if (D.Z[l]) {
-      M[l] = c.ws.dbl((size_t)rn[l] * r[l] * R);
-      gemm_x(c, kDigits, false, false, rn[l] * r[l], R, D.rD[l], 1.0, N, rn[l] * r[l], 0, D.Z[l],
-             D.rD[l], 0, 0.0, M[l], rn[l] * r[l], 0);
-    } else {
-      M[l] = N;
+  {
+    // N_l[(a',b), p] = sum_i Qn[i,a'] Q[i,b] B[i,p], the three modes grouped;
+    // M_l = N_l Z_l : (rn r) x R for a compressed operator
+    double *Nl[3];
+    KrSpec sp[3];
+    for (int l = 0; l < 3; ++l) {
+      Nl[l] = c.ws.dbl((size_t)rn[l] * r[l] * D.rD[l]);
+      sp[l] = KrSpec{Qn[l], n, rn[l], x.Q[l], n, r[l], D.B[l], n, D.rD[l], Nl[l], rn[l] * r[l]};
+    }
+    kr_t_gemm_group(c, n, 3, sp);
+    for (int l = 0; l < 3; ++l) {
+      if (D.Z[l]) {
+        M[l] = c.ws.dbl((size_t)rn[l] * r[l] * R);
+        gemm_x(c, kDigits, false, false, rn[l] * r[l], R, D.rD[l], 1.0, Nl[l], rn[l] * r[l], 0, D.Z[l],
+               D.rD[l], 0, 0.0, M[l], rn[l] * r[l], 0);
+      } else {
+        M[l] = Nl[l];
+      }
     }
   }
   const long long szo = (long long)rn[0] * rn[1] * rn[2];

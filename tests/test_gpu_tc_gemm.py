@@ -139,7 +139,7 @@ def test_gemm_kr_fp64_path_and_errors(ctx):
 
 
 def test_autotuned_chunks_keep_the_error_bound():
-    """The tile autotuner (opts.tune, default on) picks the contracted length per CTA
+    """The tile autotuner (opts.tune = 1) picks the contracted length per CTA
     of each shape class by timing 64, 128 and 256; every choice keeps the digit
     split's error bound and gives the fixed-chunk (tune = 0) result to within it."""
     pr = make_problem(16, 0.5, 1e-2, 1, 1)
