@@ -127,7 +127,9 @@ typedef struct {
   int rank_x[3];         /* Tucker ranks of the solution before the final T2C         */
   int max_rank;          /* largest Tucker rank met inside the iteration              */
   int op_rank;           /* canonical rank R of the separable F2                      */
-  int op_basis[3];       /* per-mode compressed operator basis size                   */
+  int op_basis[3];       /* per-mode compressed operator basis size (FP64 contractions,
+                            tc_gemm = 0; with tc_gemm = 1 the factors are used as they
+                            are and this equals op_rank)                              */
   int pre_rank;          /* canonical rank of the preconditioner                      */
   double op_rel_err;     /* measured max rel. error of the separable F2 (sample)      */
   double s_min, s_max;   /* spectral interval of A                                    */

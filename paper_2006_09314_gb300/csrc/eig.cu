@@ -500,6 +500,8 @@ __global__ void eig_rqi_kernel(int n, const double *d0, const double *d1, const 
   }
 }
 
+// Set-up eigenpairs: A_(l) assembled, all 3n eigenpairs by eig_rqi_kernel, the
+// eigenvalues read back (s_min, s_max of the spectral sums).
 void setup_eigs(Ctx &c) {
   const int n = c.n;
   for (int l = 0; l < 3; ++l) {
@@ -523,23 +525,23 @@ void setup_eigs(Ctx &c) {
          ee, g);
   double *Lscr = c.ws.dbl((size_t)3 * n * n);
   double *Uscr = c.ws.dbl((size_t)3 * n * n);
-  // one warp per block spreads the 3n eigenpairs over all SMs (their FP64 work is
-  // bound by the FP64 pipe of the SMs they run on)
+  // one warp per block spreads the 3n eigenpairs over all SMs; each thread's
+  // time is its eigenpair's chain of dependent FP64 recurrences
   dim3 geig((n + 31) / 32, 3);
   const auto tb0 = std::chrono::steady_clock::now();
   LAUNCH(c, eig_rqi_kernel, geig, 32, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], ee, d32,
          ee32, g, bounds, c.lam[0], c.lam[1], c.lam[2], c.V[0], c.V[1], c.V[2], Lscr, Uscr,
          fallbacks);
+  for (int l = 0; l < 3; ++l) {
+    c.lam_host[l].resize(n);
+    to_host(c, c.lam_host[l].data(), c.lam[l], n);
+  }
   if (c.trace) {
     int nf = 0;
     read_host(c, &nf, fallbacks, sizeof(int));
     std::fprintf(stderr, "[tctl] eigenpairs %.1f ms (%d of %d by bisection)\n",
                  std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tb0).count(),
                  nf, 3 * n);
-  }
-  for (int l = 0; l < 3; ++l) {
-    c.lam_host[l].resize(n);
-    to_host(c, c.lam_host[l].data(), c.lam[l], n);
   }
   c.ws.reset(mk);
   c.s_min = c.lam_host[0][0] + c.lam_host[1][0] + c.lam_host[2][0];

@@ -406,6 +406,10 @@ double frob2(Ctx &c, int n, int m, const double *A, double *tmp) {
 // below tol in relative Frobenius norm; then Z_l = B_l^T E_l. Falls back to the plain
 // factors (Z = identity) if the basis would not be smaller than R/2.
 void compress_sep(Ctx &c, Sep &D, double tol) {
+  // the tensor-core contractions use the factor matrices themselves (their error
+  // is relative to row / column maxima, which the recombination B_l Z_l would
+  // spoil): the compressed basis serves only the FP64 path
+  if (c.o.tc_gemm) return;
   const int n = c.n, R = D.R;
   const int capD = std::min(R / 2, 192);
   if (capD < 8) return;
@@ -556,12 +560,13 @@ int expsum_fit_host(double a, double b, double smin, double smax, double tol, do
   return f.err <= tol ? TCTL_OK : TCTL_E_NUMERIC;
 }
 
-void setup_spectral(Ctx &c) {
+// Host part of the spectral set-up (needs only s_min, s_max, alpha, beta and the
+// host coefficients): the operator's exponential sum and the preconditioner's
+// sum, kept as term lists in the context. It can run while the eigensolver
+// is still computing the interior eigenpairs.
+void setup_spectral_fit(Ctx &c) {
   const double a = c.alpha, b = c.beta, smin = c.s_min, smax = c.s_max;
   const auto t0 = std::chrono::steady_clock::now();
-  auto ms = [&]() {
-    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  };
   const double delta = c.o.op_tol;
   // ---- operator F2 (term order as in the canonical factor layout)
   std::vector<double> w;
@@ -655,37 +660,25 @@ void setup_spectral(Ctx &c) {
     c.op_terms_t.push_back(d.t);
     c.op_terms_m.push_back(d.lam_mode);
   }
-  const double t_fit = ms();
-  build_sep(c, c.op, w, td);
-  compress_sep(c, c.op, 1e-13);
-  const double t_op = ms();
+  c.t_fit_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 
   // ---- preconditioner P(s) = s sum_k p_k exp(-theta_k s), NNLS weights
   // pre_src 3 (case (A) of Section 3.5): the anisotropic constant-coefficient
   // Laplacian B0 = sum_l b0_l Delta_l, b0_l = (max a_l + min a_l) / 2, whose
-  // eigenbasis is the sine basis: P ~ 1/F2 on its spectrum, applied there.
+  // eigenbasis is the sine basis: P ~ 1/F2 on its spectrum (b0_l mu_k), applied
+  // there (the basis change is built with the factors, it needs V_l).
   double psmin = smin, psmax = smax;
   if (c.o.pre_src == 3) {
     const int n = c.n;
-    size_t mks = c.ws.mark();
-    double *S = c.ws.dbl((size_t)n * n);
-    const int blocks = (int)std::min<long long>(((long long)n * n + 255) / 256, 4096);
-    LAUNCH(c, sine_basis_kernel, blocks, 256, 0, n, S);
     double mu1 = 0, mun = 0;
+    const double h = 1.0 / (n + 1);
     for (int l = 0; l < 3; ++l) {
       const double *al = c.coef_host.data() + (size_t)l * (n + 1);
       const double amax = *std::max_element(al, al + n + 1), amin = *std::min_element(al, al + n + 1);
       c.b0[l] = 0.5 * (amax + amin);
-      c.lamB[l] = c.dmalloc(n);
-      LAUNCH(c, scaled_laplacian_eigs_kernel, (n + 255) / 256, 256, 0, n, c.b0[l], c.lamB[l]);
-      c.W[l] = c.dmalloc((size_t)n * n);
-      // W_l = S^T V_l (S symmetric): FP64 for the basis change of the preconditioner
-      gemm(c, true, false, n, n, n, 1.0, S, n, 0, c.V[l], n, 0, 0.0, c.W[l], n, 0);
-      const double h = 1.0 / (n + 1);
       mu1 += c.b0[l] * 4.0 * std::pow(std::sin(0.5 * M_PI * h), 2) / (h * h);
       mun += c.b0[l] * 4.0 * std::pow(std::sin(0.5 * M_PI * h * n), 2) / (h * h);
     }
-    c.ws.reset(mks);
     psmin = mu1;
     psmax = mun;
   }
@@ -766,11 +759,49 @@ void setup_spectral(Ctx &c) {
     c.pre_terms_t.push_back(d.t);
     c.pre_terms_m.push_back(d.lam_mode);
   }
-  build_sep(c, c.pre, pw, ptd, c.o.pre_src == 3 ? c.lamB : nullptr);
+}
+
+// Device part: the factor matrices of both sums (they need the eigenvalues on
+// the device) and, for pre_src 3, the sine-basis change W_l = S^T V_l.
+void setup_spectral_build(Ctx &c) {
+  const auto t0 = std::chrono::steady_clock::now();
+  auto ms = [&]() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  };
+  auto terms = [](const std::vector<double> &t, const std::vector<int> &m) {
+    std::vector<TermDesc> td;
+    for (size_t k = 0; k < t.size(); ++k) td.push_back({t[k], m[k]});
+    return td;
+  };
+  build_sep(c, c.op, c.op_terms_w, terms(c.op_terms_t, c.op_terms_m));
+  compress_sep(c, c.op, 1e-13);
+  const double t_op = ms();
+  if (c.o.pre_src == 3) {
+    const int n = c.n;
+    size_t mks = c.ws.mark();
+    double *S = c.ws.dbl((size_t)n * n);
+    const int blocks = (int)std::min<long long>(((long long)n * n + 255) / 256, 4096);
+    LAUNCH(c, sine_basis_kernel, blocks, 256, 0, n, S);
+    for (int l = 0; l < 3; ++l) {
+      c.lamB[l] = c.dmalloc(n);
+      LAUNCH(c, scaled_laplacian_eigs_kernel, (n + 255) / 256, 256, 0, n, c.b0[l], c.lamB[l]);
+      c.W[l] = c.dmalloc((size_t)n * n);
+      // W_l = S^T V_l (S symmetric): FP64 for the basis change of the preconditioner
+      gemm(c, true, false, n, n, n, 1.0, S, n, 0, c.V[l], n, 0, 0.0, c.W[l], n, 0);
+    }
+    c.ws.reset(mks);
+  }
+  build_sep(c, c.pre, c.pre_terms_w, terms(c.pre_terms_t, c.pre_terms_m),
+            c.o.pre_src == 3 ? c.lamB : nullptr);
   compress_sep(c, c.pre, 1e-13);
   if (c.trace)
-    std::fprintf(stderr, "[tctl] spectral: F2 fit %.1f ms, operator factors %.1f ms, preconditioner %.1f ms\n",
-                 t_fit, t_op - t_fit, ms() - t_op);
+    std::fprintf(stderr, "[tctl] spectral: sums fitted in %.1f ms; operator factors %.1f ms, "
+                 "preconditioner %.1f ms\n", c.t_fit_ms, t_op, ms() - t_op);
+}
+
+void setup_spectral(Ctx &c) {
+  setup_spectral_fit(c);
+  setup_spectral_build(c);
 }
 
 // State operator A^-alpha (state equation of Section 3.1, y = A^-alpha u): the

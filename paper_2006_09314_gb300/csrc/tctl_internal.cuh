@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -96,6 +97,7 @@ struct Ctx {
   double op_rel_err = 0;
   int expsum_used = 0;                     // 0 sinc, 1 fitted, 2 learned
   double op_learned_err = 0;               // expsum_src 2: the learned sum's measured error
+  double t_fit_ms = 0;                     // host time of the spectral fits (set-up trace)
   double sinc24_err = 0;                   // expsum_src 2: sinc with 24 terms per function
   Sep state;                               // A^-alpha (state equation), built on first use
   double state_rel_err = 0;
@@ -339,6 +341,7 @@ void to_dev(Ctx &c, double *dst, const double *src, size_t count);
 // Assemble A_(l) from coef and compute all three eigendecompositions in FP64.
 void setup_eigs(Ctx &c);
 
+
 // ------------------------------------------------------------ spectral.cu
 int expsum_fit_host(double a, double b, double smin, double smax, double tol, double *t, double *w,
                     int cap, int *r, double *err);
@@ -376,6 +379,10 @@ void mlp_forward_host(int r, int n, const float *model, const float *X, float *Y
 std::vector<double> nnls_solve(const std::vector<double> &A, int M, int K, const std::vector<double> &b);
 void ensure_state_sep(Ctx &c);
 void setup_spectral(Ctx &c);
+// The same in two parts: host fits of the sums (needs s_min, s_max only) and
+// the device factor matrices (needs the eigenpairs).
+void setup_spectral_fit(Ctx &c);
+void setup_spectral_build(Ctx &c);
 void fullgrid_apply(Ctx &c, const double *y, double *u, int which);
 
 // ------------------------------------------------------------ tc_modeprod.cu
