@@ -183,6 +183,83 @@ void ttm(Ctx &c, const int r[3], const double *core, const double *M, int ldm, b
   }
 }
 
+// out[i, j, k] = sum_{a,b,c} A0(i, a) A1(j, b) A2(k, c) core[a, b, c] (the
+// three mode products of a Tucker core in one launch): CTA k forms
+// S = sum_c A2(k, c) core[:, :, c] (r0 x r1), then A0 S A1^T, in shared
+// memory. A_l(x, y) = M_l[y + x ld_l] if transposed, else M_l[x + y ld_l].
+struct Ttm3Args {
+  const double *core;
+  int r0, r1, r2;
+  const double *M[3];
+  int ld[3], tr[3];
+  int p0, p1, p2;
+  double *out;
+};
+
+__global__ void __launch_bounds__(256) ttm3_kernel(Ttm3Args g) {
+  extern __shared__ double sm3[];
+  const int k = blockIdx.x;
+  const int r0 = g.r0, r1 = g.r1, r2 = g.r2, p0 = g.p0, p1 = g.p1;
+  double *S = sm3;                 // r0 x r1
+  double *T = S + r0 * r1;         // p0 x r1
+  double *A0 = T + p0 * r1;        // p0 x r0
+  double *A1 = A0 + p0 * r0;       // p1 x r1
+  auto at = [&](int l, int x, int y) {
+    return g.tr[l] ? g.M[l][y + (long long)x * g.ld[l]] : g.M[l][x + (long long)y * g.ld[l]];
+  };
+  for (int t = threadIdx.x; t < p0 * r0; t += blockDim.x) A0[t] = at(0, t % p0, t / p0);
+  for (int t = threadIdx.x; t < p1 * r1; t += blockDim.x) A1[t] = at(1, t % p1, t / p1);
+  const long long slab = (long long)r0 * r1;
+  for (int t = threadIdx.x; t < r0 * r1; t += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < r2; ++c) s = fma(at(2, k, c), g.core[t + c * slab], s);
+    S[t] = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < p0 * r1; t += blockDim.x) {
+    const int i = t % p0, b = t / p0;
+    double s = 0.0;
+    for (int a = 0; a < r0; ++a) s = fma(A0[i + a * p0], S[a + b * r0], s);
+    T[t] = s;
+  }
+  __syncthreads();
+  double *o = g.out + (long long)p0 * p1 * k;
+  for (int t = threadIdx.x; t < p0 * p1; t += blockDim.x) {
+    const int i = t % p0, j = t / p0;
+    double s = 0.0;
+    for (int b = 0; b < r1; ++b) s = fma(T[i + b * p0], A1[j + b * p1], s);
+    o[t] = s;
+  }
+}
+
+// core x_0 op(M0) x_1 op(M1) x_2 op(M2) -> out (p0 x p1 x p2); op(M_l) is p_l x r_l,
+// stored transposed (r_l x p_l, ld) when tr_l. One fused launch while the
+// shared-memory tiles fit, else three GEMM launches (ttm). t1, t2: scratch of
+// the GEMM route (p0 r1 r2 and p0 p1 r2 doubles).
+void ttm3(Ctx &c, const int r[3], const double *core, double *const M[3], const int ld[3],
+          const bool tr[3], const int p[3], double *out, double *t1, double *t2) {
+  const size_t smem = sizeof(double) * ((size_t)r[0] * r[1] + (size_t)p[0] * r[1] + (size_t)p[0] * r[0] +
+                                        (size_t)p[1] * r[1]);
+  if (smem <= 96 * 1024 && p[2] > 0) {
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(ttm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    TCTL_CUDA(attr);
+    Ttm3Args g{core, r[0], r[1], r[2], {M[0], M[1], M[2]}, {ld[0], ld[1], ld[2]},
+               {tr[0] ? 1 : 0, tr[1] ? 1 : 0, tr[2] ? 1 : 0}, p[0], p[1], p[2], out};
+    c.next_flops = 2.0 * p[2] * ((double)r[0] * r[1] * r[2] + (double)p[0] * r[0] * r[1] +
+                                 (double)p[0] * p[1] * r[1]);
+    c.next_bytes = 8.0 * ((double)r[0] * r[1] * r[2] + (double)p[0] * p[1] * p[2]);
+    LAUNCH(c, ttm3_kernel, p[2], 256, smem, g);
+    return;
+  }
+  int rc[3] = {r[0], r[1], r[2]};
+  ttm(c, rc, core, M[0], ld[0], tr[0], p[0], 0, t1);
+  rc[0] = p[0];
+  ttm(c, rc, t1, M[1], ld[1], tr[1], p[1], 1, t2);
+  rc[1] = p[1];
+  ttm(c, rc, t2, M[2], ld[2], tr[2], p[2], 2, out);
+}
+
 int rank_from_tail(const std::vector<double> &lam_desc, double thr2) {
   // smallest r such that sum_{i >= r} max(lam_i, 0) <= thr2
   const int m = (int)lam_desc.size();
@@ -268,12 +345,14 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
                  r[1], r[2], rn[0], rn[1], rn[2]);
   // new core = core x_l U_l[:, :rn]^T
   double *t1 = c.ws.dbl(sz), *t2 = c.ws.dbl(sz);
-  int rc[3] = {r[0], r[1], r[2]};
-  ttm(c, rc, x.core, U[0], r[0], true, rn[0], 0, t1);
-  rc[0] = rn[0];
-  ttm(c, rc, t1, U[1], r[1], true, rn[1], 1, t2);
-  rc[1] = rn[1];
-  ttm(c, rc, t2, U[2], r[2], true, rn[2], 2, x.core);
+  {
+    // the new core is written in place of the old one: through a separate buffer
+    double *nc = c.ws.dbl((size_t)rn[0] * rn[1] * rn[2]);
+    const int ldu[3] = {r[0], r[1], r[2]};
+    const bool tr[3] = {true, true, true};
+    ttm3(c, r, x.core, U, ldu, tr, rn, nc, t1, t2);
+    copy_d(c, x.core, nc, (size_t)rn[0] * rn[1] * rn[2]);
+  }
   // new factors Q_l U_l[:, :rn], the three modes in one launch
   {
     GemmSpec g[3];
@@ -311,12 +390,11 @@ double tucker_inner(Ctx &c, const Tucker &x, const Tucker &y) {
   const long long big = (long long)std::max(x.r[0], y.r[0]) * std::max(x.r[1], y.r[1]) *
                         std::max(x.r[2], y.r[2]);
   double *t1 = c.ws.dbl(big), *t2 = c.ws.dbl(big), *t3 = c.ws.dbl(big);
-  int rc[3] = {y.r[0], y.r[1], y.r[2]};
-  ttm(c, rc, y.core, M[0], x.r[0], false, x.r[0], 0, t1);
-  rc[0] = x.r[0];
-  ttm(c, rc, t1, M[1], x.r[1], false, x.r[1], 1, t2);
-  rc[1] = x.r[1];
-  ttm(c, rc, t2, M[2], x.r[2], false, x.r[2], 2, t3);
+  {
+    const int ldm[3] = {x.r[0], x.r[1], x.r[2]};
+    const bool tr[3] = {false, false, false};
+    ttm3(c, y.r, y.core, M, ldm, tr, x.r, t3, t1, t2);
+  }
   const double v = dot_host(c, (long long)x.r[0] * x.r[1] * x.r[2], x.core, t3);
   c.ws.reset(mk);
   return v;
@@ -415,12 +493,11 @@ void tucker_axpby_trunc(Ctx &c, double a, const Tucker &x, double b, const Tucke
            core);
   }
   double *t1 = c.ws.dbl(szz), *t2 = c.ws.dbl(szz), *t3 = c.ws.dbl(szz);
-  int rc[3] = {y.r[0], y.r[1], y.r[2]};
-  ttm(c, rc, y.core, My[0], rz[0], false, rz[0], 0, t1);
-  rc[0] = rz[0];
-  ttm(c, rc, t1, My[1], rz[1], false, rz[1], 1, t2);
-  rc[1] = rz[1];
-  ttm(c, rc, t2, My[2], rz[2], false, rz[2], 2, t3);
+  {
+    const int ldm[3] = {rz[0], rz[1], rz[2]};
+    const bool tr[3] = {false, false, false};
+    ttm3(c, y.r, y.core, My, ldm, tr, rz, t3, t1, t2);
+  }
   axpby(c, (size_t)szz, b, t3, 1.0, core);
   {
     double *dst[4] = {z.Q[0], z.Q[1], z.Q[2], z.core};
