@@ -525,11 +525,7 @@ def _pipe_peaks():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # committed ncu summaries, keyed by kernel; None where no capture of the current
 # kernel exists
-TRAFFIC_PER_LAUNCH = {
-    # profiles/dram_rank_structured_n2048_single_solve.md: the 240 launches of
-    # the timed solve, 105.6 MB read + written in all
-    "dgemm_kernel": 440e3,
-}
+TRAFFIC_PER_LAUNCH = {}
 
 
 def roofline_from_trace(rep):

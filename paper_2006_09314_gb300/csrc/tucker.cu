@@ -677,16 +677,17 @@ static double *sketch_factor(Ctx &c, const Sep &D, const Tucker &x, int m, int l
 // Y (n x ls) = mode-l unfolding of D .* X times ls Khatri-Rao Gaussian probes
 // (one Gaussian vector per other mode per probe, from the probe factors P).
 // Cl: core permuted so mode l is first.
-static void sketch_mode(Ctx &c, const Sep &D, const Tucker &x, const double *Cl, int l, int ls,
-                        double *const P[3], double *Y) {
-  const int n = c.n, R = D.R;
+// uT (r_l ls x rD_l, in the workspace) of the mode-l sketch:
+// v[a,(s,k)] = w_k sum_{b,c} Cl[a,b,c] P_m1[(b,s),k] P_m2[(c,s),k], in chunks of k;
+// uT[(a,s),p] = sum_k v[(a,s),k] Z_l[p,k] (uT = v for an uncompressed operator)
+static double *sketch_uT(Ctx &c, const Sep &D, const Tucker &x, const double *Cl, int l, int ls,
+                         double *const P[3]) {
+  const int R = D.R;
   const int r[3] = {x.r[0], x.r[1], x.r[2]};
   const int oth[3][2] = {{1, 2}, {0, 2}, {0, 1}};
   const int m1 = oth[l][0], m2 = oth[l][1];
-  size_t mk = c.ws.mark();
-  // v[a,(s,k)] = w_k sum_{b,c} Cl[a,b,c] P_m1[(b,s),k] P_m2[(c,s),k], in chunks of k;
-  // uT[(a,s),p] = sum_k v[(a,s),k] Z_l[p,k]
   double *uT = c.ws.dbl((size_t)r[l] * ls * D.rD[l]);
+  size_t mk = c.ws.mark();
   const long long per_k = (long long)r[l] * r[m1] * ls;
   const int kc = (int)std::max<long long>(1, std::min<long long>(R, (32ll << 20) / std::max(per_k, 1ll)));
   double *F = c.ws.dbl((size_t)per_k * kc);
@@ -706,20 +707,78 @@ static void sketch_mode(Ctx &c, const Sep &D, const Tucker &x, const double *Cl,
       copy_d(c, uT + (size_t)r[l] * ls * k0, v, (size_t)r[l] * ls * nk);
     }
   }
-  // Y[i, s] = sum_{a,p} Q_l[i, a] B_l[i, p] uT[(a,s), p], contracted over p
-  // first: W[i, a + r_l s] = (B_l uT^T)[i, (a,s)] (n x r_l ls, in slices of s),
-  // then over a row by row. The Khatri-Rao product KR(Q_l, B_l) (n x r_l rD)
-  // is never formed.
-  const int sc = std::max(1, std::min(ls, (int)((64ll << 20) / ((long long)n * r[l] * 8))));
-  double *W = c.ws.dbl((size_t)n * r[l] * sc);
+  c.ws.reset(mk);
+  return uT;
+}
+
+// Y[i, s] = sum_{a,p} Q_l[i, a] B_l[i, p] uT[(a,s), p], contracted over p
+// first: W[i, a + r_l s] = (B_l uT^T)[i, (a,s)] (n x r_l ls, in slices of s),
+// then over a row by row. The Khatri-Rao product KR(Q_l, B_l) (n x r_l rD)
+// is never formed.
+static int sketch_slice(const Ctx &c, const Tucker &x, int l, int ls) {
+  return std::max(1, std::min(ls, (int)((64ll << 20) / ((long long)c.n * x.r[l] * 8))));
+}
+
+static void sketch_rows(Ctx &c, const Sep &D, const Tucker &x, int l, int ls, const double *uT, double *Y) {
+  const int n = c.n, rl = x.r[l];
+  size_t mk = c.ws.mark();
+  const int sc = sketch_slice(c, x, l, ls);
+  double *W = c.ws.dbl((size_t)n * rl * sc);
   for (int s0 = 0; s0 < ls; s0 += sc) {
     const int ns = std::min(sc, ls - s0);
-    gemm_x(c, kDigits, false, true, n, r[l] * ns, D.rD[l], 1.0, D.B[l], n, 0,
-           uT + (size_t)r[l] * s0, r[l] * ls, 0, 0.0, W, n, 0, 1, 1, 1, true);
+    gemm_x(c, kDigits, false, true, n, rl * ns, D.rD[l], 1.0, D.B[l], n, 0, uT + (size_t)rl * s0, rl * ls,
+           0, 0.0, W, n, 0, 1, 1, 1, true);
     const long long tot = (long long)n * ns;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-    c.next_bytes = 8.0 * n * ((double)r[l] * ns + r[l] + ns);
-    LAUNCH(c, rowdot_kernel, blocks, 256, 0, n, r[l], ns, x.Q[l], n, W, n, Y + (size_t)n * s0, n);
+    c.next_bytes = 8.0 * n * ((double)rl * ns + rl + ns);
+    LAUNCH(c, rowdot_kernel, blocks, 256, 0, n, rl, ns, x.Q[l], n, W, n, Y + (size_t)n * s0, n);
+  }
+  c.ws.reset(mk);
+}
+
+// Y_l (n x ls) = mode-l unfolding of D .* X times ls Khatri-Rao Gaussian probes
+// (one Gaussian vector per other mode per probe, from the probe factors P), for
+// the modes in `modes`; Cl[l]: core permuted so mode l is first. With the
+// tensor-core contractions the W products of all the modes run in one grouped
+// launch when each needs a single slice.
+static void sketch_modes(Ctx &c, const Sep &D, const Tucker &x, double *const Cl[3], const int *modes,
+                         int count, int ls, double *const P[3], double *const Y[3]) {
+  const int n = c.n;
+  size_t mk = c.ws.mark();
+  double *uT[3] = {nullptr, nullptr, nullptr};
+  for (int t = 0; t < count; ++t) uT[modes[t]] = sketch_uT(c, D, x, Cl[modes[t]], modes[t], ls, P);
+  bool group = c.o.tc_gemm != 0 && count > 1;
+  for (int t = 0; t < count && group; ++t) {
+    const int l = modes[t], N = x.r[l] * ls;
+    group = !D.Z[l] && sketch_slice(c, x, l, ls) >= ls &&
+            gemm_tc_fits(std::max(n, N), std::min(n, N), D.rD[l], 1);
+  }
+  if (!group) {
+    for (int t = 0; t < count; ++t) sketch_rows(c, D, x, modes[t], ls, uT[modes[t]], Y[modes[t]]);
+    c.ws.reset(mk);
+    return;
+  }
+  double *W[3] = {nullptr, nullptr, nullptr};
+  std::vector<TcItem> items;
+  for (int t = 0; t < count; ++t) {
+    const int l = modes[t], N = x.r[l] * ls, K = D.rD[l];
+    W[l] = c.ws.dbl((size_t)n * N);
+    // op(B_l)(i, p) = B_l[i + p n] (kept factor planes); op(uT^T)(j, p) = uT[j + p N]
+    TcOpnd b{D.B[l], 1, 0, (long long)n, 0, 1 << 30};
+    b.keep = true;
+    const TcOpnd u{uT[l], 1, 0, (long long)N, 0, 1 << 30};
+    if (n >= N)
+      items.push_back(TcItem{n, N, K, b, u, 1.0, 0.0, W[l], 1, 0, 1 << 30, (long long)n});
+    else  // W^T = uT B_l^T: the larger dimension on the 128-row side
+      items.push_back(TcItem{N, n, K, u, b, 1.0, 0.0, W[l], (long long)n, 0, 1 << 30, 1});
+  }
+  gemm_tc_group(c, kDigits, (int)items.size(), items.data());
+  for (int t = 0; t < count; ++t) {
+    const int l = modes[t], rl = x.r[l];
+    const long long tot = (long long)n * ls;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+    c.next_bytes = 8.0 * n * ((double)rl * ls + rl + ls);
+    LAUNCH(c, rowdot_kernel, blocks, 256, 0, n, rl, ls, x.Q[l], n, W[l], n, Y[l], n);
   }
   c.ws.reset(mk);
 }
@@ -795,9 +854,14 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
       }
       int cnt = 0, ms[3], lds[3], caps[3], rr[3], idx[3];
       double *Ys[3], *Qs[3];
+      {
+        int modes[3], nm = 0;
+        for (int l = 0; l < 3; ++l)
+          if (todo[l]) modes[nm++] = l;
+        sketch_modes(c, D, x, Cl, modes, nm, ls, P, Y);
+      }
       for (int l = 0; l < 3; ++l) {
         if (!todo[l]) continue;
-        sketch_mode(c, D, x, Cl[l], l, ls, P, Y[l]);
         idx[cnt] = l;
         ms[cnt] = ls;
         lds[cnt] = n;
