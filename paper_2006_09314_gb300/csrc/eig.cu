@@ -243,6 +243,11 @@ __global__ void twisted_kernel(int n, const double *d0, const double *d1, const 
 //      in FP64 from the Courant-Fischer bracket as before.
 // The eigenvector is the normalised z of the last factorization.
 
+#ifndef TCTL_EIG_BLOCK
+#define TCTL_EIG_BLOCK 32
+#endif
+constexpr int kEigBlock = TCTL_EIG_BLOCK;  // threads (eigenpairs) per block, a power of two <= 64
+
 // FP32 copies of d and e^2 (the guess phase), e^2 in FP64, the Weyl sign weights.
 __global__ void eig_prep_kernel(int n, const double *d0, const double *d1, const double *d2,
                                 const double *e0, const double *e1, const double *e2,
@@ -525,11 +530,12 @@ void setup_eigs(Ctx &c) {
          ee, g);
   double *Lscr = c.ws.dbl((size_t)3 * n * n);
   double *Uscr = c.ws.dbl((size_t)3 * n * n);
-  // one warp per block spreads the 3n eigenpairs over all SMs; each thread's
-  // time is its eigenpair's chain of dependent FP64 recurrences
-  dim3 geig((n + 31) / 32, 3);
+  // kEigBlock eigenpairs per block (a warp or part of one) spread the 3n
+  // eigenpairs over all SMs; each thread's time is its eigenpair's chain of
+  // dependent FP64 recurrences
+  dim3 geig((n + kEigBlock - 1) / kEigBlock, 3);
   const auto tb0 = std::chrono::steady_clock::now();
-  LAUNCH(c, eig_rqi_kernel, geig, 32, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], ee, d32,
+  LAUNCH(c, eig_rqi_kernel, geig, kEigBlock, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], ee, d32,
          ee32, g, bounds, c.lam[0], c.lam[1], c.lam[2], c.V[0], c.V[1], c.V[2], Lscr, Uscr,
          fallbacks);
   for (int l = 0; l < 3; ++l) {

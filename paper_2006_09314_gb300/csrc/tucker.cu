@@ -260,6 +260,101 @@ void ttm3(Ctx &c, const int r[3], const double *core, double *const M[3], const 
   ttm(c, rc, t2, M[2], ld[2], tr[2], p[2], 2, out);
 }
 
+// Core of the truncated Hadamard product in the new bases, fused:
+// out[a', b', c'] = sum_k w_k sum_{a,b,c} M0k(a', a) M1k(b', b) M2k(c', c) core[a, b, c],
+// M_lk(x, y) = M_l[x + p_l y + p_l r_l k] (p_l x r_l per operator term k).
+// CTA (c', q) sums the terms of k chunk q in shared memory (per term the
+// mode-3 contraction first, then modes 1 and 2, as ttm3_kernel) and writes
+// its partial sum; core_proj_reduce adds the chunks in a fixed order.
+struct CoreProjArgs {
+  const double *core;
+  int r0, r1, r2, p0, p1, p2;
+  const double *M[3];
+  const double *w;
+  int R, kchunk;
+  double *part;  // [(q p2 + c') p0 p1 + a' + p0 b']
+};
+
+__global__ void __launch_bounds__(256) core_proj_kernel(CoreProjArgs g) {
+  extern __shared__ double smc[];
+  const int cp = blockIdx.x, q = blockIdx.y;
+  const int r0 = g.r0, r1 = g.r1, r2 = g.r2, p0 = g.p0, p1 = g.p1, p2 = g.p2;
+  double *S = smc;            // r0 x r1
+  double *T = S + r0 * r1;    // p0 x r1
+  double *acc = T + p0 * r1;  // p0 x p1
+  for (int t = threadIdx.x; t < p0 * p1; t += blockDim.x) acc[t] = 0.0;
+  const long long slab = (long long)r0 * r1;
+  const int k0 = q * g.kchunk, k1 = min(g.R, k0 + g.kchunk);
+  for (int k = k0; k < k1; ++k) {
+    const double *M0 = g.M[0] + (long long)p0 * r0 * k;
+    const double *M1 = g.M[1] + (long long)p1 * r1 * k;
+    const double *M2 = g.M[2] + (long long)p2 * r2 * k;
+    __syncthreads();  // acc / T of the previous term are complete
+    for (int t = threadIdx.x; t < r0 * r1; t += blockDim.x) {
+      double sacc = 0.0;
+      for (int c = 0; c < r2; ++c) sacc = fma(M2[cp + (long long)p2 * c], g.core[t + c * slab], sacc);
+      S[t] = sacc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < p0 * r1; t += blockDim.x) {
+      const int i = t % p0, b = t / p0;
+      double sacc = 0.0;
+      for (int a = 0; a < r0; ++a) sacc = fma(M0[i + (long long)p0 * a], S[a + r0 * b], sacc);
+      T[t] = sacc;
+    }
+    __syncthreads();
+    const double wk = g.w[k];
+    for (int t = threadIdx.x; t < p0 * p1; t += blockDim.x) {
+      const int i = t % p0, j = t / p0;
+      double sacc = 0.0;
+      for (int b = 0; b < r1; ++b) sacc = fma(T[i + p0 * b], M1[j + (long long)p1 * b], sacc);
+      acc[t] = fma(wk, sacc, acc[t]);
+    }
+  }
+  __syncthreads();
+  double *o = g.part + ((long long)q * p2 + cp) * p0 * p1;
+  for (int t = threadIdx.x; t < p0 * p1; t += blockDim.x) o[t] = acc[t];
+}
+
+__global__ void core_proj_reduce(long long slab3, int chunks, const double *__restrict__ part,
+                                 double *__restrict__ out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < slab3;
+       t += (long long)gridDim.x * blockDim.x) {
+    double sacc = 0.0;
+    for (int q = 0; q < chunks; ++q) sacc += part[t + q * slab3];
+    out[t] = sacc;
+  }
+}
+
+// The fused core projection for small ranks: its FP64 work per operator term,
+// r0 r1 r2 + p0 r0 r1 + p0 p1 r1 FMAs, stays below 40k (ranks around 20, as in
+// the PCG iterates); larger cores take the GEMM chain, whose last product runs
+// on the tensor cores. False if the caller must use the chain.
+bool core_proj(Ctx &c, const int r[3], const int p[3], const double *core, double *const M[3],
+               const double *w, int R, double *out) {
+  const size_t smem = sizeof(double) * ((size_t)r[0] * r[1] + (size_t)p[0] * r[1] + (size_t)p[0] * p[1]);
+  const double per_term = (double)r[0] * r[1] * r[2] + (double)p[0] * r[0] * r[1] + (double)p[0] * p[1] * r[1];
+  if (smem > 48 * 1024 || R <= 0 || per_term > 40000.0) return false;
+  // the terms of one output slab in chunks so that the grid has about two CTAs per SM
+  const int chunks = std::max(1, std::min(R, (2 * 152 + p[2] - 1) / p[2]));
+  const int kchunk = (R + chunks - 1) / chunks;
+  const int nq = (R + kchunk - 1) / kchunk;
+  const long long slab3 = (long long)p[0] * p[1] * p[2];
+  size_t mk = c.ws.mark();
+  double *part = c.ws.dbl((size_t)slab3 * nq);
+  CoreProjArgs g{core, r[0], r[1], r[2], p[0], p[1], p[2], {M[0], M[1], M[2]}, w, R, kchunk, part};
+  c.next_flops = 2.0 * R * p[2] * ((double)r[0] * r[1] * r[2] + (double)p[0] * r[0] * r[1] +
+                                   (double)p[0] * p[1] * r[1]);
+  c.next_bytes = 8.0 * ((double)r[0] * r[1] * r[2] + (double)R * (p[0] * r[0] + p[1] * r[1] + p[2] * r[2]) +
+                        (double)slab3 * nq);
+  LAUNCH(c, core_proj_kernel, dim3(p[2], nq), 256, smem, g);
+  const int blocks = (int)std::min<long long>((slab3 + 255) / 256, 4096);
+  c.next_bytes = 8.0 * (double)slab3 * (nq + 1);
+  LAUNCH(c, core_proj_reduce, blocks, 256, 0, slab3, nq, part, out);
+  c.ws.reset(mk);
+  return true;
+}
+
 int rank_from_tail(const std::vector<double> &lam_desc, double thr2) {
   // smallest r such that sum_{i >= r} max(lam_i, 0) <= thr2
   const int m = (int)lam_desc.size();
@@ -908,7 +1003,7 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
   }
   const long long szo = (long long)rn[0] * rn[1] * rn[2];
   double *nc = c.ws.dbl(szo);
-  {
+  if (!core_proj(c, r, rn, x.core, M, D.w, R, nc)) {
     const long long s1 = (long long)rn[0] * r[1] * r[2];
     const long long s2 = (long long)rn[0] * r[1] * rn[2];
     const long long s3 = szo;
