@@ -702,6 +702,46 @@ void fill_gaussian(Ctx &c, double *x, size_t count, uint64_t seed) {
   LAUNCH(c, gaussian_kernel, blocks, 256, 0, x, count, seed);
 }
 
+// Several Gaussian fills in one launch: fill i writes x[i][t] = the value
+// gaussian_kernel would write with seed[i] (the same counter-based draws).
+struct GaussArgs {
+  int count;
+  double *x[3];
+  uint64_t seed[3];
+  long long off[4];  // prefix of the element counts
+};
+
+__global__ void gaussian_multi_kernel(GaussArgs a) {
+  const long long total = a.off[a.count];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i = 0;
+    while (i + 1 < a.count && t >= a.off[i + 1]) ++i;
+    const uint64_t r = (uint64_t)(t - a.off[i]);
+    const uint64_t h1 = mix64(a.seed[i] ^ mix64(2 * r));
+    const uint64_t h2 = mix64(a.seed[i] ^ mix64(2 * r + 1));
+    const double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
+    const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);          // [0, 1)
+    a.x[i][r] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+void fill_gaussian_multi(Ctx &c, int count, double *const *x, const size_t *n, const uint64_t *seed) {
+  GaussArgs a{};
+  long long tot = 0;
+  for (int i = 0; i < count && i < 3; ++i) {
+    a.x[a.count] = x[i];
+    a.seed[a.count] = seed[i];
+    a.off[a.count] = tot;
+    tot += (long long)n[i];
+    ++a.count;
+  }
+  if (!tot) return;
+  a.off[a.count] = tot;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  LAUNCH(c, gaussian_multi_kernel, blocks, 256, 0, a);
+}
+
 void fill_zero(Ctx &c, double *x, size_t count) {
   if (count) TCTL_CUDA(cudaMemsetAsync(x, 0, count * sizeof(double), c.st));
 }
@@ -1153,6 +1193,27 @@ __global__ void orth_check_kernel(int r, const double *__restrict__ G, double to
   if (threadIdx.x == 0) *flag = bad;
 }
 
+// orth_check_kernel for up to ORTH_BATCH matrices, one CTA each (r = 0: skipped).
+struct OcBatch {
+  const double *G[8];
+  int r[8];
+  int *flag[8];
+};
+
+__global__ void orth_check_multi_kernel(OcBatch b, double tol) {
+  const int q = blockIdx.x, r = b.r[q];
+  if (r <= 0) return;
+  const double *G = b.G[q];
+  int bad = 0;
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+    const int i = t % r, j = t / r;
+    const double d = G[t] - (i == j ? 1.0 : 0.0);
+    if (!(fabs(d) <= tol)) bad = 1;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) *b.flag[q] = bad;
+}
+
 // Q[i, :] = Y[i, perm] L^{-T}: forward substitution per row (x L^T = y).
 __device__ __forceinline__ void trsm_rows_body(int n, int r, const double *__restrict__ Y, int ldy,
                                                const int *__restrict__ perm,
@@ -1286,9 +1347,14 @@ void orth_multi(Ctx &c, int count, int n, const int *m, double *const *Y, const 
   };
   // pass 1: pivoted Cholesky of Y^T Y picks the columns and the ranks
   std::vector<int> mm(m, m + count), cap(count);
-  for (int i = 0; i < count; ++i) {
-    cap[i] = rcap[i];
-    if (m[i] > 0) gemm(c, true, false, m[i], m[i], n, 1.0, Y[i], ldy[i], 0, Y[i], ldy[i], 0, 0.0, G[i], m[i], 0);
+  {
+    // the Gram matrices of all the matrices in one grouped launch
+    std::vector<GemmSpec> g;
+    for (int i = 0; i < count; ++i) {
+      cap[i] = rcap[i];
+      if (m[i] > 0) g.push_back(GemmSpec{true, false, m[i], m[i], n, 1.0, Y[i], ldy[i], Y[i], ldy[i], 0.0, G[i], m[i]});
+    }
+    gemm_group(c, (int)g.size(), g.data());
   }
   pivchol_all(mm, cap, tol, relative ? 1 : 0);
   for (int i = 0; i < count; ++i) r[i] = m[i] > 0 ? rr[i] : 0;
@@ -1303,18 +1369,22 @@ void orth_multi(Ctx &c, int count, int n, const int *m, double *const *Y, const 
   std::vector<char> active(count);
   for (int i = 0; i < count; ++i) active[i] = r[i] > 0;
   for (int pass = 0; pass < 2; ++pass) {
-    bool any = false;
+    std::vector<GemmSpec> g;
     for (int i = 0; i < count; ++i)
-      if (active[i]) {
-        gemm(c, true, false, r[i], r[i], n, 1.0, Q[i], n, 0, Q[i], n, 0, 0.0, G[i], r[i], 0);
-        any = true;
-      }
-    if (!any) break;
+      if (active[i]) g.push_back(GemmSpec{true, false, r[i], r[i], n, 1.0, Q[i], n, Q[i], n, 0.0, G[i], r[i]});
+    if (g.empty()) break;
+    gemm_group(c, (int)g.size(), g.data());
     if (pass == 1) {
-      for (int i = 0; i < count; ++i)
-        if (active[i]) LAUNCH(c, orth_check_kernel, 1, 256, 0, r[i], G[i], 1e-13, rdev + count + i);
+      OcBatch ob{};
+      for (int i = 0; i < count; ++i) {
+        ob.G[i] = G[i];
+        ob.r[i] = active[i] ? r[i] : 0;
+        ob.flag[i] = rdev + count + i;
+      }
+      TCTL_CUDA(cudaMemsetAsync(rdev + count, 0, sizeof(int) * count, c.st));
+      LAUNCH(c, orth_check_multi_kernel, count, 256, 0, ob, 1e-13);
       read_ints(2 * count);
-      any = false;
+      bool any = false;
       for (int i = 0; i < count; ++i) {
         if (active[i] && !rr[count + i]) active[i] = 0;
         any = any || active[i];
@@ -1335,9 +1405,20 @@ void orth_multi(Ctx &c, int count, int n, const int *m, double *const *Y, const 
       std::vector<int> ld(count, n);
       trsm_all(src, ld, r2, Q2);
     }
+    {
+      std::vector<double *> dst;
+      std::vector<const double *> srcq;
+      std::vector<size_t> cnt;
+      for (int i = 0; i < count; ++i)
+        if (active[i] && r2[i] > 0) {
+          dst.push_back(Q[i]);
+          srcq.push_back(Q2[i]);
+          cnt.push_back((size_t)n * r2[i]);
+        }
+      copy_multi(c, (int)dst.size(), dst.data(), srcq.data(), cnt.data());
+    }
     for (int i = 0; i < count; ++i)
       if (active[i]) {
-        if (r2[i] > 0) copy_d(c, Q[i], Q2[i], (size_t)n * r2[i]);
         r[i] = r2[i];
         if (r[i] == 0) active[i] = 0;
       }

@@ -321,6 +321,8 @@ int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relati
 void col_norms(Ctx &c, int n, int m, const double *A, int lda, double *out);
 void scale_cols(Ctx &c, int n, int m, double *A, int lda, const double *s, bool inverse);
 void fill_gaussian(Ctx &c, double *x, size_t count, uint64_t seed);
+// Up to three fills in one launch, each with the draws fill_gaussian gives its seed.
+void fill_gaussian_multi(Ctx &c, int count, double *const *x, const size_t *n, const uint64_t *seed);
 void fill_zero(Ctx &c, double *x, size_t count);
 void copy_d(Ctx &c, double *dst, const double *src, size_t count);
 // Several device-to-device copies (dst[i] <- src[i], n[i] doubles) in one launch.

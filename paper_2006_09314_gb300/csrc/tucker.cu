@@ -51,6 +51,30 @@ __global__ void permute3_kernel(int r0, int r1, int r2, const double *__restrict
   }
 }
 
+// The mode-2 and mode-3 unfoldings of a core in one pass (and, with o0, a copy):
+// o1 = permute3(in, 1, 0, 2), o2 = permute3(in, 2, 0, 1).
+__global__ void unfold3_kernel(int r0, int r1, int r2, const double *__restrict__ in,
+                               double *__restrict__ o0, double *__restrict__ o1,
+                               double *__restrict__ o2) {
+  const long long total = (long long)r0 * r1 * r2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(t % r0), b = (int)((t / r0) % r1), cc = (int)(t / ((long long)r0 * r1));
+    const double v = in[t];
+    if (o0) o0[t] = v;
+    o1[b + (long long)r1 * (a + (long long)r0 * cc)] = v;
+    o2[cc + (long long)r2 * (a + (long long)r0 * b)] = v;
+  }
+}
+
+void unfold3(Ctx &c, const int r[3], const double *in, double *o0, double *o1, double *o2) {
+  const long long total = (long long)r[0] * r[1] * r[2];
+  if (!total) return;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 2048);
+  c.next_bytes = 8.0 * total * (o0 ? 4 : 3);
+  LAUNCH(c, unfold3_kernel, blocks, 256, 0, r[0], r[1], r[2], in, o0, o1, o2);
+}
+
 void permute3(Ctx &c, const int r[3], const double *in, int p0, int p1, int p2, double *out) {
   const long long total = (long long)r[0] * r[1] * r[2];
   if (!total) return;
@@ -89,6 +113,31 @@ __global__ void rowdot_kernel(int n, int ra, int ns, const double *__restrict__ 
     double acc = 0.0;
     for (int a = 0; a < ra; ++a) acc = fma(Q[i + (long long)a * ldq], w[(long long)a * ldw], acc);
     Y[i + (long long)s * ldy] = acc;
+  }
+}
+
+// rowdot_kernel for the three modes of a sketch in one launch (ld = n throughout).
+struct RowdotGroup {
+  int count;
+  int ra[3];
+  const double *Q[3];
+  const double *W[3];
+  double *Y[3];
+};
+
+__global__ void rowdot_group_kernel(int n, int ns, RowdotGroup g) {
+  const long long per = (long long)n * ns, total = per * g.count;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(t / per);
+    const long long u = t - per * m;
+    const int i = (int)(u % n), s = (int)(u / n);
+    const int ra = g.ra[m];
+    const double *w = g.W[m] + i + (long long)ra * s * n;
+    const double *q = g.Q[m] + i;
+    double acc = 0.0;
+    for (int a = 0; a < ra; ++a) acc = fma(q[(long long)a * n], w[(long long)a * n], acc);
+    g.Y[m][i + (long long)s * n] = acc;
   }
 }
 
@@ -401,8 +450,7 @@ void tucker_hosvd_trunc(Ctx &c, Tucker &x, double eps) {
   double *G[3], *lam[3], *U[3];
   std::vector<double> lh[3];
   double *lam_all = c.ws.dbl((size_t)r[0] + r[1] + r[2]);  // one read-back for the three modes
-  permute3(c, r, x.core, 1, 0, 2, perm1);
-  permute3(c, r, x.core, 2, 0, 1, perm2);
+  unfold3(c, r, x.core, nullptr, perm1, perm2);
   {
     // Gram matrices of the three mode-l unfoldings (r_l x rest, ld r_l) in one launch
     const double *src[3] = {x.core, perm1, perm2};
@@ -868,13 +916,21 @@ static void sketch_modes(Ctx &c, const Sep &D, const Tucker &x, double *const Cl
       items.push_back(TcItem{N, n, K, u, b, 1.0, 0.0, W[l], (long long)n, 0, 1 << 30, 1});
   }
   gemm_tc_group(c, kDigits, (int)items.size(), items.data());
+  RowdotGroup rg{};
+  double bytes = 0;
   for (int t = 0; t < count; ++t) {
-    const int l = modes[t], rl = x.r[l];
-    const long long tot = (long long)n * ls;
-    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-    c.next_bytes = 8.0 * n * ((double)rl * ls + rl + ls);
-    LAUNCH(c, rowdot_kernel, blocks, 256, 0, n, rl, ls, x.Q[l], n, W[l], n, Y[l], n);
+    const int l = modes[t];
+    rg.ra[t] = x.r[l];
+    rg.Q[t] = x.Q[l];
+    rg.W[t] = W[l];
+    rg.Y[t] = Y[l];
+    bytes += 8.0 * n * ((double)x.r[l] * ls + x.r[l] + ls);
   }
+  rg.count = count;
+  const long long tot = (long long)n * ls * count;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  c.next_bytes = bytes;
+  LAUNCH(c, rowdot_group_kernel, blocks, 256, 0, n, ls, rg);
   c.ws.reset(mk);
 }
 
@@ -908,12 +964,8 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
   int rn[3];
   // permuted cores with mode l first: Cl[l] dims (r_l, r_m1, r_m2), m1 < m2 the other modes
   double *Cl[3];
-  for (int l = 0; l < 3; ++l) {
-    Cl[l] = c.ws.dbl((size_t)r[0] * r[1] * r[2]);
-    if (l == 0) copy_d(c, Cl[0], x.core, (size_t)r[0] * r[1] * r[2]);
-    else if (l == 1) permute3(c, r, x.core, 1, 0, 2, Cl[1]);
-    else permute3(c, r, x.core, 2, 0, 1, Cl[2]);
-  }
+  for (int l = 0; l < 3; ++l) Cl[l] = c.ws.dbl((size_t)r[0] * r[1] * r[2]);
+  unfold3(c, r, x.core, Cl[0], Cl[1], Cl[2]);
   // ---------------- range finding per mode
   int ls = std::min(kMaxRank, rmax + 24);
   const double rtol = std::max(1e-8, c.o.range_tol * eps);
@@ -938,11 +990,15 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
         double *Om[3];
         KrSpec sp[3];
         for (int m = 0; m < 3; ++m) P[m] = c.ws.dbl((size_t)x.r[m] * ls * R);
+        size_t cnt[3];
+        uint64_t seeds[3];
         for (int m = 0; m < 3; ++m) {
           Om[m] = c.ws.dbl((size_t)n * ls);
-          fill_gaussian(c, Om[m], (size_t)n * ls, c.o.seed * 0x9E3779B97F4A7C15ull + (c.rng_counter++));
+          cnt[m] = (size_t)n * ls;
+          seeds[m] = c.o.seed * 0x9E3779B97F4A7C15ull + (c.rng_counter++);
           sp[m] = KrSpec{x.Q[m], n, x.r[m], Om[m], n, ls, D.B[m], n, D.rD[m], P[m], x.r[m] * ls};
         }
+        fill_gaussian_multi(c, 3, Om, cnt, seeds);
         kr_t_gemm_group(c, n, 3, sp);
       } else {
         for (int m = 0; m < 3; ++m) P[m] = sketch_factor(c, D, x, m, ls);
