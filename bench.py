@@ -522,10 +522,26 @@ def _pipe_peaks():
                     else "fallback 6.8 TB/s")}
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
-# committed ncu summaries, keyed by kernel; None where no capture of the current
-# kernel exists
-TRAFFIC_PER_LAUNCH = {}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, bytes)
+# of one n = 2048 solve traced alone (profiles/dram_rank_structured_n2048_single_solve.md),
+# keyed by kernel; a kernel missing here has no capture of its current code
+TRAFFIC_PER_LAUNCH = {
+    "dgemm_group_kernel": 1468085,
+    "tcg_group_kernel": 58770101,
+    "tcg_kernel": 28367633,
+    "split_group_kernel": 15342908,
+    "split_kernel": 7879151,
+    "row_exp_group_kernel": 2550754,
+    "row_exp_kernel": 5928764,
+    "rowdot_group_kernel": 48142507,
+    "khatri_rao_kernel": 189594,
+    "contract_b_kernel": 18571193,
+    "ttm3_kernel": 217792,
+    "skinny_nn_kernel": 45234534,
+    "skinny_tn_kernel": 33656832,
+    "dgemm_kernel": 381087,
+    "core_proj_kernel": 632768,
+}
 
 
 def roofline_from_trace(rep):
@@ -552,6 +568,11 @@ def roofline_from_trace(rep):
         if "bound" in e:
             e["frac"] = round(e["achieved"] / peaks[e["bound"]][0], 4)
             e["achieved"] = round(e["achieved"], 4)
+        if name in TRAFFIC_PER_LAUNCH:
+            # measured DRAM bytes of the capture over this trace's launch time
+            gbs = TRAFFIC_PER_LAUNCH[name] * v["launches"] / sec / 1e9
+            e["dram_gbs"] = round(gbs, 1)
+            e["dram_frac_of_hbm"] = round(gbs / peaks["hbm"][0], 4)
         kern[name] = e
     iso = {"solve_kernel_ms": tot,
            "kernels": dict(sorted(kern.items(), key=lambda kv: -kv[1]["ms"])[:12])}
