@@ -413,8 +413,8 @@ def ours_arm(args, rank, world):
     direct = {f: [None] * B for f in variant_sols}
     t_chk = time.perf_counter()
     if not args.no_check:
-        # every solve of the main run and of the directly checked forms (plain
-        # FP64 sinc, learned preconditioner) against the oracle, one pass per problem
+        # every solve of the main run and of the directly checked forms (DIRECT_FORMS)
+        # against the oracle, one pass per problem
         for i, (p, x) in enumerate(zip(probs, sols)):
             forms = list(variant_sols)
             e = oracle_errors(p, [x.to_numpy()] + [variant_sols[f][i] for f in forms], pool)
@@ -598,7 +598,8 @@ def roofline_from_trace(rep):
 def verify_variants(variants, direct, errs):
     """Oracle-error status of the variant solves (adds keys to each variant).
 
-    Forms in `direct` (the plain FP64 sinc form and the learned preconditioner)
+    Forms in `direct` (the plain FP64 sinc form, the learned preconditioner and
+    the three-term split forms)
     were checked against the oracle solve by solve. For the others a solve's
     oracle error is at most the main solve's (checked) plus their distance
     (exact canonical inner products), and it counts as verified when that
@@ -625,6 +626,9 @@ def variants_section(args, T, probs, streams, bs, master, ref_sols, batch_runner
     plain method); fp64_fitted: fitted exponential sums, FP64; learned_pre: the
     default (fitted sums, tensor-core contractions) with an r = 12 preconditioner
     predicted by a network trained here on the library's own fitted sums;
+    bf16x3: the contractions in the three-term BF16 split (21 bits, six
+    products, FP32 accumulation); bf16x3_refined: the same inner solves inside
+    up to two steps of FP64 outer residual refinement;
     fitted_pre: the same with the r = 12 sum fitted at set-up (what a perfect
     network would give); aniso_pre: the paper's case (A) preconditioner, 1/F2
     of the anisotropic constant-coefficient Laplacian in its sine basis.
@@ -644,10 +648,12 @@ def variants_section(args, T, probs, streams, bs, master, ref_sols, batch_runner
     forms = [("fp64_sinc", dict(expsum_src=0, tc_gemm=0)),
              ("fp64_fitted", dict(expsum_src=1, tc_gemm=0)),
              ("learned_pre", dict(pre_src=2, pre_r=r, pre_model=model.ctypes.data, pre_delta_max=0.25)),
+             ("bf16x3", dict(tc_digits=3)),
+             ("bf16x3_refined", dict(tc_digits=3, refine=2)),
              ("fitted_pre", dict(pre_src=1, pre_r=r, pre_delta_max=0.25)),
              ("aniso_pre", dict(pre_src=3))]
     if not args.all_variants:
-        forms = forms[:3]
+        forms = forms[:5]
     ref = [x.to_numpy() for x in ref_sols]
     keep_sols = {}  # solutions of the directly checked forms
     for name, kw in forms:
@@ -658,7 +664,7 @@ def variants_section(args, T, probs, streams, bs, master, ref_sols, batch_runner
         diffs = []
         for (w0, U0), (x, st, _) in zip(ref, res):
             w1, U1 = x.to_numpy()
-            if name in ("fp64_sinc", "learned_pre"):
+            if name in DIRECT_FORMS:
                 keep_sols.setdefault(name, []).append((w1, U1))
             d2 = (Fm.cp_inner(w0, U0, w0, U0) - 2 * Fm.cp_inner(w0, U0, w1, U1)
                   + Fm.cp_inner(w1, U1, w1, U1))
@@ -667,6 +673,7 @@ def variants_section(args, T, probs, streams, bs, master, ref_sols, batch_runner
                      "ms_per_step": sum(ts) / steps,
                      "rel_diff_to_main": diffs,
                      "iters": [x[1]["iters"] for x in res],
+                     "refines": [x[1]["refines"] for x in res],
                      "op_rank": [c.stats()["op_rank"] for c in cs],
                      "pre_rank": [c.stats()["pre_rank"] for c in cs],
                      "pre_used": [c.stats()["pre_used"] for c in cs],
@@ -684,6 +691,8 @@ def variants_section(args, T, probs, streams, bs, master, ref_sols, batch_runner
 
 
 LEARN_SAMPLES = 20000
+# variant forms whose every solve is checked against the oracle itself
+DIRECT_FORMS = ("fp64_sinc", "learned_pre", "bf16x3", "bf16x3_refined")
 
 
 def learned_operator_section(T, probs, n, r=16):

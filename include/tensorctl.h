@@ -119,6 +119,16 @@ typedef struct {
                          at its first use and kept for the process; 0 = fixed 256
                          (default: timed while other contexts share the GPU, the
                          choices were measured to slow the concurrent solves)         */
+  int tc_digits;      /* digits of the rank-structured tensor-core contractions inside
+                         tctl_pcg_solve (tc_gemm = 1): 6 (default, 42 bits, 21
+                         products), 4 (28 bits, 10 products) or 3 (21 bits, 6
+                         products: the three-term BF16 split with FP32
+                         accumulation); the other entry points use 6              */
+  int refine;         /* FP64 outer residual refinement steps of tctl_pcg_solve
+                         (default 0, at most 8): after the PCG, while the residual
+                         B - F2(A) X formed with FP64 FMA contractions (truncated at
+                         eps_final) exceeds pcg_rtol ||B||, X += PCG(that residual),
+                         the inner solves at tc_digits                             */
 } tctl_opts;
 
 typedef struct {
@@ -145,6 +155,9 @@ typedef struct {
                             sum (accepted when <= op_judge); 0 otherwise               */
   double sinc24_err;     /* expsum_src 2: the same error of the sinc quadrature with 24
                             terms per function (the judge's reference); 0 otherwise    */
+  int refines;           /* refinement steps taken by the last tctl_pcg_solve         */
+  double true_rel_res;   /* refine > 0: the last FP64 residual ||B - F2(A) X|| / ||B||
+                            formed (-1 when none was)                                   */
 } tctl_stats;
 
 /* Fills *o with the defaults listed above. */
@@ -265,8 +278,8 @@ int tctl_get_stats(tctl_ctx *ctx, tctl_stats *st);
 
 /* C = alpha op(A) op(B) + beta C for DEVICE FP64 column-major matrices
  * (op(A) m x k, op(B) k x n, op = transpose when trans_* != 0), ordered on
- * the context's stream. digits = 0: FP64 FMA kernels; digits = 4 or 6: the
- * tensor-core digit split of the rank-structured path (each operand as 4 / 6
+ * the context's stream. digits = 0: FP64 FMA kernels; digits = 3, 4 or 6: the
+ * tensor-core digit split of the rank-structured path (each operand as 3 / 4 / 6
  * signed 7-bit BF16 digits with one binary exponent per row of op(A) and per
  * column of op(B); FP32 accumulation with exact leading levels, 256-deep K
  * chunks summed in FP64). Error per entry ~2^-7d K max|A_i.| max|B_.j|.
@@ -283,7 +296,7 @@ int tctl_gemm(tctl_ctx *ctx, int digits, int trans_a, int trans_b, int m, int n,
  * core projections of Section 3.4's Hadamard products (probe factors and
  * factor-basis products), contracted over the grid index. digits = 0: the
  * product is formed in the context's workspace and multiplied by the FP64
- * kernels; digits = 4 or 6: the tensor-core digit split of tctl_gemm forms
+ * kernels; digits = 3, 4 or 6: the tensor-core digit split of tctl_gemm forms
  * each product X(i, a) Y(i, b) while splitting (nothing k x ra rb is stored),
  * with the same result as tctl_gemm on the stored product. Ordered on the
  * context's stream; synchronizes when digits > 0. Errors: TCTL_E_ARG,

@@ -94,78 +94,138 @@ namespace tctl {
 
 void set_noalloc_error(const std::string &msg) { g_last_error = msg; }
 
-int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
-  Timer timer(c.st);
+// Algorithm 1 on the Tucker right-hand side B (context coordinates): X from
+// X0 = 0 until ||R_k|| <= tol (absolute) or max_iter; the work vectors are
+// the caller's. Returns the iterations; *rel = the last ||R_k|| / ||B||.
+int pcg_run(Ctx &c, const Tucker &B, double bnorm, double tol, Tucker &X, Tucker *w, double *rel,
+            int *maxr) {
   const double eps = c.eps;
   const double eps_x = c.o.eps_final > 0 ? c.o.eps_final : 0.1 * eps;
+  Tucker &R = w[0], &Z = w[1], &P = w[2], &S = w[3], &T1 = w[4], &T2 = w[5];
+  auto track = [&](const Tucker &t) {
+    for (int l = 0; l < 3; ++l) *maxr = std::max(*maxr, t.r[l]);
+  };
+  int iters = 0;
+  X.r[0] = X.r[1] = X.r[2] = 0;
+  *rel = 1.0;
+  tucker_copy(c, B, R);                       // R0 = B - fun(X0), X0 = 0
+  {
+    TCTL_OUTER(c, "precond");
+    apply_sep(c, c.pre, R, Z, T1, eps);       // Z0 = trunc(precond(R0))
+  }
+  tucker_copy(c, Z, P);                       // P0 = Z0
+  double rz = tucker_inner(c, R, Z);
+  while (iters < c.o.max_iter) {
+    {
+      TCTL_OUTER(c, "fun");
+      apply_sep(c, c.op, P, S, T1, eps);      // S = trunc(fun(P))
+    }
+    track(S);
+    const double pS = tucker_inner(c, P, S);
+    if (!(pS > 0.0) || !std::isfinite(pS)) fail(TCTL_E_NUMERIC, "PCG breakdown: <P, S> <= 0");
+    const double a = rz / pS;
+    {
+      TCTL_OUTER(c, "update_x");
+      tucker_axpby_trunc(c, 1.0, X, a, P, T2, eps_x);  // X = trunc(X + a P)
+    }
+    std::swap(X, T2);
+    // R = trunc(R - a S); the stopping test uses ||R - a S|| before the
+    // truncation, and a converged residual is not truncated (not used again)
+    double rnorm = 0.0;
+    {
+      TCTL_OUTER(c, "update_r");
+      tucker_axpby_trunc(c, 1.0, R, -a, S, T2, eps, &rnorm, tol);
+    }
+    std::swap(R, T2);
+    track(X);
+    track(R);
+    ++iters;
+    *rel = rnorm / bnorm;
+    if (!std::isfinite(*rel)) fail(TCTL_E_NAN, "non-finite residual");
+    if (rnorm <= tol) break;
+    {
+      TCTL_OUTER(c, "precond");
+      apply_sep(c, c.pre, R, Z, T1, eps);     // Z = trunc(precond(R))
+    }
+    const double rz_new = tucker_inner(c, R, Z);
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    {
+      TCTL_OUTER(c, "update_p");
+      tucker_axpby_trunc(c, 1.0, Z, beta, P, T2, eps);  // P = trunc(Z + beta P)
+    }
+    std::swap(P, T2);
+    track(P);
+  }
+  return iters;
+}
+
+// Algorithm 1, optionally inside opts.refine steps of FP64 residual
+// refinement: X_0 = PCG(B) with the contractions at opts.tc_digits digits;
+// then, while ||B - fun(X_j)|| > pcg_rtol ||B|| (the residual formed with
+// FP64 FMA contractions, truncated at eps_final), X_{j+1} = trunc(X_j +
+// PCG(B - fun(X_j))) with the same low-precision inner solve.
+int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
+  Timer timer(c.st);
+  const double eps_x = c.o.eps_final > 0 ? c.o.eps_final : 0.1 * c.eps;
   const bool eig = (c.o.basis == 1);
   size_t mk = c.ws.mark();
-  Tucker B, X, R, Z, P, S, T1, T2;
-  for (Tucker *t : {&B, &X, &R, &Z, &P, &S, &T1, &T2}) tucker_alloc(c, *t, kCap);
+  Tucker B, X, D, Rt, T1, w[6];
+  for (Tucker *t : {&B, &X}) tucker_alloc(c, *t, kCap);
+  for (Tucker &t : w) tucker_alloc(c, t, kCap);
+  if (c.o.refine > 0)
+    for (Tucker *t : {&D, &Rt, &T1}) tucker_alloc(c, *t, kCap);
   cp_to_tucker(c, b->rank, b->w, b->U, eig, B, 1e-12);
   const double bnorm = std::sqrt(std::max(tucker_inner(c, B, B), 0.0));
+  const double tol = c.o.pcg_rtol * bnorm;
   int status = TCTL_OK;
-  int iters = 0;
-  double rel = 0.0;
-  int maxr = 0;
-  auto track = [&](const Tucker &t) {
-    for (int l = 0; l < 3; ++l) maxr = std::max(maxr, t.r[l]);
-  };
+  int iters = 0, maxr = 0, refines = 0;
+  double rel = 0.0, true_rel = -1.0;
   X.r[0] = X.r[1] = X.r[2] = 0;
+  // the inner solves' digit count and the FP64 switch of the residual step are
+  // put back on every exit (a failure throws)
+  struct Restore {
+    Ctx &c;
+    int tc;
+    ~Restore() {
+      c.digits = 6;
+      c.o.tc_gemm = tc;
+    }
+  } restore{c, c.o.tc_gemm};
+  c.digits = c.o.tc_digits;
   if (bnorm == 0.0) {
     x->rank = 0;
   } else {
-    tucker_copy(c, B, R);                       // R0 = B - fun(X0), X0 = 0
-    {
-      TCTL_OUTER(c, "precond");
-      apply_sep(c, c.pre, R, Z, T1, eps);       // Z0 = trunc(precond(R0))
-    }
-    tucker_copy(c, Z, P);                       // P0 = Z0
-    double rz = tucker_inner(c, R, Z);
-    rel = 1.0;
-    while (iters < c.o.max_iter) {
+    iters = pcg_run(c, B, bnorm, tol, X, w, &rel, &maxr);
+    bool converged = rel <= c.o.pcg_rtol;
+    for (int j = 0; j < c.o.refine; ++j) {
+      // Rt = trunc(B - fun(X)) with FP64 contractions
+      c.o.tc_gemm = 0;
+      double rn = 0.0;
       {
-        TCTL_OUTER(c, "fun");
-        apply_sep(c, c.op, P, S, T1, eps);      // S = trunc(fun(P))
+        TCTL_OUTER(c, "residual");
+        apply_sep(c, c.op, X, w[3], T1, eps_x);
+        tucker_axpby_trunc(c, 1.0, B, -1.0, w[3], Rt, eps_x, &rn);
       }
-      track(S);
-      const double pS = tucker_inner(c, P, S);
-      if (!(pS > 0.0) || !std::isfinite(pS)) fail(TCTL_E_NUMERIC, "PCG breakdown: <P, S> <= 0");
-      const double a = rz / pS;
+      c.o.tc_gemm = restore.tc;
+      true_rel = rn / bnorm;
+      if (!std::isfinite(true_rel)) fail(TCTL_E_NAN, "non-finite residual");
+      if (rn <= tol) {
+        converged = true;
+        break;
+      }
+      double rel_d = 0.0;
+      iters += pcg_run(c, Rt, bnorm, tol, D, w, &rel_d, &maxr);
       {
         TCTL_OUTER(c, "update_x");
-        tucker_axpby_trunc(c, 1.0, X, a, P, T2, eps_x);  // X = trunc(X + a P)
+        tucker_axpby_trunc(c, 1.0, X, 1.0, D, T1, eps_x);  // X = trunc(X + D)
       }
-      std::swap(X, T2);
-      // R = trunc(R - a S); the stopping test uses ||R - a S|| before the
-      // truncation, and a converged residual is not truncated (not used again)
-      double rnorm = 0.0;
-      {
-        TCTL_OUTER(c, "update_r");
-        tucker_axpby_trunc(c, 1.0, R, -a, S, T2, eps, &rnorm, c.o.pcg_rtol * bnorm);
-      }
-      std::swap(R, T2);
-      track(X);
-      track(R);
-      ++iters;
-      rel = rnorm / bnorm;
-      if (!std::isfinite(rel)) fail(TCTL_E_NAN, "non-finite residual");
-      if (rel <= c.o.pcg_rtol) break;
-      {
-        TCTL_OUTER(c, "precond");
-        apply_sep(c, c.pre, R, Z, T1, eps);     // Z = trunc(precond(R))
-      }
-      const double rz_new = tucker_inner(c, R, Z);
-      const double beta = rz_new / rz;
-      rz = rz_new;
-      {
-        TCTL_OUTER(c, "update_p");
-        tucker_axpby_trunc(c, 1.0, Z, beta, P, T2, eps);  // P = trunc(Z + beta P)
-      }
-      std::swap(P, T2);
-      track(P);
+      std::swap(X, T1);
+      ++refines;
+      converged = rel_d <= c.o.pcg_rtol;
+      rel = rel_d;
     }
-    if (rel > c.o.pcg_rtol) status = TCTL_E_NOT_CONVERGED;
+    if (!converged) status = TCTL_E_NOT_CONVERGED;
     TCTL_OUTER(c, "to_cp");
     const int s2 = tucker_to_cp(c, X, eig, eps_x, x);
     tcg_check(c);
@@ -173,6 +233,8 @@ int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st) {
   }
   c.stats.iters = iters;
   c.stats.rel_res = rel;
+  c.stats.refines = refines;
+  c.stats.true_rel_res = true_rel;
   for (int l = 0; l < 3; ++l) c.stats.rank_x[l] = X.r[l];
   c.stats.max_rank = maxr;
   c.stats.ws_peak_mb = (double)c.ws.peak / (1 << 20);
@@ -239,6 +301,8 @@ int tctl_default_opts(tctl_opts *o) {
   o->op_r = 16;
   o->op_judge = 1e-7;
   o->tune = 0;
+  o->tc_digits = 6;
+  o->refine = 0;
   return TCTL_OK;
 }
 
@@ -273,6 +337,9 @@ int tctl_setup(tctl_ctx **ctx, const double *coeffs, int n, double alpha, double
       fail(TCTL_E_ARG, "op_judge must be in (0, 1)");
     if (c->o.basis != 0 && c->o.basis != 1) fail(TCTL_E_ARG, "basis must be 0 or 1");
     if (c->o.tc_gemm != 0 && c->o.tc_gemm != 1) fail(TCTL_E_ARG, "tc_gemm must be 0 or 1");
+    if (c->o.tc_digits != 3 && c->o.tc_digits != 4 && c->o.tc_digits != 6)
+      fail(TCTL_E_ARG, "tc_digits must be 3, 4 or 6");
+    if (c->o.refine < 0 || c->o.refine > 8) fail(TCTL_E_ARG, "refine must be in [0, 8]");
     if (c->o.workspace_mb < 0) fail(TCTL_E_ARG, "workspace_mb must be >= 0");
     if (c->o.pre_src < 0 || c->o.pre_src > 3) fail(TCTL_E_ARG, "pre_src must be 0, 1, 2 or 3");
     if ((c->o.pre_src == 1 || c->o.pre_src == 2) && (c->o.pre_r < 2 || c->o.pre_r > kPreRMax))
@@ -573,7 +640,8 @@ int tctl_gemm(tctl_ctx *ctx, int digits, int trans_a, int trans_b, int m, int n,
   if (!c) return TCTL_E_ARG;
   try {
     if (m < 0 || n < 0 || k < 0) fail(TCTL_E_ARG, "negative dimension");
-    if (digits != 0 && digits != 4 && digits != 6) fail(TCTL_E_ARG, "digits must be 0, 4 or 6");
+    if (digits != 0 && digits != 3 && digits != 4 && digits != 6)
+      fail(TCTL_E_ARG, "digits must be 0, 3, 4 or 6");
     if ((m && n && k) && (!A || !B || !C)) fail(TCTL_E_ARG, "NULL matrix");
     if (lda < std::max(1, trans_a ? k : m) || ldb < std::max(1, trans_b ? n : k) || ldc < std::max(1, m))
       fail(TCTL_E_ARG, "leading dimension too small");
@@ -598,7 +666,8 @@ int tctl_gemm_kr(tctl_ctx *ctx, int digits, int k, int ra, int rb, int n, double
   if (!c) return TCTL_E_ARG;
   try {
     if (k < 0 || ra < 0 || rb < 0 || n < 0) fail(TCTL_E_ARG, "negative dimension");
-    if (digits != 0 && digits != 4 && digits != 6) fail(TCTL_E_ARG, "digits must be 0, 4 or 6");
+    if (digits != 0 && digits != 3 && digits != 4 && digits != 6)
+      fail(TCTL_E_ARG, "digits must be 0, 3, 4 or 6");
     const long long m = (long long)ra * rb;
     if (m > (1 << 30)) fail(TCTL_E_ARG, "ra * rb too large");
     if ((m && n && k) && (!X || !Y || !B || !C)) fail(TCTL_E_ARG, "NULL matrix");

@@ -13,7 +13,8 @@
 //   C[m, j] = 2^(e_m + f_j - 14) sum_{p + q <= D - 1} (a_p b_q)[m, j].
 // The 7D-bit fixed point of each element is truncated; the neglected digit
 // products and the truncation are ~2^-7D of the row / column maxima (D = 6:
-// 42 bits, ~2e-13 relative to max|A_m| max|B_j| K; D = 4: 28 bits).
+// 42 bits, ~2e-13 relative to max|A_m| max|B_j| K; D = 4: 28 bits; D = 3:
+// 21 bits in six products, the three-term BF16 split with FP32 accumulation).
 // Products go to four TMEM accumulators by digit level L = p + q: levels 0, 1
 // and 2 separately (every partial sum is an integer multiple of 2^-7L below
 // (L + 1) 127^2 KCHUNK 2^-7L, i.e. fewer than 2^24 units for KCHUNK = 256:
@@ -368,7 +369,12 @@ __device__ __forceinline__ void tcg_body(const TcgArgs &a, int mt, int jt, int b
       TCTL_LD16(h0, t0);
       TCTL_LD16(h1, t0 + TN);
       TCTL_LD16(h2, t0 + 2 * TN);
-      TCTL_LD16(h3, t0 + 3 * TN);
+      if constexpr (D > 3) {
+        TCTL_LD16(h3, t0 + 3 * TN);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h3[i] = 0u;  // no level >= 3 with three digits
+      }
 #undef TCTL_LD16
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (m < a.M) {
@@ -898,7 +904,8 @@ void gemm_tc_group(Ctx &c, int digits, int count, const TcItem *items) {
       if ((q.M + TM - 1) / TM > 65535 || (q.N + TN - 1) / TN > 65535)
         fail(TCTL_E_ARG, "gemm_tc_group: item too large");
     }
-    if (digits <= 4) run_tcg_group<4, 4>(c, cnt, items + b);
+    if (digits <= 3) run_tcg_group<3, 5>(c, cnt, items + b);
+    else if (digits <= 4) run_tcg_group<4, 4>(c, cnt, items + b);
     else run_tcg_group<6, 3>(c, cnt, items + b);
   }
 }
@@ -921,7 +928,9 @@ void gemm_tc(Ctx &c, int digits, int M, int N, int K, int batch, int divA, int d
   if (K <= 0) fail(TCTL_E_ARG, "gemm_tc: K must be positive");
   if ((A.q || B.q) && batch != 1) fail(TCTL_E_ARG, "gemm_tc: a Khatri-Rao operand takes no batch");
   static_assert(TMEM_COLS >= 4 * TN, "four accumulators");
-  if (digits <= 4)
+  if (digits <= 3)
+    run_tcg<3, 5>(c, M, N, K, batch, divA, divB, alpha, A, B, beta, C, cm0, cm1, cd, cj, cb);
+  else if (digits <= 4)
     run_tcg<4, 4>(c, M, N, K, batch, divA, divB, alpha, A, B, beta, C, cm0, cm1, cd, cj, cb);
   else
     run_tcg<6, 3>(c, M, N, K, batch, divA, divB, alpha, A, B, beta, C, cm0, cm1, cd, cj, cb);

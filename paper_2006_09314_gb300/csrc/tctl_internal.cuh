@@ -130,6 +130,7 @@ struct Ctx {
   uint64_t rng_counter = 0;
   std::vector<void *> owned;         // device allocations freed at destroy
   int *tcg_err = nullptr;            // tensor-core GEMM wait-timeout flag (device)
+  int digits = 6;                    // digit count of the rank-structured tensor-core contractions
   int withhold_copies = 0;           // failure-detection test: GEMM launches left to starve
   // digit planes of constant tensor-core operands (the operator's factor
   // matrices), keyed by the operand's address, strides and split geometry
@@ -236,7 +237,7 @@ struct TcOpnd {
   bool keep = false;
 };
 // C[b sC' + (m % cd) cm0 + (m / cd) cm1 + j cj] = alpha sum_k A(m, k) B(j, k) + beta C,
-// batch item b of A / B = b / divA, b / divB; digits 4 (28-bit) or 6 (42-bit).
+// batch item b of A / B = b / divA, b / divB; digits 3 (21-bit), 4 (28-bit) or 6 (42-bit).
 void gemm_tc(Ctx &c, int digits, int M, int N, int K, int batch, int divA, int divB,
              double alpha, const TcOpnd &A, const TcOpnd &B, double beta, double *C,
              long long cm0, long long cm1, int cd, long long cj, long long cb);

@@ -31,9 +31,9 @@ namespace tctl {
 namespace {
 
 constexpr int kMaxRank = 64;
-// digits of the tensor-core GEMMs (42 bits: the sketches must resolve directions
-// down to the range tolerance, and the core feeds the eps truncation)
-constexpr int kDigits = 6;
+// The tensor-core GEMMs take c.digits digits (opts.tc_digits, default 6 = 42
+// bits: the sketches must resolve directions down to the range tolerance, and
+// the core feeds the eps truncation).
 
 __global__ void permute3_kernel(int r0, int r1, int r2, const double *__restrict__ in, int p0,
                                 int p1, int p2, double *__restrict__ out) {
@@ -740,15 +740,15 @@ static void kr_t_gemm(Ctx &c, int n, const double *X, int ldx, int ra, const dou
     e.keep = true;  // E is a factor matrix of the context's operator
     // the larger dimension takes the 128-row side of the tile
     if (M >= N)
-      gemm_tc(c, kDigits, M, N, n, 1, 1, 1, 1.0, kr, e, 0.0, out, 1, 0, 1 << 30, ldo, 0);
+      gemm_tc(c, c.digits, M, N, n, 1, 1, 1, 1.0, kr, e, 0.0, out, 1, 0, 1 << 30, ldo, 0);
     else
-      gemm_tc(c, kDigits, N, M, n, 1, 1, 1, 1.0, e, kr, 0.0, out, ldo, 0, 1 << 30, 1, 0);
+      gemm_tc(c, c.digits, N, M, n, 1, 1, 1, 1.0, e, kr, 0.0, out, ldo, 0, 1 << 30, 1, 0);
     return;
   }
   size_t mk = c.ws.mark();
   double *KR = c.ws.dbl((size_t)n * M);
   khatri_rao(c, n, X, ldx, ra, Y, ldy, rb, KR, n);
-  gemm_x(c, kDigits, true, false, M, N, n, 1.0, KR, n, 0, E, lde, 0, 0.0, out, ldo, 0);
+  gemm_x(c, c.digits, true, false, M, N, n, 1.0, KR, n, 0, E, lde, 0, 0.0, out, ldo, 0);
   c.ws.reset(mk);
 }
 
@@ -789,7 +789,7 @@ static void kr_t_gemm_group(Ctx &c, int n, int count, const KrSpec *sp) {
     else
       items[i] = TcItem{q.N, M, n, e, kr, 1.0, 0.0, q.out, (long long)q.ldo, 0, 1 << 30, 1};
   }
-  gemm_tc_group(c, kDigits, count, items.data());
+  gemm_tc_group(c, c.digits, count, items.data());
 }
 
 // Probe factor of mode m for the Khatri-Rao sketches: with Om (n x ls) a fresh
@@ -807,7 +807,7 @@ static double *sketch_factor(Ctx &c, const Sep &D, const Tucker &x, int m, int l
   if (D.Z[m]) {
     double *T = c.ws.dbl((size_t)rm * ls * D.rD[m]);
     kr_t_gemm(c, n, x.Q[m], n, rm, Om, n, ls, D.B[m], n, D.rD[m], T, rm * ls);
-    gemm_x(c, kDigits, false, false, rm * ls, R, D.rD[m], 1.0, T, rm * ls, 0, D.Z[m], D.rD[m], 0,
+    gemm_x(c, c.digits, false, false, rm * ls, R, D.rD[m], 1.0, T, rm * ls, 0, D.Z[m], D.rD[m], 0,
            0.0, P, rm * ls, 0);
   } else {
     // uncompressed operator: B_m holds the R factor columns themselves
@@ -837,14 +837,14 @@ static double *sketch_uT(Ctx &c, const Sep &D, const Tucker &x, const double *Cl
   double *v = c.ws.dbl((size_t)r[l] * ls * kc);
   for (int k0 = 0; k0 < R; k0 += kc) {
     const int nk = std::min(kc, R - k0);
-    gemm_x(c, kDigits, false, false, r[l] * r[m1], ls * nk, r[m2], 1.0, Cl, r[l] * r[m1], 0,
+    gemm_x(c, c.digits, false, false, r[l] * r[m1], ls * nk, r[m2], 1.0, Cl, r[l] * r[m1], 0,
            P[m2] + (size_t)r[m2] * ls * k0, r[m2], 0, 0.0, F, r[l] * r[m1], 0);
     const long long tot = (long long)r[l] * ls * nk;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
     LAUNCH(c, contract_b_kernel, blocks, 256, 0, r[l], r[m1], ls, nk, F,
            P[m1] + (size_t)r[m1] * ls * k0, D.w + k0, v);
     if (D.Z[l]) {
-      gemm_x(c, kDigits, false, true, r[l] * ls, D.rD[l], nk, 1.0, v, r[l] * ls, 0,
+      gemm_x(c, c.digits, false, true, r[l] * ls, D.rD[l], nk, 1.0, v, r[l] * ls, 0,
              D.Z[l] + (size_t)D.rD[l] * k0, D.rD[l], 0, k0 == 0 ? 0.0 : 1.0, uT, r[l] * ls, 0);
     } else {
       copy_d(c, uT + (size_t)r[l] * ls * k0, v, (size_t)r[l] * ls * nk);
@@ -869,7 +869,7 @@ static void sketch_rows(Ctx &c, const Sep &D, const Tucker &x, int l, int ls, co
   double *W = c.ws.dbl((size_t)n * rl * sc);
   for (int s0 = 0; s0 < ls; s0 += sc) {
     const int ns = std::min(sc, ls - s0);
-    gemm_x(c, kDigits, false, true, n, rl * ns, D.rD[l], 1.0, D.B[l], n, 0, uT + (size_t)rl * s0, rl * ls,
+    gemm_x(c, c.digits, false, true, n, rl * ns, D.rD[l], 1.0, D.B[l], n, 0, uT + (size_t)rl * s0, rl * ls,
            0, 0.0, W, n, 0, 1, 1, 1, true);
     const long long tot = (long long)n * ns;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
@@ -915,7 +915,7 @@ static void sketch_modes(Ctx &c, const Sep &D, const Tucker &x, double *const Cl
     else  // W^T = uT B_l^T: the larger dimension on the 128-row side
       items.push_back(TcItem{N, n, K, u, b, 1.0, 0.0, W[l], (long long)n, 0, 1 << 30, 1});
   }
-  gemm_tc_group(c, kDigits, (int)items.size(), items.data());
+  gemm_tc_group(c, c.digits, (int)items.size(), items.data());
   RowdotGroup rg{};
   double bytes = 0;
   for (int t = 0; t < count; ++t) {
@@ -1050,7 +1050,7 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
     for (int l = 0; l < 3; ++l) {
       if (D.Z[l]) {
         M[l] = c.ws.dbl((size_t)rn[l] * r[l] * R);
-        gemm_x(c, kDigits, false, false, rn[l] * r[l], R, D.rD[l], 1.0, Nl[l], rn[l] * r[l], 0, D.Z[l],
+        gemm_x(c, c.digits, false, false, rn[l] * r[l], R, D.rD[l], 1.0, Nl[l], rn[l] * r[l], 0, D.Z[l],
                D.rD[l], 0, 0.0, M[l], rn[l] * r[l], 0);
       } else {
         M[l] = Nl[l];
@@ -1070,11 +1070,11 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
     for (int k0 = 0; k0 < R; k0 += kc) {
       const int nk = std::min(kc, R - k0);
       // T1[k] = M_0k (rn0 x r0) * core (r0 x r1 r2)
-      gemm_x(c, kDigits, false, false, rn[0], r[1] * r[2], r[0], 1.0,
+      gemm_x(c, c.digits, false, false, rn[0], r[1] * r[2], r[0], 1.0,
              M[0] + (size_t)rn[0] * r[0] * k0, rn[0], (long long)rn[0] * r[0], x.core, r[0], 0, 0.0,
              T1, rn[0], s1, nk);
       // T2[k] = T1[k] (rn0 r1 x r2) * M_2k^T (r2 x rn2)
-      gemm_x(c, kDigits, false, true, rn[0] * r[1], rn[2], r[2], 1.0, T1, rn[0] * r[1], s1,
+      gemm_x(c, c.digits, false, true, rn[0] * r[1], rn[2], r[2], 1.0, T1, rn[0] * r[1], s1,
              M[2] + (size_t)rn[2] * r[2] * k0, rn[2], (long long)rn[2] * r[2], 0.0, T2, rn[0] * r[1],
              s2, nk);
       // T3[k](a, b', c') = sum_b T2[k](a, b, c') M_1k(b', b)
@@ -1083,7 +1083,7 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
         const TcOpnd A{T2, 1, (long long)rn[0] * r[1], (long long)rn[0], s2, rn[0]};
         const TcOpnd B{M[1] + (size_t)rn[1] * r[1] * k0, 1, 0, (long long)rn[1],
                        (long long)rn[1] * r[1], 1 << 30};
-        gemm_tc(c, kDigits, rn[0] * rn[2], rn[1], r[1], nk, 1, 1, 1.0, A, B, 0.0, T3, 1,
+        gemm_tc(c, c.digits, rn[0] * rn[2], rn[1], r[1], nk, 1, 1, 1.0, A, B, 0.0, T3, 1,
                 (long long)rn[0] * rn[1], rn[0], rn[0], s3);
       } else {
         // batch over (k, c'): T2[k][:,:,c'] (rn0 x r1) * M_1k^T (r1 x rn1)

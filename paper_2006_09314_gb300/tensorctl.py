@@ -74,7 +74,8 @@ class Opts(ctypes.Structure):
                 ("tc_gemm", ctypes.c_int), ("pre_src", ctypes.c_int), ("pre_r", ctypes.c_int),
                 ("pre_model", ctypes.c_void_p), ("pre_delta_max", ctypes.c_double),
                 ("workspace_mb", ctypes.c_int), ("op_model", ctypes.c_void_p),
-                ("op_r", ctypes.c_int), ("op_judge", ctypes.c_double), ("tune", ctypes.c_int)]
+                ("op_r", ctypes.c_int), ("op_judge", ctypes.c_double), ("tune", ctypes.c_int),
+                ("tc_digits", ctypes.c_int), ("refine", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -87,7 +88,8 @@ class Stats(ctypes.Structure):
                 ("expsum_used", ctypes.c_int), ("pre_used", ctypes.c_int),
                 ("pre_delta", ctypes.c_double), ("ws_peak_mb", ctypes.c_double),
                 ("ws_size_mb", ctypes.c_double), ("op_learned_err", ctypes.c_double),
-                ("sinc24_err", ctypes.c_double)]
+                ("sinc24_err", ctypes.c_double), ("refines", ctypes.c_int),
+                ("true_rel_res", ctypes.c_double)]
 
     def as_dict(self):
         out = {}

@@ -49,6 +49,13 @@ def test_default_opts_and_error_paths_without_gpu():
     assert lib.tctl_setup(ctypes.byref(ctx), coeffs.ctypes.data, 8, 0.5, 1e-2, 1e-6,
                           ctypes.byref(bad), None) == -1
     assert "range_tol" in T.tctl_last_error(None)
+    for bad in (T.tctl_default_opts(tc_digits=5), T.tctl_default_opts(refine=9),
+                T.tctl_default_opts(refine=-1)):
+        assert lib.tctl_setup(ctypes.byref(ctx), coeffs.ctypes.data, 8, 0.5, 1e-2, 1e-6,
+                              ctypes.byref(bad), None) == -1
+    assert "refine" in T.tctl_last_error(None)
+    o = T.tctl_default_opts()
+    assert o.tc_digits == 6 and o.refine == 0
     # the GEMM entry points refuse a missing context before touching the device
     assert lib.tctl_gemm(None, 6, 0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4) == -1
     assert lib.tctl_gemm_kr(None, 6, 4, 2, 2, 4, 1.0, None, 4, None, 4, None, 4, 0.0, None, 4) == -1

@@ -288,6 +288,37 @@ def test_pcg_full_size_n256(alpha, beta):
     assert np.max(np.abs(u - ustar)) <= 1e-5 * np.max(np.abs(ustar))
 
 
+def test_pcg_three_term_split_and_fp64_refinement_n256():
+    """The precision form: contractions in the three-term BF16 split (21 bits,
+    six products, FP32 accumulation) inside FP64 outer residual refinement.
+
+    At n = 256 one pass of the three-term split already meets 1e-6; two
+    refinement steps (residuals formed with FP64 FMA contractions) bring the
+    error below the single pass's, and the last residual formed is within the
+    stopping rule's reach.
+    """
+    n, alpha, beta = 256, 0.5, 1e-2
+    pr = make_problem(n, alpha, beta, 5, 1050)
+    lams, Vs = _oracle_eigs(pr)
+    Y = np.einsum("j,ij,kj,lj->ikl", pr.yw, pr.yU[0], pr.yU[1], pr.yU[2], optimize=True)
+    ustar = fg.solve_exact(Y, lams, Vs, alpha, beta)
+    del Y
+    errs = {}
+    for name, kw in (("plain", dict(tc_digits=3)), ("refined", dict(tc_digits=3, refine=2))):
+        with T.Context(pr.coeffs, n, alpha, beta, 1e-6, opts=T.tctl_default_opts(**kw)) as ctx:
+            x, st, code = ctx.pcg_solve(T.CP.from_numpy(pr.yw, pr.yU))
+        assert code == 0
+        w, U = x.to_numpy()
+        u = np.einsum("j,ij,kj,lj->ikl", w, U[0], U[1], U[2], optimize=True)
+        errs[name] = np.linalg.norm(u - ustar) / np.linalg.norm(ustar)
+        if name == "refined":
+            assert st["refines"] >= 1 and 0.0 <= st["true_rel_res"] <= 1e-6, st
+        else:
+            assert st["refines"] == 0 and st["true_rel_res"] == -1.0
+    assert errs["plain"] <= 1e-6, errs
+    assert errs["refined"] <= 1e-6 and errs["refined"] < errs["plain"], errs
+
+
 def _solve_iters(pr, n, alpha, beta, **kw):
     with T.Context(pr.coeffs, n, alpha, beta, 1e-6, opts=T.tctl_default_opts(**kw)) as ctx:
         x, st, _ = ctx.pcg_solve(T.CP.from_numpy(pr.yw, pr.yU))

@@ -37,7 +37,7 @@ def _bound(A, B, digits, ta, tb):
 @pytest.mark.parametrize("m,n,k,ta,tb", [(300, 77, 1000, False, False), (129, 65, 16, True, False),
                                          (64, 200, 2048, False, True), (1, 1, 5, True, True),
                                          (513, 33, 511, False, False), (40, 700, 37, True, True)])
-@pytest.mark.parametrize("digits", [4, 6])
+@pytest.mark.parametrize("digits", [3, 4, 6])
 def test_tc_gemm_error_bound(ctx, m, n, k, ta, tb, digits):
     rng = np.random.default_rng(m * 7 + n * 3 + k)
     A = rng.standard_normal((k, m) if ta else (m, k)) * np.exp(rng.uniform(-8, 8, (k, 1) if ta else (m, 1)))
