@@ -526,7 +526,6 @@ def _pipe_peaks():
 # of one n = 2048 solve traced alone (profiles/dram_rank_structured_n2048_single_solve.md),
 # keyed by kernel; a kernel missing here has no capture of its current code
 TRAFFIC_PER_LAUNCH = {
-    "dgemm_group_kernel": 1468085,
     "tcg_group_kernel": 58770101,
     "tcg_kernel": 28367633,
     "split_group_kernel": 15342908,
@@ -539,7 +538,6 @@ TRAFFIC_PER_LAUNCH = {
     "ttm3_kernel": 217792,
     "skinny_nn_kernel": 45234534,
     "skinny_tn_kernel": 33656832,
-    "dgemm_kernel": 381087,
     "core_proj_kernel": 632768,
 }
 

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "tctl_internal.cuh"
@@ -336,6 +337,12 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
     gemm_skinny(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     return;
   }
+  if (batch == 1) {
+    // one product: the exact-work kernel of the grouped GEMMs
+    const GemmSpec g{ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc};
+    gemm_group(c, 1, &g);
+    return;
+  }
   const bool small = (m <= 32 && n <= 32);
   const int BM = small ? 32 : 64, BN = small ? 32 : 64;
   const int gx = (m + BM - 1) / BM, gy = (n + BN - 1) / BN;
@@ -432,73 +439,95 @@ struct GArgs {
   GItem it[kGroupMax];
 };
 
+// Grouped FP64 GEMMs with exact work. An item's output is cut into tiles of
+// at most GT x GT; in a tile of P = mt nt outputs thread t takes output t % P
+// and, for P < 256, the k-lane t / P of S = 256 / P lanes that split the CTA's
+// k range (summed in a fixed order at the end). Every FMA is one of the
+// product's: the Grams of the orthonormalisations and truncations have m, n
+// of 5..64 and K = n, where a padded 32 x 32 register tile spent 3-10 times
+// the algorithmic FMAs. This part issues FP64 at 2 FMA/clk/SM, so shared
+// memory (two loads per FMA) has headroom and no register reuse is needed.
+// The next k block is fetched into registers while the current one is used.
+constexpr int GT = 16, GBK = 32;
+
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) dgemm_group_kernel(GArgs g) {
-  constexpr int BM = 32, BN = 32, TM = BM / 16, TN = BN / 16;
-  __shared__ double As[GEMM_BK][BM + 1];
-  __shared__ double Bs[GEMM_BK][BN + 1];
+  __shared__ double As[GBK][GT + 1];
+  __shared__ double Bs[GBK][GT + 1];
+  __shared__ double red[256];
   int item = 0;
   while (item + 1 < g.count && (int)blockIdx.x >= g.it[item + 1].cta0) ++item;
   const GItem &it = g.it[item];
   const int local = blockIdx.x - it.cta0;
   const int split = local % it.splits, tile = local / it.splits;
-  const int row0 = (tile % it.gx) * BM, col0 = (tile / it.gx) * BN;
-  const int m = it.m, n = it.n, k = it.k, lda = it.lda, ldb = it.ldb;
+  const int row0 = (tile % it.gx) * GT, col0 = (tile / it.gx) * GT;
+  const int m = it.m, n = it.n, lda = it.lda, ldb = it.ldb;
   const double *__restrict__ A = it.A;
   const double *__restrict__ B = it.B;
   const int k0 = split * it.kchunk;
-  const int k1 = min(k, k0 + it.kchunk);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[TM][TN];
+  const int k1 = min(it.k, k0 + it.kchunk);
+  const int mt = min(GT, m - row0), nt = min(GT, n - col0), P = mt * nt;
+  const int S = 256 / P;  // k-lanes per output (>= 1)
+  const int t = threadIdx.x;
+  const int o = t % P, s = t / P;
+  const bool active = s < S;
+  const int oi = o % mt, oj = o / mt;
+  // staging: elements e = t and t + 256 of the A block (GT x GBK) and the B block
+  double pa[2], pb[2];
+  auto fetch = [&](int kb) {
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
-  for (int kb = k0; kb < k1; kb += GEMM_BK) {
-    for (int e = threadIdx.x; e < BM * GEMM_BK; e += 256) {
+    for (int h = 0; h < 2; ++h) {
+      const int e = t + 256 * h;
       int i, kk;
-      if (!TA) { i = e % BM; kk = e / BM; } else { kk = e % GEMM_BK; i = e / GEMM_BK; }
+      if (!TA) { i = e % GT; kk = e / GT; } else { kk = e % GBK; i = e / GBK; }
       const int gi = row0 + i, gk = kb + kk;
-      double v = 0.0;
-      if (gi < m && gk < k1) v = TA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda];
-      As[kk][i] = v;
+      pa[h] = (gi < m && gk < k1) ? (TA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda])
+                                  : 0.0;
+      int j;
+      if (!TB) { kk = e % GBK; j = e / GBK; } else { j = e % GT; kk = e / GT; }
+      const int gj = col0 + j;
+      const int gk2 = kb + kk;
+      pb[h] = (gj < n && gk2 < k1) ? (TB ? B[gj + (long long)gk2 * ldb] : B[gk2 + (long long)gj * ldb])
+                                   : 0.0;
     }
-    for (int e = threadIdx.x; e < BN * GEMM_BK; e += 256) {
-      int j, kk;
-      if (!TB) { kk = e % GEMM_BK; j = e / GEMM_BK; } else { j = e % BN; kk = e / BN; }
-      const int gj = col0 + j, gk = kb + kk;
-      double v = 0.0;
-      if (gj < n && gk < k1) v = TB ? B[gj + (long long)gk * ldb] : B[gk + (long long)gj * ldb];
-      Bs[kk][j] = v;
+  };
+  double a0 = 0.0, a1 = 0.0;
+  if (k0 < k1) fetch(k0);
+  for (int kb = k0; kb < k1; kb += GBK) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = t + 256 * h;
+      if (!TA) As[e / GT][e % GT] = pa[h]; else As[e % GBK][e / GBK] = pa[h];
+      if (!TB) Bs[e % GBK][e / GBK] = pb[h]; else Bs[e / GT][e % GT] = pb[h];
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GEMM_BK; ++kk) {
-      double a[TM], bb[TN];
-#pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    if (kb + GBK < k1) fetch(kb + GBK);
+    const int kn = min(GBK, k1 - kb);
+    if (active) {
+      int kk = s;
+      for (; kk + S < kn; kk += 2 * S) {
+        a0 = fma(As[kk][oi], Bs[kk][oj], a0);
+        a1 = fma(As[kk + S][oi], Bs[kk + S][oj], a1);
+      }
+      if (kk < kn) a0 = fma(As[kk][oi], Bs[kk][oj], a0);
     }
     __syncthreads();
   }
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const int gi = row0 + ty + 16 * i, gj = col0 + tx + 16 * j;
-      if (gi >= m || gj >= n) continue;
-      if (it.splits == 1) {
-        double *p = it.C + gi + (long long)gj * it.ldc;
-        *p = (it.beta == 0.0) ? it.alpha * acc[i][j] : fma(it.alpha, acc[i][j], it.beta * *p);
-      } else {
-        it.part[(long long)split * m * n + gi + (long long)gj * m] = acc[i][j];
-      }
-    }
+  double v = a0 + a1;
+  if (S > 1) {
+    red[t] = active ? v : 0.0;
+    __syncthreads();
+    if (active && s == 0)
+      for (int q = 1; q < S; ++q) v += red[o + q * P];
+  }
+  if (!active || s != 0) return;
+  const int gi = row0 + oi, gj = col0 + oj;
+  if (it.splits == 1) {
+    double *p = it.C + gi + (long long)gj * it.ldc;
+    *p = (it.beta == 0.0) ? it.alpha * v : fma(it.alpha, v, it.beta * *p);
+  } else {
+    it.part[(long long)split * m * n + gi + (long long)gj * m] = v;
+  }
 }
 
 // C_i = alpha_i sum_q part_i,q + beta_i C_i for the items with split K, in the
@@ -568,21 +597,23 @@ void gemm_group(Ctx &c, int count, const GemmSpec *spec) {
       it.lda = q.lda;
       it.ldb = q.ldb;
       it.ldc = q.ldc;
-      it.gx = (q.m + 31) / 32;
-      const int tiles = it.gx * ((q.n + 31) / 32);
+      it.gx = (q.m + GT - 1) / GT;
+      const long long tiles = (long long)it.gx * ((q.n + GT - 1) / GT);
+      if (tiles > (1ll << 30)) fail(TCTL_E_ARG, "gemm_group: item too large");
       // the group as a whole aims at about two CTAs per SM; a CTA contracts at
-      // least 4 k-steps of 16, so its fixed costs stay small against its work
+      // least two k blocks of 32, so its fixed costs stay small against its work
       const int target = (kSplitTarget + g.count - 1) / g.count;
       int splits = 1;
-      if (tiles < target && q.k >= 8 * GEMM_BK)
-        splits = std::min((target + tiles - 1) / tiles, q.k / (4 * GEMM_BK));
+      if (tiles < target && q.k >= 4 * GBK)
+        splits = (int)std::min<long long>((target + tiles - 1) / tiles, q.k / (2 * GBK));
       splits = std::max(1, std::min(splits, 256));
       int kchunk = (q.k + splits - 1) / splits;
-      kchunk = ((kchunk + GEMM_BK - 1) / GEMM_BK) * GEMM_BK;
+      kchunk = ((kchunk + GBK - 1) / GBK) * GBK;
       it.splits = (q.k + kchunk - 1) / kchunk;
       it.kchunk = kchunk;
       it.cta0 = ctas;
-      ctas += tiles * it.splits;
+      if ((long long)ctas + tiles * it.splits > (1ll << 31) - 1) fail(TCTL_E_ARG, "gemm_group: grid too large");
+      ctas += (int)(tiles * it.splits);
       it.out0 = outs;
       outs += (long long)q.m * q.n;
       if (it.splits > 1) part_total += (long long)it.splits * q.m * q.n;
@@ -599,6 +630,16 @@ void gemm_group(Ctx &c, int count, const GemmSpec *spec) {
       }
     c.next_flops = flops;
     c.next_bytes = bytes;
+    if (c.prof && c.trace) {
+      // per-shape profile names (TCTL_TRACE=1 with profiling on)
+      std::string nm = std::string("dgroup[") + (ta ? "T" : "N") + (tb ? "T" : "N");
+      for (int t = 0; t < g.count; ++t) {
+        char b[64];
+        std::snprintf(b, sizeof(b), " %dx%dx%d s%d", g.it[t].m, g.it[t].n, g.it[t].k, g.it[t].splits);
+        nm += b;
+      }
+      c.next_tag = c.intern((nm + "]").c_str());
+    }
 #define TCTL_GG(TA_, TB_) LAUNCH(c, (dgemm_group_kernel<TA_, TB_>), ctas, 256, 0, g)
     if (!ta && !tb) TCTL_GG(false, false);
     else if (!ta && tb) TCTL_GG(false, true);
