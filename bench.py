@@ -526,12 +526,6 @@ def _pipe_peaks():
 # of one n = 2048 solve traced alone (profiles/dram_rank_structured_n2048_single_solve.md),
 # keyed by kernel; a kernel missing here has no capture of its current code
 TRAFFIC_PER_LAUNCH = {
-    "tcg_group_kernel": 58770101,
-    "tcg_kernel": 28367633,
-    "split_group_kernel": 15342908,
-    "split_kernel": 7879151,
-    "row_exp_group_kernel": 2550754,
-    "row_exp_kernel": 5928764,
     "rowdot_group_kernel": 48142507,
     "khatri_rao_kernel": 189594,
     "contract_b_kernel": 18571193,

@@ -79,12 +79,88 @@ __device__ __forceinline__ RowPtr row_ptr(const TcOpnd &o, int item, int r) {
 // contiguous in memory.
 constexpr int E_BIAS = 2000, RE_K = 256;
 
+// The digit cuts and the epilogue work on the IEEE-754 fields of the FP64
+// values with integer instructions: this part issues FP64 arithmetic and
+// FP64 conversions at 2 per clock per SM, so a frexp / ldexp / double-to-int
+// per element would bound these kernels by the FP64 pipe.
+
+// Biased exponent code of v: E_BIAS + e with |v| in [2^(e-1), 2^e); 0 for zero,
+// E_NONFINITE for Inf / NaN.
 __device__ __forceinline__ int exp_code(double v) {
-  if (!isfinite(v)) return E_NONFINITE;
-  if (v == 0.0) return 0;
-  int e;
-  frexp(v, &e);
-  return e + E_BIAS;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long man = bits & 0xFFFFFFFFFFFFFull;
+  if (E == 0x7FF) return E_NONFINITE;
+  if (E == 0) {
+    if (man == 0) return 0;
+    return (63 - __clzll((long long)man)) - 1073 + E_BIAS;  // subnormal: man 2^-1074
+  }
+  return E - 1022 + E_BIAS;
+}
+
+// floor(|v| 2^(7D - e)) for |v| < 2^e: the 7D-bit fixed point of |v| / 2^e
+// (truncated), from |v| = m 2^x with m the significand as an integer.
+template <int D>
+__device__ __forceinline__ unsigned long long fixed_point(double v, int e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long man = bits & 0xFFFFFFFFFFFFFull;
+  const unsigned long long m = E ? (man | (1ull << 52)) : man;
+  const int x = E ? E - 1075 : -1074;
+  const int sh = e - 7 * D - x;  // right shift
+  unsigned long long F;
+  if (sh >= 64) F = 0;
+  else if (sh >= 0) F = m >> sh;
+  else F = m << (-sh);  // a subnormal row: m < 2^(e - x), no overflow
+  const unsigned long long cap = (1ull << (7 * D)) - 1;
+  return F < cap ? F : cap;
+}
+
+// BF16 bits of s dg 2^(-7p), dg in [0, 127] (exact: at most 7 significant bits).
+__device__ __forceinline__ uint32_t bf16_digit(uint32_t dg, int p, uint32_t sign) {
+  if (dg == 0) return 0u;
+  const int q = 31 - __clz((int)dg);  // leading bit, 0..6
+  const uint32_t man = (dg << (7 - q)) & 0x7Fu;
+  const uint32_t ex = (uint32_t)(127 + q - 7 * p);
+  return (sign << 15) | (ex << 7) | man;
+}
+
+// t 2^sc as an FP64 number (t rounded to 53 bits, to nearest, ties to even),
+// assembled from its fields; results outside the normal range take the FP64 route.
+__device__ __forceinline__ double scaled_to_double(long long t, int sc) {
+  if (t == 0) return 0.0;
+  const unsigned long long u = t < 0 ? (unsigned long long)(-t) : (unsigned long long)t;
+  int msb = 63 - __clzll((long long)u);
+  unsigned long long mant;  // in [2^52, 2^53)
+  if (msb > 52) {
+    const int drop = msb - 52;
+    mant = u >> drop;
+    const unsigned long long rem = u & ((1ull << drop) - 1), half = 1ull << (drop - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++msb;
+      }
+    }
+  } else {
+    mant = u << (52 - msb);
+  }
+  const int ef = 1023 + msb + sc;
+  if (ef <= 0 || ef >= 2047) return ldexp((double)t, sc);
+  const unsigned long long bits = ((unsigned long long)(t < 0) << 63) |
+                                  ((unsigned long long)ef << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
+// h 2^35 truncated toward zero, for |h| < 2^20 (FP32 fields; |h| < 2^-126 gives 0).
+__device__ __forceinline__ long long fixed35(uint32_t hb) {
+  const int E = (int)((hb >> 23) & 0xFF);
+  if (E == 0) return 0;
+  const long long M = (long long)((hb & 0x7FFFFFu) | 0x800000u);
+  const int sh = E - 115;  // h 2^35 = M 2^(E - 150 + 35)
+  const long long v = sh >= 0 ? (M << sh) : (sh > -32 ? (M >> (-sh)) : 0);
+  return (hb >> 31) ? -v : v;
 }
 
 __device__ __forceinline__ void row_exp_body(const TcOpnd &o, int R, int K, int Rpad,
@@ -155,19 +231,16 @@ __device__ __forceinline__ void split_body(const TcOpnd &o, int R, int K, int Rp
   if (r < R && ec != 0 && ec != E_NONFINITE) {
     const RowPtr x = row_ptr(o, item, r);
     const bool kr = o.q != nullptr;
-    const double cap = ldexp(1.0, 7 * D) - 1.0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = k0 + i;
       const double v = (k < K) ? x.at(k, o.sk, kr) : 0.0;
-      if (v == 0.0) continue;
-      const uint64_t F = (uint64_t)fmin(ldexp(fabs(v), 7 * D - e), cap);  // 7D-bit fixed point
-      const float sg = v < 0.0 ? -1.0f : 1.0f;
+      const unsigned long long F = fixed_point<D>(v, e);  // 7D-bit fixed point (0 for v = 0)
+      const uint32_t sg = (uint32_t)((unsigned long long)__double_as_longlong(v) >> 63);
 #pragma unroll
       for (int p = 0; p < D; ++p) {
-        const int dg = (int)((F >> (7 * (D - 1 - p))) & 127);
-        const __nv_bfloat16 bv = __float2bfloat16_rn(sg * (float)dg * pow2f(-7 * p));
-        w[p][i >> 1] |= (uint32_t)__bfloat16_as_ushort(bv) << (16 * (i & 1));
+        const uint32_t dg = (uint32_t)((F >> (7 * (D - 1 - p))) & 127);
+        w[p][i >> 1] |= bf16_digit(dg, p, sg) << (16 * (i & 1));
       }
     }
   }
@@ -386,14 +459,22 @@ __device__ __forceinline__ void tcg_body(const TcgArgs &a, int mt, int jt, int b
           double v;
           if (ec == E_NONFINITE || fc == E_NONFINITE) v = __longlong_as_double(0x7FF8000000000000ll);
           else if (ec == 0 || fc == 0) v = 0.0;
-          else
-            v = ldexp(((double)__uint_as_float(h0[i]) + (double)__uint_as_float(h1[i])) +
-                          ((double)__uint_as_float(h2[i]) + (double)__uint_as_float(h3[i])),
-                      ec + fc - 2 * E_BIAS - 14);
+          else {
+            // levels 0..2 are exact integers in units of 2^-7L (below 2^24 units); the
+            // levels >= 3 (below 2^3 in value) are taken in units of 2^-35: the sum
+            // t (below 2^60) is exact and rounded once to FP64
+            const long long l0 = __float2int_rn(__uint_as_float(h0[i]));
+            const long long l1 = __float2int_rn(__uint_as_float(h1[i]) * 128.0f);
+            const long long l2 = __float2int_rn(__uint_as_float(h2[i]) * 16384.0f);
+            const long long l3 = fixed35(h3[i]);
+            const long long t = l0 * 34359738368ll + l1 * 268435456ll + l2 * 2097152ll + l3;
+            v = scaled_to_double(t, ec + fc - 2 * E_BIAS - 14 - 35);
+          }
           if (a.nchunk == 1) {
             double *out = a.C + (long long)b * a.cb + (long long)(m % a.cd) * a.cm0 +
                           (long long)(m / a.cd) * a.cm1 + (long long)j * a.cj;
-            *out = (a.beta == 0.0) ? a.alpha * v : fma(a.alpha, v, a.beta * *out);
+            if (a.beta == 0.0) *out = (a.alpha == 1.0) ? v : a.alpha * v;
+            else *out = fma(a.alpha, v, a.beta * *out);
           } else {
             a.part[((long long)(b * a.nchunk + ch) * a.N + j) * a.M + m] = v;
           }

@@ -74,11 +74,32 @@ def test_tc_gemm_zero_rows_and_nan(ctx):
     assert np.all(np.abs(C[ok] - ref) <= _bound(A[ok], B, 6, False, False))
 
 
+@pytest.mark.parametrize("digits", [3, 6])
+def test_tc_gemm_extreme_exponents(ctx, digits):
+    """Rows of A scaled by 2^-1030 (subnormal), 2^-600, 1 and 2^600, columns of B
+    by 1 and 2^400: the digit cut reads exponents and significands from the
+    IEEE-754 fields and the epilogue assembles the result's fields (results
+    from about 2^1000 down to subnormal ones, which take the FP64 route)."""
+    rng = np.random.default_rng(11 + digits)
+    m, n, k = 160, 70, 300
+    A = rng.standard_normal((m, k))
+    B = rng.standard_normal((k, n))
+    sa = np.array([-1030.0, -600.0, 0.0, 600.0])[np.arange(m) % 4]
+    sb = np.array([0.0, 400.0])[np.arange(n) % 2]
+    A = A * np.ldexp(1.0, sa.astype(int))[:, None]
+    B = B * np.ldexp(1.0, sb.astype(int))[None, :]
+    assert np.all(np.abs(A[0::4]) < 2.0 ** -1022)  # subnormal rows
+    ref = A @ B
+    C = ctx.gemm(digits, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    assert np.all(np.isfinite(C))
+    assert np.all(np.abs(C - ref) <= _bound(A, B, digits, False, False))
+
+
 @pytest.mark.parametrize("m,n,k", [(70, 30, 50), (2048, 5, 2048), (3000, 1, 126), (500, 16, 700),
                                    (257, 9, 33)])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
 def test_fp64_path_digits0(ctx, m, n, k, ta, tb):
-    """FP64 FMA kernels (64x64 tiles; skinny kernels for n <= 16) vs numpy."""
+    """FP64 FMA kernels (exact-work 16 x 16 output tiles; skinny kernels for n <= 16) vs numpy."""
     rng = np.random.default_rng(m + 10 * n + 100 * k)
     A = rng.standard_normal((k, m) if ta else (m, k))
     B = rng.standard_normal((n, k) if tb else (k, n))
