@@ -718,7 +718,7 @@ void scale_cols(Ctx &c, int n, int m, double *A, int lda, const double *s, bool 
   LAUNCH(c, scale_cols_kernel, blocks, 256, 0, n, m, A, lda, s, inverse ? 1 : 0);
 }
 
-// splitmix64 counter hash -> two uniforms -> Box-Muller normal
+// splitmix64 counter hash -> two uniforms -> Box-Muller normal (gauss_draw)
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z += 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -726,15 +726,22 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+// Draw r of stream `seed`. The probes of the randomized range finder need
+// Gaussian directions, not FP64-accurate samples: the Box-Muller transform runs
+// in FP32 (24-bit uniforms; FP64 log / sqrt / cospi would cost tens of FP64
+// operations per draw on this part) and the result is widened to FP64.
+__device__ __forceinline__ double gauss_draw(uint64_t seed, uint64_t r) {
+  const uint64_t h1 = mix64(seed ^ mix64(2 * r));
+  const uint64_t h2 = mix64(seed ^ mix64(2 * r + 1));
+  const float u1 = ((float)(uint32_t)(h1 >> 40) + 1.0f) * (1.0f / 16777216.0f);  // (0, 1]
+  const float u2 = (float)(uint32_t)(h2 >> 40) * (1.0f / 16777216.0f);           // [0, 1)
+  return (double)(sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2));
+}
+
 __global__ void gaussian_kernel(double *x, size_t count, uint64_t seed) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const uint64_t h1 = mix64(seed ^ mix64(2 * t));
-    const uint64_t h2 = mix64(seed ^ mix64(2 * t + 1));
-    const double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
-    const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);          // [0, 1)
-    x[t] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
-  }
+       t += (size_t)gridDim.x * blockDim.x)
+    x[t] = gauss_draw(seed, t);
 }
 
 void fill_gaussian(Ctx &c, double *x, size_t count, uint64_t seed) {
@@ -759,11 +766,7 @@ __global__ void gaussian_multi_kernel(GaussArgs a) {
     int i = 0;
     while (i + 1 < a.count && t >= a.off[i + 1]) ++i;
     const uint64_t r = (uint64_t)(t - a.off[i]);
-    const uint64_t h1 = mix64(a.seed[i] ^ mix64(2 * r));
-    const uint64_t h2 = mix64(a.seed[i] ^ mix64(2 * r + 1));
-    const double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
-    const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);          // [0, 1)
-    a.x[i][r] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    a.x[i][r] = gauss_draw(a.seed[i], r);
   }
 }
 
@@ -1256,22 +1259,50 @@ __global__ void orth_check_multi_kernel(OcBatch b, double tol) {
 }
 
 // Q[i, :] = Y[i, perm] L^{-T}: forward substitution per row (x L^T = y).
+// Q[i, :] solves Q[i, :] L^T = Y[i, perm] (row i independent), one thread per
+// row. Columns go in blocks of 8: the contributions of the solved columns to a
+// block are 8 independent FMA chains that share each loaded x_k, and the
+// diagonal is applied through its reciprocal (one FP64 division per column and
+// block instead of per row: this part's FP64 pipe issues 2 FMA per clock per SM).
 __device__ __forceinline__ void trsm_rows_body(int n, int r, const double *__restrict__ Y, int ldy,
                                                const int *__restrict__ perm,
                                                const double *__restrict__ Lg, double *__restrict__ Q,
                                                int ldq, int bx, int gx) {
   __shared__ double L[JMAX][JMAX + 1];
+  __shared__ double inv[JMAX];
   __shared__ int pm[JMAX];
   for (int t = threadIdx.x; t < r * r; t += blockDim.x) L[t % r][t / r] = Lg[(t % r) + (t / r) * JMAX];
-  for (int t = threadIdx.x; t < r; t += blockDim.x) pm[t] = perm[t];
+  for (int t = threadIdx.x; t < r; t += blockDim.x) {
+    pm[t] = perm[t];
+    inv[t] = 1.0 / Lg[t + t * JMAX];
+  }
   __syncthreads();
+  constexpr int JB = 8;
   for (int i = bx * blockDim.x + threadIdx.x; i < n; i += gx * blockDim.x) {
     double x[JMAX];
 #pragma unroll 1
-    for (int j = 0; j < r; ++j) {
-      double s = Y[i + (long long)pm[j] * ldy];
-      for (int k = 0; k < j; ++k) s -= x[k] * L[j][k];
-      x[j] = s / L[j][j];
+    for (int j0 = 0; j0 < r; j0 += JB) {
+      const int nb = min(JB, r - j0);
+      double sb[JB];
+#pragma unroll
+      for (int q = 0; q < JB; ++q) sb[q] = q < nb ? Y[i + (long long)pm[j0 + q] * ldy] : 0.0;
+#pragma unroll 1
+      for (int k = 0; k < j0; ++k) {
+        const double xk = x[k];
+#pragma unroll
+        for (int q = 0; q < JB; ++q) sb[q] = fma(-xk, L[j0 + q < r ? j0 + q : 0][k], sb[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < JB; ++q) {
+        if (q < nb) {
+#pragma unroll
+          for (int q2 = 0; q2 < q; ++q2) sb[q] = fma(-sb[q2], L[j0 + q][j0 + q2], sb[q]);
+          sb[q] *= inv[j0 + q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < JB; ++q)
+        if (q < nb) x[j0 + q] = sb[q];
     }
 #pragma unroll 1
     for (int j = 0; j < r; ++j) Q[i + (long long)j * ldq] = x[j];

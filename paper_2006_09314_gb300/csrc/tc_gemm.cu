@@ -780,6 +780,12 @@ void run_tcg(Ctx &c, int M, int N, int K, int batch, int divA, int divB, double 
   dim3 grid(Mt, Nt, batch * nchunk);
   c.next_flops = 2.0 * M * (double)N * K * batch;
   c.next_mma = (D * (D + 1) / 2) * c.next_flops;  // digit products with p + q <= D - 1
+  if (c.prof && c.trace) {
+    // per-shape profile names (TCTL_TRACE=1 with profiling on)
+    char nm[96];
+    std::snprintf(nm, sizeof(nm), "tcg[%dx%dx%d b%d c%d]", M, N, K, batch, nchunk);
+    c.next_tag = c.intern(nm);
+  }
   constexpr int smem_bytes = tcg_smem<D, NST>();
   LAUNCH(c, (tcg_kernel<D, NST>), grid, NTHREADS, smem_bytes, ar);
   if (nchunk > 1) {
@@ -952,6 +958,16 @@ void run_tcg_group(Ctx &c, int count, const TcItem *items) {
   g.cta0[count] = ctas;
   c.next_flops = flops;
   c.next_mma = (D * (D + 1) / 2) * flops;
+  if (c.prof && c.trace) {
+    std::string nm = "tcgroup[";
+    for (int i = 0; i < count; ++i) {
+      char b[64];
+      std::snprintf(b, sizeof(b), "%s%dx%dx%d c%d", i ? " " : "", items[i].M, items[i].N, items[i].K,
+                    g.it[i].nchunk);
+      nm += b;
+    }
+    c.next_tag = c.intern((nm + "]").c_str());
+  }
   constexpr int smem_bytes = tcg_smem<D, NST>();
   LAUNCH(c, (tcg_group_kernel<D, NST>), ctas, NTHREADS, smem_bytes, g);
   long long outs = 0;

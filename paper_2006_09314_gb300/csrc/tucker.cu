@@ -670,6 +670,35 @@ void tucker_factor_change(Ctx &c, Tucker &x, double *const M[3], bool transpose)
   c.ws.reset(mk);
 }
 
+// Y_l = op(V_l) X_l (n x m_l, contracted over the grid index) for the three
+// modes: the boundary basis changes into and out of the eigenbasis (Section
+// 3.3). With the tensor-core contractions they run as one grouped digit-split
+// launch (6 digits; V_l's planes cut once per orientation and kept by the
+// context) however narrow X_l is: the padded 128 x 64 tiles cost far less than
+// the FP64 product on this part. FP64 otherwise.
+static void basis_change3(Ctx &c, bool transpose_v, const int m[3], double *const X[3],
+                          double *const Y[3]) {
+  const int n = c.n;
+  bool tc = c.o.tc_gemm != 0;
+  for (int l = 0; l < 3 && tc; ++l) tc = m[l] <= 0 || ((n + 127) / 128 <= 65535 && m[l] <= 65535 * 64);
+  if (!tc) {
+    for (int l = 0; l < 3; ++l)
+      if (m[l] > 0)
+        gemm(c, transpose_v, false, n, m[l], n, 1.0, c.V[l], n, 0, X[l], n, 0, 0.0, Y[l], n, 0);
+    return;
+  }
+  std::vector<TcItem> items;
+  for (int l = 0; l < 3; ++l) {
+    if (m[l] <= 0) continue;
+    // op(V)(i, k) = transpose_v ? V[k + i n] : V[i + k n];  op(X)(k, j) = X[k + j n]
+    TcOpnd v{c.V[l], transpose_v ? (long long)n : 1ll, 0, transpose_v ? 1ll : (long long)n, 0, 1 << 30};
+    v.keep = true;
+    const TcOpnd x{X[l], (long long)n, 0, 1, 0, 1 << 30};
+    items.push_back(TcItem{n, m[l], n, v, x, 1.0, 0.0, Y[l], 1, 0, 1 << 30, (long long)n});
+  }
+  gemm_tc_group(c, 6, (int)items.size(), items.data());
+}
+
 void cp_to_tucker(Ctx &c, int m, const double *w, double *const U[3], bool to_eig, Tucker &out,
                   double eps_core) {
   const int n = c.n;
@@ -682,10 +711,13 @@ void cp_to_tucker(Ctx &c, int m, const double *w, double *const U[3], bool to_ei
   double *X[3], *nu[3];
   for (int l = 0; l < 3; ++l) {
     X[l] = c.ws.dbl((size_t)n * m);
-    if (to_eig)
-      gemm(c, true, false, n, m, n, 1.0, c.V[l], n, 0, U[l], n, 0, 0.0, X[l], n, 0);
-    else
-      copy_d(c, X[l], U[l], (size_t)n * m);
+    if (!to_eig) copy_d(c, X[l], U[l], (size_t)n * m);
+  }
+  if (to_eig) {
+    const int mm[3] = {m, m, m};
+    basis_change3(c, true, mm, U, X);
+  }
+  for (int l = 0; l < 3; ++l) {
     nu[l] = c.ws.dbl(m);
     col_norms(c, n, m, X[l], n, nu[l]);
   }
@@ -1121,11 +1153,9 @@ int tucker_to_cp(Ctx &c, const Tucker &x, bool from_eig, double eps, tctl_cp *y)
   double *Qp[3];
   for (int l = 0; l < 3; ++l) {
     Qp[l] = c.ws.dbl((size_t)n * x.r[l]);
-    if (from_eig)
-      gemm(c, false, false, n, x.r[l], n, 1.0, c.V[l], n, 0, x.Q[l], n, 0, 0.0, Qp[l], n, 0);
-    else
-      copy_d(c, Qp[l], x.Q[l], (size_t)n * x.r[l]);
+    if (!from_eig) copy_d(c, Qp[l], x.Q[l], (size_t)n * x.r[l]);
   }
+  if (from_eig) basis_change3(c, false, x.r, x.Q, Qp);
   // slice Grams S_c^T S_c (r1 x r1), batch r2
   double *G = c.ws.dbl((size_t)r1 * r1 * r2);
   gemm(c, true, false, r1, r1, r0, 1.0, x.core, r0, (long long)r0 * r1, x.core, r0,
