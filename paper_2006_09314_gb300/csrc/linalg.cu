@@ -1259,11 +1259,14 @@ __global__ void orth_check_multi_kernel(OcBatch b, double tol) {
 }
 
 // Q[i, :] = Y[i, perm] L^{-T}: forward substitution per row (x L^T = y).
-// Q[i, :] solves Q[i, :] L^T = Y[i, perm] (row i independent), one thread per
-// row. Columns go in blocks of 8: the contributions of the solved columns to a
-// block are 8 independent FMA chains that share each loaded x_k, and the
-// diagonal is applied through its reciprocal (one FP64 division per column and
-// block instead of per row: this part's FP64 pipe issues 2 FMA per clock per SM).
+// Q[i, :] solves Q[i, :] L^T = Y[i, perm] (row i independent), four lanes per
+// row (blockDim / 4 rows per block). Columns go in blocks of 8, two per lane:
+// a lane sums the contributions of the solved columns to its two, then the 8
+// x values of the block are formed one by one by their owner and broadcast to
+// the other three lanes (each keeps a full copy of the row's x). The diagonal
+// is applied through its reciprocal. Four lanes per row give the 3 x n rows of
+// a batch enough warps to keep every SM sub-partition's FP64 unit busy (this
+// part issues 2 FP64 FMA per clock per SM).
 __device__ __forceinline__ void trsm_rows_body(int n, int r, const double *__restrict__ Y, int ldy,
                                                const int *__restrict__ perm,
                                                const double *__restrict__ Lg, double *__restrict__ Q,
@@ -1278,34 +1281,37 @@ __device__ __forceinline__ void trsm_rows_body(int n, int r, const double *__res
   }
   __syncthreads();
   constexpr int JB = 8;
-  for (int i = bx * blockDim.x + threadIdx.x; i < n; i += gx * blockDim.x) {
+  const int lane = threadIdx.x & 31, cl = lane & 3, grp = lane & ~3;
+  const int rows = blockDim.x >> 2;
+  for (int base = bx * rows; base < n; base += gx * rows) {
+    const int i = base + (threadIdx.x >> 2);
+    const bool ok = i < n;
     double x[JMAX];
 #pragma unroll 1
     for (int j0 = 0; j0 < r; j0 += JB) {
       const int nb = min(JB, r - j0);
-      double sb[JB];
-#pragma unroll
-      for (int q = 0; q < JB; ++q) sb[q] = q < nb ? Y[i + (long long)pm[j0 + q] * ldy] : 0.0;
-#pragma unroll 1
+      const int c0 = 2 * cl, c1 = 2 * cl + 1;  // this lane's columns j0 + c0, j0 + c1
+      const int l0 = min(j0 + c0, r - 1), l1 = min(j0 + c1, r - 1);
+      double s0 = (ok && c0 < nb) ? Y[i + (long long)pm[j0 + c0] * ldy] : 0.0;
+      double s1 = (ok && c1 < nb) ? Y[i + (long long)pm[j0 + c1] * ldy] : 0.0;
+#pragma unroll 4
       for (int k = 0; k < j0; ++k) {
         const double xk = x[k];
-#pragma unroll
-        for (int q = 0; q < JB; ++q) sb[q] = fma(-xk, L[j0 + q < r ? j0 + q : 0][k], sb[q]);
+        s0 = fma(-xk, L[l0][k], s0);
+        s1 = fma(-xk, L[l1][k], s1);
       }
-#pragma unroll
-      for (int q = 0; q < JB; ++q) {
-        if (q < nb) {
-#pragma unroll
-          for (int q2 = 0; q2 < q; ++q2) sb[q] = fma(-sb[q2], L[j0 + q][j0 + q2], sb[q]);
-          sb[q] *= inv[j0 + q];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < JB; ++q)
-        if (q < nb) x[j0 + q] = sb[q];
-    }
 #pragma unroll 1
-    for (int j = 0; j < r; ++j) Q[i + (long long)j * ldq] = x[j];
+      for (int q = 0; q < nb; ++q) {
+        const double v = ((q & 1) ? s1 : s0) * inv[j0 + q];
+        const double xq = __shfl_sync(0xffffffffu, v, grp + (q >> 1));
+        x[j0 + q] = xq;
+        if (c0 > q) s0 = fma(-xq, L[l0][j0 + q], s0);
+        if (c1 > q) s1 = fma(-xq, L[l1][j0 + q], s1);
+      }
+    }
+    if (ok)
+#pragma unroll 1
+      for (int j = cl; j < r; j += 4) Q[i + (long long)j * ldq] = x[j];
   }
 }
 
@@ -1344,7 +1350,7 @@ int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relati
   int *perm = c.ws.i32(JMAX);
   int *rdev = c.ws.i32(4);
   double *Q2 = c.ws.dbl((size_t)n * std::min(m, rcap > 0 ? rcap : 1));
-  // one warp per block: each thread solves one row, so n rows spread over n/32 SMs
+  // 32 rows per block of 128 threads (four lanes per row)
   const int blocks = std::min((n + 31) / 32, 4096);
   auto read_int = [&](const int *p) {
     int v = 0;
@@ -1356,7 +1362,7 @@ int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relati
   LAUNCH(c, pivchol_kernel, 1, 256, 0, m, G, tol, relative ? 1 : 0, rcap, perm, L, rdev);
   int r = read_int(rdev);
   if (r > 0) {
-    LAUNCH(c, trsm_rows_kernel, blocks, 32, 0, n, r, Y, ldy, perm, L, Q, n);
+    LAUNCH(c, trsm_rows_kernel, blocks, 128, 0, n, r, Y, ldy, perm, L, Q, n);
     // passes 2 and 3 (Cholesky QR on the result) restore orthogonality to rounding
     // level; a column whose residual has fallen to rounding noise (kept in pass 1 at
     // the edge of the tolerance) is dropped here instead of breaking the factorization.
@@ -1370,7 +1376,7 @@ int orth(Ctx &c, int n, int m, const double *Y, int ldy, double tol, bool relati
       LAUNCH(c, pivchol_kernel, 1, 256, 0, r, G, 1e-10, 1, r, perm, L, rdev);
       const int r2 = read_int(rdev);
       if (r2 > 0) {
-        LAUNCH(c, trsm_rows_kernel, blocks, 32, 0, n, r2, Q, n, perm, L, Q2, n);
+        LAUNCH(c, trsm_rows_kernel, blocks, 128, 0, n, r2, Q, n, perm, L, Q2, n);
         copy_d(c, Q, Q2, (size_t)n * r2);
       }
       r = r2;
@@ -1415,7 +1421,7 @@ void orth_multi(Ctx &c, int count, int n, const int *m, double *const *Y, const 
   auto trsm_all = [&](const std::vector<const double *> &src, const std::vector<int> &ld,
                       const std::vector<int> &rk, const std::vector<double *> &dst) {
     for (int i = 0; i < count; ++i) ht.d[i] = TrDesc{src[i], ld[i], rk[i], perm[i], L[i], dst[i]};
-    LAUNCH(c, trsm_rows_multi_kernel, dim3(blocks, count), 32, 0, n, ht);
+    LAUNCH(c, trsm_rows_multi_kernel, dim3(blocks, count), 128, 0, n, ht);
   };
   // pass 1: pivoted Cholesky of Y^T Y picks the columns and the ranks
   std::vector<int> mm(m, m + count), cap(count);
