@@ -230,15 +230,16 @@ __global__ void twisted_kernel(int n, const double *d0, const double *d1, const 
 // ------------------------------------------------------------------ set-up eigensolver
 // The set-up path spends its FP64 work (GB300: 2 FP64 FMA per clock per SM)
 // on few inertia counts: per eigenvalue,
-//   1. an FP32 Sturm bisection inside the Courant-Fischer bracket gives a
-//      guess (the FP32 pipe is ~64x the FP64 one; its counts are only a guess);
+//   1. an FP32 Sturm trisection inside the Courant-Fischer bracket (the two
+//      lanes of the eigenpair count at the two inner points) gives a guess
+//      (the FP32 pipe is ~64x the FP64 one; its counts are only a guess);
 //   2. Rayleigh-quotient iteration on twisted factorizations in FP64: the
 //      factorization of T - sigma I with twist r gives (T - sigma I) z = gamma_r e_r
 //      (z_r = 1), so z^T (T - sigma I) z / z^T z = gamma_r / ||z||^2 and
 //      sigma + gamma_r / ||z||^2 is the Rayleigh quotient of z (cubic
 //      convergence); the inertia of the same factorization (signs of D+)
 //      shrinks a safeguarding bracket, and a step leaving it is a bisection;
-//   3. two FP64 inertia counts at lambda -+ tau confirm the index k; if they
+//   3. two FP64 inertia counts at lambda -+ tau (one per lane) confirm the index k; if they
 //      do not (or the iteration does not settle), the eigenvalue is bisected
 //      in FP64 from the Courant-Fischer bracket as before.
 // The eigenvector is the normalised z of the last factorization.
@@ -246,7 +247,7 @@ __global__ void twisted_kernel(int n, const double *d0, const double *d1, const 
 #ifndef TCTL_EIG_BLOCK
 #define TCTL_EIG_BLOCK 32
 #endif
-constexpr int kEigBlock = TCTL_EIG_BLOCK;  // threads (eigenpairs) per block, a power of two <= 64
+constexpr int kEigBlock = TCTL_EIG_BLOCK;  // threads per block (two per eigenpair), a power of two <= 64
 
 // FP32 copies of d and e^2 (the guess phase), e^2 in FP64, the Weyl sign weights.
 __global__ void eig_prep_kernel(int n, const double *d0, const double *d1, const double *d2,
@@ -318,57 +319,103 @@ struct Twist {
   double nrm2;  // ||z||^2 with z_r = 1
 };
 
-// Twisted factorization of T - sigma I. Forward multipliers L_i = e_i / D+_i and
-// backward ones U_i = e_i / D-_{i+1} go to L[i * ld], U[i * ld] (ld = n: the
-// threads of a warp, consecutive eigenvalues, touch consecutive words).
-__device__ Twist twisted64(int n, const double *__restrict__ d, const double *__restrict__ e,
-                           double sigma, double pivmin, double *__restrict__ L,
-                           double *__restrict__ U, int ld) {
-  Twist t;
-  double dplus = d[0] - sigma;
-  if (fabs(dplus) < pivmin) dplus = pivmin;
-  int cnt = dplus < 0.0;
-  for (int i = 0; i < n - 1; ++i) {
-    const double Li = e[i] * rcp_nr(dplus);
-    L[(size_t)i * ld] = Li;
-    dplus = fma(-Li, e[i], d[i + 1] - sigma);
-    if (fabs(dplus) < pivmin) dplus = pivmin;
-    cnt += dplus < 0.0;
+// The two lanes (2j, 2j + 1 of a warp) of one eigenpair run the same
+// instructions on mirrored data: side 0 the forward recurrence of the twisted
+// factorization over i = 0, 1, ..., side 1 the backward one over
+// i = n - 1, n - 2, ... (the backward recurrence is the forward one of the
+// reversed tridiagonal), so the warp does not diverge; values cross between the
+// two lanes by shuffles. Each warp instruction of the FP64 pipe costs tens of
+// cycles on this part, so the chain of one eigenpair, not the total work, sets
+// the time: two lanes halve the sweeps' part of it.
+struct Pair {
+  unsigned mask;  // the pair's two lanes
+  int side;       // 0: forward, 1: backward
+};
+
+__device__ __forceinline__ double xchg(const Pair &p, double v) { return __shfl_xor_sync(p.mask, v, 1); }
+__device__ __forceinline__ int xchg(const Pair &p, int v) { return __shfl_xor_sync(p.mask, v, 1); }
+
+__device__ __forceinline__ double piv(double q, double pivmin) { return fabs(q) < pivmin ? pivmin : q; }
+
+// Twisted factorization of T - sigma I by the pair: side 0 the forward
+// multipliers L_i = e_i / D+_i (to L[i ld]) and the inertia count, side 1 the
+// backward ones U_i = e_i / D-_{i+1} (to U[i ld]); then each side scans half of
+// the twist candidates gamma_i = D+_i + D-_i - (d_i - sigma) (gamma_{n-1} =
+// D+_{n-1}; both pivots re-formed from the stored multipliers by the sweeps'
+// own operations; the smallest |gamma| wins, ties to the larger index) and sums
+// ||z||^2 over its part of z (z_r = 1, z_i = -L_i z_{i+1} for i < r, z_{i+1} =
+// -U_i z_i for i >= r). Both lanes return the same Twist.
+__device__ Twist twisted_pair(const Pair &pr, int n, const double *__restrict__ d,
+                              const double *__restrict__ e, double sigma, double pivmin,
+                              double *__restrict__ L, double *__restrict__ U, int ld) {
+  const int s = pr.side;
+  double *Mo = s ? U : L;
+  double p = piv(d[s ? n - 1 : 0] - sigma, pivmin);
+  int cnt = p < 0.0;
+  for (int t = 0; t < n - 1; ++t) {
+    const int ie = s ? n - 2 - t : t;
+    const int id = s ? n - 2 - t : t + 1;
+    const double m = e[ie] * rcp_nr(p);
+    Mo[(size_t)ie * ld] = m;
+    p = piv(fma(-m, e[ie], d[id] - sigma), pivmin);
+    cnt += p < 0.0;
   }
-  t.cnt = cnt;
-  t.r = n - 1;
-  t.gam = dplus;  // gamma_{n-1} = D+_{n-1}
-  double gbest = fabs(dplus);
-  double dminus = d[n - 1] - sigma;
-  if (fabs(dminus) < pivmin) dminus = pivmin;
-  for (int i = n - 2; i >= 0; --i) {
-    const double Ui = e[i] * rcp_nr(dminus);
-    U[(size_t)i * ld] = Ui;
+  __syncwarp(pr.mask);  // each lane reads the other's multipliers below
+  Twist t;
+  const int ocnt = xchg(pr, cnt);
+  t.cnt = s ? ocnt : cnt;              // side 0's inertia count
+  const double op = xchg(pr, p);
+  const double dplus_last = s ? op : p;  // D+_{n-1}
+  // candidates: side 0 takes i in [0, h), side 1 [h, n)
+  const int h = n / 2;
+  const int i0 = s ? h : 0, i1 = s ? n : h;
+  double best = 1e308, bgam = 0.0;
+  int br = -1;
+  for (int i = i0; i < i1; ++i) {
     const double ci = d[i] - sigma;
-    dminus = fma(-Ui, e[i], ci);
-    if (fabs(dminus) < pivmin) dminus = pivmin;
-    // D+_i again, from the stored multiplier (same operations as the forward pass)
-    double dp = i == 0 ? ci : fma(-L[(size_t)(i - 1) * ld], e[i - 1], ci);
-    if (fabs(dp) < pivmin) dp = pivmin;
-    const double gam = dp + dminus - ci;
-    if (fabs(gam) < gbest) {
-      gbest = fabs(gam);
-      t.r = i;
-      t.gam = gam;
+    double gam;
+    if (i == n - 1) {
+      gam = dplus_last;
+    } else {
+      const double dp = i == 0 ? piv(ci, pivmin) : piv(fma(-L[(size_t)(i - 1) * ld], e[i - 1], ci), pivmin);
+      const double dm = piv(fma(-U[(size_t)i * ld], e[i], ci), pivmin);
+      gam = dp + dm - ci;
+    }
+    if (fabs(gam) <= best) {
+      best = fabs(gam);
+      bgam = gam;
+      br = i;
     }
   }
-  // ||z||^2: z_r = 1, z_i = -L_i z_{i+1} (i < r), z_{i+1} = -U_i z_i (i >= r)
-  double zi = 1.0, nrm2 = 1.0;
-  for (int i = t.r - 1; i >= 0; --i) {
-    zi = -L[(size_t)i * ld] * zi;
-    nrm2 = fma(zi, zi, nrm2);
+  {
+    const double ob = xchg(pr, best), og = xchg(pr, bgam);
+    const int orr = xchg(pr, br);
+    const double b0 = s ? ob : best, b1 = s ? best : ob;
+    const double g0 = s ? og : bgam, g1 = s ? bgam : og;
+    const int r0 = s ? orr : br, r1 = s ? br : orr;
+    if (r1 >= 0 && (r0 < 0 || b1 <= b0)) {
+      t.r = r1;
+      t.gam = g1;
+    } else {
+      t.r = r0;
+      t.gam = g0;
+    }
+    if (t.r < 0) {  // no finite candidate: the last index, as an unscanned factorization would give
+      t.r = n - 1;
+      t.gam = dplus_last;
+    }
   }
-  zi = 1.0;
-  for (int i = t.r; i < n - 1; ++i) {
-    zi = -U[(size_t)i * ld] * zi;
-    nrm2 = fma(zi, zi, nrm2);
+  // ||z||^2
+  const int len = s ? n - 1 - t.r : t.r;
+  double z = 1.0, acc = 0.0;
+  for (int q = 0; q < len; ++q) {
+    const int i = s ? t.r + q : t.r - 1 - q;
+    z = -Mo[(size_t)i * ld] * z;
+    acc = fma(z, z, acc);
   }
-  t.nrm2 = nrm2;
+  const double other = xchg(pr, acc);
+  const double left = s ? other : acc, right = s ? acc : other;
+  t.nrm2 = (1.0 + left) + right;
   return t;
 }
 
@@ -413,8 +460,12 @@ __global__ void eig_rqi_kernel(int n, const double *d0, const double *d1, const 
   }
   amin = s_min[0];
   amax = s_max[0];
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  // two lanes per eigenpair (see Pair); a pair's lanes return together
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = gt >> 1;
   if (k >= n) return;
+  const Pair pr{3u << (threadIdx.x & 30), (int)(threadIdx.x & 1)};
+  const int side = pr.side;
   double blo = glo, bhi = ghi;
   if (amin > 0.0) {
     const double sn = sin(0.5 * M_PI * h * (k + 1));
@@ -427,13 +478,23 @@ __global__ void eig_rqi_kernel(int n, const double *d0, const double *d1, const 
   }
   double *Lk = Lscr + (size_t)l * n * n + k;
   double *Uk = Uscr + (size_t)l * n * n + k;
-  // 1. FP32 guess
+  // 1. FP32 guess by trisection: the two lanes count at the two inner points
   float flo = (float)blo, fhi = (float)bhi;
   for (int it = 0; it < 64; ++it) {
-    const float mid = 0.5f * (flo + fhi);
-    if (mid <= flo || mid >= fhi) break;
     if (fhi - flo <= 4.0f * FLT_EPSILON * fmaxf(fabsf(flo), fabsf(fhi))) break;
-    if (count32(n, d32, ee32, mid, pivmin32) > k) fhi = mid; else flo = mid;
+    const float w = fhi - flo;
+    const float m1 = flo + w * (1.0f / 3.0f), m2 = flo + w * (2.0f / 3.0f);
+    if (!(m1 > flo && m2 > m1 && m2 < fhi)) break;
+    const int cmine = count32(n, d32, ee32, side ? m2 : m1, pivmin32);
+    const int cother = xchg(pr, cmine);
+    const int c1 = side ? cother : cmine, c2 = side ? cmine : cother;
+    if (c1 > k) fhi = m1;
+    else if (c2 > k) {
+      flo = m1;
+      fhi = m2;
+    } else {
+      flo = m2;
+    }
   }
   // 2. Rayleigh-quotient iteration, safeguarded by [lo, hi] (shrunk by every inertia)
   double lo = blo, hi = bhi;
@@ -442,7 +503,7 @@ __global__ void eig_rqi_kernel(int n, const double *d0, const double *d1, const 
   Twist t{};
   bool ok = false;
   for (int it = 0; it < 10; ++it) {
-    t = twisted64(n, d, e, sigma, pivmin, Lk, Uk, n);
+    t = twisted_pair(pr, n, d, e, sigma, pivmin, Lk, Uk, n);
     if (t.cnt <= k) lo = fmax(lo, sigma); else hi = fmin(hi, sigma);
     const double delta = t.gam / t.nrm2;
     if (fabs(delta) <= 2.0 * DBL_EPSILON * fabs(sigma) + 8.0 * DBL_EPSILON * gnorm) {
@@ -455,12 +516,17 @@ __global__ void eig_rqi_kernel(int n, const double *d0, const double *d1, const 
     sigma = sn;
   }
   // 3. the index: exactly k eigenvalues below lambda - tau, k + 1 below lambda + tau
+  //    (one count per lane)
   if (ok) {
     const double tau = 64.0 * DBL_EPSILON * gnorm + 4.0 * DBL_EPSILON * fabs(lamk);
-    ok = count64(n, d, ee, lamk - tau, pivmin) <= k && count64(n, d, ee, lamk + tau, pivmin) > k;
+    const int cm = count64(n, d, ee, side ? lamk + tau : lamk - tau, pivmin);
+    const int co = xchg(pr, cm);
+    const int cminus = side ? co : cm, cplus = side ? cm : co;
+    ok = cminus <= k && cplus > k;
   }
   if (!ok) {
-    // FP64 bisection from the Courant-Fischer bracket (Gershgorin if it fails)
+    // FP64 bisection from the Courant-Fischer bracket (Gershgorin if it fails);
+    // both lanes take the same steps (a rare path)
     lo = blo;
     hi = bhi;
     if (!(count64(n, d, ee, lo, pivmin) <= k && count64(n, d, ee, hi, pivmin) > k)) {
@@ -474,34 +540,30 @@ __global__ void eig_rqi_kernel(int n, const double *d0, const double *d1, const 
       if (count64(n, d, ee, mid, pivmin) > k) hi = mid; else lo = mid;
     }
     lamk = 0.5 * (lo + hi);
-    t = twisted64(n, d, e, lamk, pivmin, Lk, Uk, n);
-    atomicAdd(fallbacks, 1);
+    t = twisted_pair(pr, n, d, e, lamk, pivmin, Lk, Uk, n);
+    if (side == 0) atomicAdd(fallbacks, 1);
   }
-  lam[k] = lamk;
-  // eigenvector: z of the last factorization, unit norm, sum_i z_i g_i > 0
-  double dot = 0.0, zi = 1.0;
-  for (int i = t.r - 1; i >= 0; --i) {
-    zi = -Lk[(size_t)i * n] * zi;
-    dot = fma(zi, g[i], dot);
+  if (side == 0) lam[k] = lamk;
+  // eigenvector: z of the last factorization, unit norm, sum_i z_i g_i > 0;
+  // side 0 forms z_i for i <= r (from L), side 1 for i > r (from U)
+  const int len = side ? n - 1 - t.r : t.r;
+  const double *Mk = side ? Uk : Lk;
+  double dot = side ? 0.0 : g[t.r], zi = 1.0;
+  for (int q = 0; q < len; ++q) {
+    const int i = side ? t.r + q : t.r - 1 - q;
+    zi = -Mk[(size_t)i * n] * zi;
+    dot = fma(zi, g[side ? i + 1 : i], dot);
   }
-  dot = fma(1.0, g[t.r], dot);
-  zi = 1.0;
-  for (int i = t.r; i < n - 1; ++i) {
-    zi = -Uk[(size_t)i * n] * zi;
-    dot = fma(zi, g[i + 1], dot);
-  }
-  const double sc = (dot < 0.0 ? -1.0 : 1.0) / sqrt(t.nrm2);
+  const double odot = xchg(pr, dot);
+  const double tot = side ? odot + dot : dot + odot;
+  const double sc = (tot < 0.0 ? -1.0 : 1.0) / sqrt(t.nrm2);
   double *z = V + (size_t)k * n;
+  if (side == 0) z[t.r] = sc;
   zi = 1.0;
-  for (int i = t.r - 1; i >= 0; --i) {
-    zi = -Lk[(size_t)i * n] * zi;
-    z[i] = zi * sc;
-  }
-  z[t.r] = sc;
-  zi = 1.0;
-  for (int i = t.r; i < n - 1; ++i) {
-    zi = -Uk[(size_t)i * n] * zi;
-    z[i + 1] = zi * sc;
+  for (int q = 0; q < len; ++q) {
+    const int i = side ? t.r + q : t.r - 1 - q;
+    zi = -Mk[(size_t)i * n] * zi;
+    z[side ? i + 1 : i] = zi * sc;
   }
 }
 
@@ -530,10 +592,10 @@ void setup_eigs(Ctx &c) {
          ee, g);
   double *Lscr = c.ws.dbl((size_t)3 * n * n);
   double *Uscr = c.ws.dbl((size_t)3 * n * n);
-  // kEigBlock eigenpairs per block (a warp or part of one) spread the 3n
-  // eigenpairs over all SMs; each thread's time is its eigenpair's chain of
-  // dependent FP64 recurrences
-  dim3 geig((n + kEigBlock - 1) / kEigBlock, 3);
+  // kEigBlock / 2 eigenpairs per block (a warp or part of one) spread the 3n
+  // eigenpairs over all SMs; each pair of lanes' time is its eigenpair's chain
+  // of dependent FP64 recurrences
+  dim3 geig((2 * n + kEigBlock - 1) / kEigBlock, 3);
   const auto tb0 = std::chrono::steady_clock::now();
   LAUNCH(c, eig_rqi_kernel, geig, kEigBlock, 0, n, c.d[0], c.d[1], c.d[2], c.e[0], c.e[1], c.e[2], ee, d32,
          ee32, g, bounds, c.lam[0], c.lam[1], c.lam[2], c.V[0], c.V[1], c.V[2], Lscr, Uscr,
