@@ -526,13 +526,20 @@ def _pipe_peaks():
 # of one n = 2048 solve traced alone (profiles/dram_rank_structured_n2048_single_solve.md),
 # keyed by kernel; a kernel missing here has no capture of its current code
 TRAFFIC_PER_LAUNCH = {
-    "rowdot_group_kernel": 48142507,
-    "khatri_rao_kernel": 189594,
-    "contract_b_kernel": 18571193,
-    "ttm3_kernel": 217792,
-    "skinny_nn_kernel": 45234534,
-    "skinny_tn_kernel": 33656832,
-    "core_proj_kernel": 632768,
+    "dgemm_group_kernel": 1250863,
+    "tcg_group_kernel": 69086451,
+    "tcg_kernel": 29128892,
+    "split_group_kernel": 13568216,
+    "split_kernel": 7716070,
+    "row_exp_group_kernel": 2323766,
+    "row_exp_kernel": 5858475,
+    "rowdot_group_kernel": 48150699,
+    "contract_b_kernel": 18570169,
+    "ttm3_kernel": 216869,
+    "core_proj_kernel": 631808,
+    "tcg_reduce_group_kernel": 13552423,
+    "trsm_rows_multi_kernel": 1116879,
+    "splitk_reduce_group": 239608,
 }
 
 
