@@ -528,7 +528,6 @@ def _pipe_peaks():
 TRAFFIC_PER_LAUNCH = {
     "dgemm_group_kernel": 1250863,
     "tcg_group_kernel": 69086451,
-    "tcg_kernel": 29128892,
     "split_group_kernel": 13568216,
     "split_kernel": 7716070,
     "row_exp_group_kernel": 2323766,

@@ -950,6 +950,59 @@ struct EigDesc {
   int m;
 };
 
+// The rotation parameters are one warp's chain of dependent FP64 operations
+// per step (a warp instruction of the FP64 pipe costs tens of cycles on this
+// part): divisions and square roots are taken as the hardware approximations
+// refined by Newton steps (r <- r + r (1 - q r) for 1/q; y <- y + y (1 - q y^2) / 2
+// for 1/sqrt(q); each doubles the correct bits), a few dependent operations
+// each instead of a long correctly rounded sequence. The rotation stays
+// orthogonal to rounding level (c = 1/sqrt(1 + t^2) to a few ulp, s = t c).
+__device__ __forceinline__ double jac_rcp(double q) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(q));
+  double e = fma(-q, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-q, r, 1.0);
+  return fma(r, e, r);
+}
+
+__device__ __forceinline__ double jac_rsqrt(double q) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(q));
+  double hy = 0.5 * y;
+  double e = fma(-q * y, y, 1.0);
+  y = fma(hy, e, y);
+  hy = 0.5 * y;
+  e = fma(-q * y, y, 1.0);
+  return fma(hy, e, y);
+}
+
+// Rotate the pair when a_pq^2 is above the absolute floor and |a_pq| above
+// 1e-15 sqrt(|a_pp a_qq|) (compared squared: no square root).
+__device__ __forceinline__ bool jac_rotates(double app, double aqq, double apq, double abs_floor) {
+  const double a2 = apq * apq;
+  return a2 > abs_floor && a2 > 1e-30 * fabs(app * aqq);
+}
+
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / (2 a_pq);
+// c = 1 / sqrt(1 + t^2), s = t c. For |tau| > 2^64, tau^2 would lose the 1:
+// t = 1 / (2 tau) there.
+__device__ __forceinline__ void jac_rotation(double app, double aqq, double apq, double &t, double &c,
+                                             double &s) {
+  const double tau = (aqq - app) * jac_rcp(2.0 * apq);
+  const double at = fabs(tau);
+  double ta;
+  if (at > 1.8446744073709552e19) {
+    ta = 0.5 * jac_rcp(at);
+  } else {
+    const double q = fma(tau, tau, 1.0);
+    ta = jac_rcp(at + q * jac_rsqrt(q));
+  }
+  t = tau >= 0.0 ? ta : -ta;
+  c = jac_rsqrt(fma(t, t, 1.0));
+  s = t * c;
+}
+
 __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__ desc) {
   extern __shared__ double sm[];
   const EigDesc dsc = desc[blockIdx.x];
@@ -993,11 +1046,8 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__
         if (p > q) { const int tmp = p; p = q; q = tmp; }
         const double app = A[p + p * ld], aqq = A[q + q * ld], apq = A[p + q * ld];
         double cc = 1.0, sn = 0.0, tt = 0.0;
-        if (apq * apq > abs_floor && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          cc = 1.0 / sqrt(1.0 + tt * tt);
-          sn = tt * cc;
+        if (jac_rotates(app, aqq, apq, abs_floor)) {
+          jac_rotation(app, aqq, apq, tt, cc, sn);
           nrot = 1;
         }
         rc[t] = cc;
@@ -1061,9 +1111,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__
     for (int u = threadIdx.x; u < m * m; u += blockDim.x) {
       const int i = u % m, j = u / m;
       if (i >= j) continue;
-      const double apq = A[i + j * ld];
-      if (apq * apq > abs_floor && fabs(apq) > 1e-15 * sqrt(fabs(A[i + i * ld] * A[j + j * ld])))
-        more = 1;
+      if (jac_rotates(A[i + i * ld], A[j + j * ld], A[i + j * ld], abs_floor)) more = 1;
     }
     __syncthreads();
     if (more == 0) break;

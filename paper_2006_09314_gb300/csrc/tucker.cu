@@ -1099,12 +1099,39 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
     const int kc = (int)std::max<long long>(1, std::min<long long>(R, (48ll << 20) / per));
     double *T1 = c.ws.dbl((size_t)s1 * kc), *T2 = c.ws.dbl((size_t)s2 * kc),
            *T3 = c.ws.dbl((size_t)s3 * kc);
+    // On the tensor cores T2 is written with the term next to the contracted
+    // index, T2'[(a, c'), (b, k)], so that T3 and the weighted sum over the terms
+    // are one GEMM contracted over (b, k) (K = r1 nk instead of r1), with the
+    // weights folded into a scaled copy of M_1: nc[a, b', c'] += sum_(b,k)
+    // T2'[(a, c'), (b, k)] w_k M_1k[b', b].
+    const bool fused = c.o.tc_gemm && gemm_tc_fits(rn[0] * r[1], rn[2], r[2], kc) &&
+                       gemm_tc_fits(rn[0] * rn[2], rn[1], r[1] * kc, 1);
+    double *M1w = nullptr;
+    if (fused) {
+      M1w = c.ws.dbl((size_t)rn[1] * r[1] * R);
+      copy_d(c, M1w, M[1], (size_t)rn[1] * r[1] * R);
+      scale_cols(c, rn[1] * r[1], R, M1w, rn[1] * r[1], D.w, false);
+    }
     for (int k0 = 0; k0 < R; k0 += kc) {
       const int nk = std::min(kc, R - k0);
       // T1[k] = M_0k (rn0 x r0) * core (r0 x r1 r2)
       gemm_x(c, c.digits, false, false, rn[0], r[1] * r[2], r[0], 1.0,
              M[0] + (size_t)rn[0] * r[0] * k0, rn[0], (long long)rn[0] * r[0], x.core, r[0], 0, 0.0,
              T1, rn[0], s1, nk);
+      if (fused) {
+        // T2'[(a + rn0 c') + rn0 rn2 (b + r1 k)] = sum_c T1[k](a, b, c) M_2k(c', c)
+        const TcOpnd A{T1, 1, 0, (long long)rn[0] * r[1], s1, 1 << 30};
+        const TcOpnd B{M[2] + (size_t)rn[2] * r[2] * k0, 1, 0, (long long)rn[2], (long long)rn[2] * r[2],
+                       1 << 30};
+        gemm_tc(c, c.digits, rn[0] * r[1], rn[2], r[2], nk, 1, 1, 1.0, A, B, 0.0, T2, 1,
+                (long long)rn[0] * rn[2], rn[0], rn[0], s2);
+        // nc[a + rn0 b' + rn0 rn1 c'] (+)= sum_(b,k) T2'[(a, c'), (b, k)] M1w[b' + rn1 (b + r1 k)]
+        const TcOpnd A3{T2, 1, 0, (long long)rn[0] * rn[2], 0, 1 << 30};
+        const TcOpnd B3{M1w + (size_t)rn[1] * r[1] * k0, 1, 0, (long long)rn[1], 0, 1 << 30};
+        gemm_tc(c, c.digits, rn[0] * rn[2], rn[1], r[1] * nk, 1, 1, 1, 1.0, A3, B3, k0 == 0 ? 0.0 : 1.0,
+                nc, 1, (long long)rn[0] * rn[1], rn[0], rn[0], 0);
+        continue;
+      }
       // T2[k] = T1[k] (rn0 r1 x r2) * M_2k^T (r2 x rn2)
       gemm_x(c, c.digits, false, true, rn[0] * r[1], rn[2], r[2], 1.0, T1, rn[0] * r[1], s1,
              M[2] + (size_t)rn[2] * r[2] * k0, rn[2], (long long)rn[2] * r[2], 0.0, T2, rn[0] * r[1],

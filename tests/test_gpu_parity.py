@@ -171,6 +171,29 @@ def test_apply_op_matches_oracle(n, alpha, beta):
     assert np.linalg.norm(Yg - exact) <= 1.2e-6 * nrm
 
 
+def test_apply_op_high_rank_core_projection_chain():
+    """A rank-36 canonical input whose factors lie in the span of the first 30
+    eigenvectors of each mode: in the eigenbasis F2 .* X then has Tucker ranks
+    <= 30 (no rank cap binds), while the core projection's FP64 work per
+    operator term (~8e4 FMAs) is above the fused kernel's limit, so the GEMM
+    chain runs, with T3 and the weighted sum over the terms in one tensor-core
+    GEMM contracted over (b, k). Element-wise against the oracle's exact
+    spectral apply."""
+    n, alpha, beta, rank, span = 192, 0.5, 1e-2, 36, 30
+    pr = make_problem(n, alpha, beta, 3, 777)
+    rng = np.random.default_rng(777)
+    lams, Vs = _oracle_eigs(pr)
+    w = rng.standard_normal(rank)
+    U = [Vs[l][:, :span] @ rng.standard_normal((span, rank)) for l in range(3)]
+    S = fg.spectral_sum(lams)
+    X = F.cp_full(w, U)
+    exact = fg.apply_spectral(fg.F2(S, alpha, beta), X, Vs)
+    with T.Context(pr.coeffs, n, alpha, beta, 1e-6) as ctx:
+        y = ctx.apply_op(T.CP.from_numpy(w, U))
+    Yg = _full_from_gpu(y)
+    assert np.linalg.norm(Yg - exact) <= 1.5e-6 * np.linalg.norm(exact)
+
+
 def _expsum_on_grid(t, w, m, lams):
     """Value of the separable sum on every eigenvalue triple (i, j, k) of the grid."""
     L = [np.asarray(l) for l in lams]
