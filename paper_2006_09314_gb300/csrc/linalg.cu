@@ -1003,30 +1003,75 @@ __device__ __forceinline__ void jac_rotation(double app, double aqq, double apq,
   s = t * c;
 }
 
-__global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__ desc) {
+// One symmetric eigenproblem per thread-block cluster of kJacCluster CTAs
+// (parallel-order Jacobi with exact 2x2 block updates). Every CTA keeps a
+// replica of A and computes all rotation parameters of a step from it (the
+// same operations on the same values); the 2x2 block updates of the step are
+// dealt out over the CTAs, each writing its blocks into all replicas through
+// distributed shared memory; each CTA owns a quarter of V's rows, whose
+// updates need nothing from the others. Two cluster barriers per step: after
+// the parameters (all pivots read before any replica changes) and after the
+// updates (every replica complete before the next parameters).
+// The sweep-exit tests are taken from rank 0's flags by every CTA, so all
+// CTAs run the same sequence of barriers whatever their replicas hold.
+constexpr int kJacCluster = 4;
+
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of this CTA's shared variable p as held by CTA `rank`
+__device__ __forceinline__ uint32_t cl_map(const void *p, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_st(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ int cl_ld(uint32_t addr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+__global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(256)
+    jacobi_kernel(const EigDesc *__restrict__ desc) {
   extern __shared__ double sm[];
-  const EigDesc dsc = desc[blockIdx.x];
+  const int crank = (int)cl_rank();
+  const EigDesc dsc = desc[blockIdx.x / kJacCluster];
   const int m = dsc.m;
   const int mp = (m + 1) & ~1;
   const int ld = mp + 1;
   const int half = mp / 2;
-  double *A = sm;               // mp x ld
-  double *V = A + mp * ld;      // mp x ld
-  double *rc = V + mp * ld;     // half: c
+  const int vr = (mp + kJacCluster - 1) / kJacCluster;  // rows of V per CTA
+  const int v0 = crank * vr, v1 = min(mp, v0 + vr);
+  double *A = sm;               // mp x ld, replica
+  double *V = A + mp * ld;      // rows v0..v1 of V, row-major: V[(i - v0) * ld + j]
+  double *rc = V + vr * ld;     // half: c
   double *rs = rc + half;       // half: s
   double *rt = rs + half;       // half: t (0: no rotation)
   int *rp = reinterpret_cast<int *>(rt + half);  // half: p
   int *rq = rp + half;                           // half: q
   __shared__ double red[8];
-  __shared__ int nrot, more;
+  __shared__ int nrot, more, flag;
   const double *Ab = dsc.A;
   double ss = 0.0;
   for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
     const int i = t % mp, j = t / mp;
     const double v = (i < m && j < m) ? Ab[i + j * m] : 0.0;
     A[i + j * ld] = v;
-    V[i + j * ld] = (i == j) ? 1.0 : 0.0;
     ss = fma(v, v, ss);
+  }
+  for (int t = threadIdx.x; t < (v1 - v0) * mp; t += blockDim.x) {
+    const int i = v0 + t / mp, j = t % mp;
+    V[(i - v0) * ld + j] = (i == j) ? 1.0 : 0.0;
   }
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
@@ -1034,6 +1079,11 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__
   double tot = 0.0;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
   const double abs_floor = 1e-36 * tot;  // |a_pq|^2 below this: no rotation
+  uint32_t abase[kJacCluster];
+#pragma unroll
+  for (int r = 0; r < kJacCluster; ++r) abase[r] = cl_map(A, (uint32_t)r);
+  const uint32_t nrot0 = cl_map(&nrot, 0), more0 = cl_map(&more, 0);
+  cl_sync();  // every replica is initialised before any remote write
   for (int sweep = 0; sweep < 40 && mp > 1; ++sweep) {
     if (threadIdx.x == 0) nrot = 0;
     __syncthreads();
@@ -1056,9 +1106,11 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__
         rp[t] = p;
         rq[t] = q;
       }
-      __syncthreads();
-      // 2 x 2 blocks (a, b), a <= b, of J^T A J
-      for (int u = threadIdx.x; u < half * half; u += blockDim.x) {
+      cl_sync();  // every CTA has read the step's pivots before any replica changes
+      // this CTA's 2 x 2 blocks (a, b), a <= b, of J^T A J, into every replica
+      for (int w = threadIdx.x;; w += blockDim.x) {
+        const int u = crank + kJacCluster * w;
+        if (u >= half * half) break;
         const int a = u % half, b = u / half;
         if (a > b) continue;
         const double ta = rt[a], tb = rt[b];
@@ -1066,10 +1118,14 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__
         const int pa = rp[a], qa = rq[a];
         if (a == b) {
           const double apq = A[pa + qa * ld];
-          A[pa + pa * ld] -= ta * apq;
-          A[qa + qa * ld] += ta * apq;
-          A[pa + qa * ld] = 0.0;
-          A[qa + pa * ld] = 0.0;
+          const double vpp = A[pa + pa * ld] - ta * apq, vqq = A[qa + qa * ld] + ta * apq;
+#pragma unroll
+          for (int r = 0; r < kJacCluster; ++r) {
+            cl_st(abase[r] + 8u * (uint32_t)(pa + pa * ld), vpp);
+            cl_st(abase[r] + 8u * (uint32_t)(qa + qa * ld), vqq);
+            cl_st(abase[r] + 8u * (uint32_t)(pa + qa * ld), 0.0);
+            cl_st(abase[r] + 8u * (uint32_t)(qa + pa * ld), 0.0);
+          }
           continue;
         }
         const int pb = rp[b], qb = rq[b];
@@ -1080,32 +1136,41 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__
         const double l10 = sa * b00 + ca * b10, l11 = sa * b01 + ca * b11;
         const double n00 = l00 * cb - l01 * sb, n01 = l00 * sb + l01 * cb;
         const double n10 = l10 * cb - l11 * sb, n11 = l10 * sb + l11 * cb;
-        A[pa + pb * ld] = n00;
-        A[pa + qb * ld] = n01;
-        A[qa + pb * ld] = n10;
-        A[qa + qb * ld] = n11;
-        A[pb + pa * ld] = n00;
-        A[qb + pa * ld] = n01;
-        A[pb + qa * ld] = n10;
-        A[qb + qa * ld] = n11;
+#pragma unroll
+        for (int r = 0; r < kJacCluster; ++r) {
+          const uint32_t B0 = abase[r];
+          cl_st(B0 + 8u * (uint32_t)(pa + pb * ld), n00);
+          cl_st(B0 + 8u * (uint32_t)(pa + qb * ld), n01);
+          cl_st(B0 + 8u * (uint32_t)(qa + pb * ld), n10);
+          cl_st(B0 + 8u * (uint32_t)(qa + qb * ld), n11);
+          cl_st(B0 + 8u * (uint32_t)(pb + pa * ld), n00);
+          cl_st(B0 + 8u * (uint32_t)(qb + pa * ld), n01);
+          cl_st(B0 + 8u * (uint32_t)(pb + qa * ld), n10);
+          cl_st(B0 + 8u * (uint32_t)(qb + qa * ld), n11);
+        }
       }
-      // columns p, q of V
-      for (int u = threadIdx.x; u < half * mp; u += blockDim.x) {
+      // columns p, q of this CTA's rows of V
+      const int nv = v1 - v0;
+      for (int u = threadIdx.x; u < half * nv; u += blockDim.x) {
         const int a = u % half, i = u / half;
         if (rt[a] == 0.0) continue;
         const double cc = rc[a], sn = rs[a];
         const int p = rp[a], q = rq[a];
-        const double vp = V[i + p * ld], vq = V[i + q * ld];
-        V[i + p * ld] = cc * vp - sn * vq;
-        V[i + q * ld] = sn * vp + cc * vq;
+        double *row = V + i * ld;
+        const double vp = row[p], vq = row[q];
+        row[p] = cc * vp - sn * vq;
+        row[q] = sn * vp + cc * vq;
       }
-      __syncthreads();
+      cl_sync();  // every replica holds the step's blocks before the next parameters
     }
-    if (nrot == 0) break;
-    // Would the next sweep rotate anything? A pair's test reads only entries
-    // that nothing but rotations change, so a sweep without rotations is
-    // exactly the case where no pair passes the test now: checking every pair
-    // once replaces that confirming sweep (same result, 1/(mp-1) of its work).
+    // Rank 0's flags decide for the whole cluster. Would the next sweep rotate
+    // anything? A pair's test reads only entries that nothing but rotations
+    // change, so a sweep without rotations is exactly the case where no pair
+    // passes the test now: checking every pair once replaces that confirming
+    // sweep (same result, 1/(mp-1) of its work).
+    if (threadIdx.x == 0) flag = cl_ld(nrot0);
+    cl_sync();  // read by every CTA before rank 0 resets it
+    if (flag == 0) break;
     if (threadIdx.x == 0) more = 0;
     __syncthreads();
     for (int u = threadIdx.x; u < m * m; u += blockDim.x) {
@@ -1113,11 +1178,14 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__
       if (i >= j) continue;
       if (jac_rotates(A[i + i * ld], A[j + j * ld], A[i + j * ld], abs_floor)) more = 1;
     }
-    __syncthreads();
-    if (more == 0) break;
-    __syncthreads();  // nrot and more are reset at the top of the next sweep
+    cl_sync();  // rank 0's flag is final
+    if (threadIdx.x == 0) flag = cl_ld(more0);
+    cl_sync();  // read by every CTA before the next sweep resets the flags
+    if (flag == 0) break;
   }
-  // sort eigenvalues descending (selection by rank, m <= 64)
+  cl_sync();  // no remote access to this CTA's shared memory after here
+  // sort eigenvalues descending (selection by rank, m <= 64); this CTA writes
+  // its rows of each eigenvector
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     const double di = A[i + i * ld];
     int rank = 0;
@@ -1125,8 +1193,8 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EigDesc *__restrict__
       const double dj = A[j + j * ld];
       rank += (dj > di) || (dj == di && j < i);
     }
-    dsc.lam[rank] = di;
-    for (int r = 0; r < m; ++r) dsc.V[r + (long long)rank * m] = V[r + i * ld];
+    if (crank == 0) dsc.lam[rank] = di;
+    for (int r = v0; r < min(v1, m); ++r) dsc.V[r + (long long)rank * m] = V[(r - v0) * ld + i];
   }
 }
 
@@ -1139,7 +1207,8 @@ static void jacobi_launch(Ctx &c, const std::vector<EigDesc> &d) {
   }
   if (mmax <= 0) return;
   const int mp = (mmax + 1) & ~1;
-  const size_t smem = sizeof(double) * (2 * mp * (mp + 1) + 3 * (mp / 2)) + sizeof(int) * mp;
+  const int vr = (mp + kJacCluster - 1) / kJacCluster;
+  const size_t smem = sizeof(double) * ((size_t)(mp + vr) * (mp + 1) + 3 * (mp / 2)) + sizeof(int) * mp;
   // set once per process, thread-safely (function-local static initialisation)
   static const cudaError_t attr =
       cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -1147,7 +1216,7 @@ static void jacobi_launch(Ctx &c, const std::vector<EigDesc> &d) {
   size_t mk = c.ws.mark();
   EigDesc *dd = static_cast<EigDesc *>(c.ws.alloc(sizeof(EigDesc) * d.size()));
   TCTL_CUDA(cudaMemcpyAsync(dd, d.data(), sizeof(EigDesc) * d.size(), cudaMemcpyHostToDevice, c.st));
-  LAUNCH(c, jacobi_kernel, (int)d.size(), 256, smem, dd);
+  LAUNCH(c, jacobi_kernel, (int)d.size() * kJacCluster, 256, smem, dd);
   // the descriptor buffer must outlive the (asynchronous) launch
   TCTL_CUDA(cudaStreamSynchronize(c.st));
   c.ws.reset(mk);
