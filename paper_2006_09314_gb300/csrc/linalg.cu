@@ -1009,9 +1009,9 @@ __device__ __forceinline__ void jac_rotation(double app, double aqq, double apq,
 // same operations on the same values); the 2x2 block updates of the step are
 // dealt out over the CTAs, each writing its blocks into all replicas through
 // distributed shared memory; each CTA owns a quarter of V's rows, whose
-// updates need nothing from the others. Two cluster barriers per step: after
-// the parameters (all pivots read before any replica changes) and after the
-// updates (every replica complete before the next parameters).
+// updates need nothing from the others. The diagonal blocks are rotated by
+// every CTA in its own replica, so one cluster barrier per step (every replica
+// complete before the next parameters) suffices.
 // The sweep-exit tests are taken from rank 0's flags by every CTA, so all
 // CTAs run the same sequence of barriers whatever their replicas hold.
 constexpr int kJacCluster = 4;
@@ -1106,28 +1106,33 @@ __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(256)
         rp[t] = p;
         rq[t] = q;
       }
-      cl_sync();  // every CTA has read the step's pivots before any replica changes
-      // this CTA's 2 x 2 blocks (a, b), a <= b, of J^T A J, into every replica
+      __syncthreads();
+      // The diagonal blocks (a, a), the only entries the parameters read, are
+      // rotated by every CTA in its own replica (identical operations on
+      // identical values), so no remote write can meet another CTA still
+      // reading its pivots; the off-diagonal blocks (a, b), a < b, are dealt
+      // out and written into every replica.
+      if (threadIdx.x < half) {
+        const int a = threadIdx.x;
+        const double ta = rt[a];
+        if (ta != 0.0) {
+          const int pa = rp[a], qa = rq[a];
+          const double apq = A[pa + qa * ld];
+          const double vpp = A[pa + pa * ld] - ta * apq, vqq = A[qa + qa * ld] + ta * apq;
+          A[pa + pa * ld] = vpp;
+          A[qa + qa * ld] = vqq;
+          A[pa + qa * ld] = 0.0;
+          A[qa + pa * ld] = 0.0;
+        }
+      }
       for (int w = threadIdx.x;; w += blockDim.x) {
         const int u = crank + kJacCluster * w;
         if (u >= half * half) break;
         const int a = u % half, b = u / half;
-        if (a > b) continue;
+        if (a >= b) continue;
         const double ta = rt[a], tb = rt[b];
         if (ta == 0.0 && tb == 0.0) continue;
         const int pa = rp[a], qa = rq[a];
-        if (a == b) {
-          const double apq = A[pa + qa * ld];
-          const double vpp = A[pa + pa * ld] - ta * apq, vqq = A[qa + qa * ld] + ta * apq;
-#pragma unroll
-          for (int r = 0; r < kJacCluster; ++r) {
-            cl_st(abase[r] + 8u * (uint32_t)(pa + pa * ld), vpp);
-            cl_st(abase[r] + 8u * (uint32_t)(qa + qa * ld), vqq);
-            cl_st(abase[r] + 8u * (uint32_t)(pa + qa * ld), 0.0);
-            cl_st(abase[r] + 8u * (uint32_t)(qa + pa * ld), 0.0);
-          }
-          continue;
-        }
         const int pb = rp[b], qb = rq[b];
         const double ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
         const double b00 = A[pa + pb * ld], b01 = A[pa + qb * ld];
