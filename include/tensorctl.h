@@ -233,7 +233,9 @@ int tctl_fullgrid_state(tctl_ctx *ctx, const double *u, double *y);
  * device-to-host copy of the canonical solution, teardown. coeffs as in
  * tctl_setup; yw (S) and yU (3 x n x S, mode-major, column-major per mode)
  * the canonical y_Omega; uw (cap) and uU (3 x n x cap) receive the solution,
- * *u_rank its rank. Returns the same codes as tctl_pcg_solve. */
+ * *u_rank its rank. Runs on a non-blocking stream of its own, so calls from
+ * several host threads overlap on the GPU. Returns the same codes as
+ * tctl_pcg_solve. */
 int tctl_solve_host(const double *coeffs, int n, double alpha, double beta,
                     double eps_trunc, const tctl_opts *opts, const double *yw,
                     const double *yU, int S, double *uw, double *uU, int cap,

@@ -579,8 +579,22 @@ int tctl_solve_host(const double *coeffs, int n, double alpha, double beta, doub
                     const tctl_opts *opts, const double *yw, const double *yU, int S, double *uw,
                     double *uU, int cap, int *u_rank, tctl_stats *st) {
   if (!yw || !yU || S < 0 || !uw || !uU || cap < 0 || !u_rank) return TCTL_E_ARG;
+  // a stream of its own (non-blocking): concurrent calls from several host
+  // threads overlap on the GPU instead of serialising on the legacy default stream
+  cudaStream_t hs = nullptr;
+  if (cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking) != cudaSuccess) {
+    set_noalloc_error("tctl_solve_host: cudaStreamCreateWithFlags failed");
+    return TCTL_E_CUDA;
+  }
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  } guard{hs};
   tctl_ctx *ctx = nullptr;
-  int s = tctl_setup(&ctx, coeffs, n, alpha, beta, eps_trunc, opts, nullptr);
+  int s = tctl_setup(&ctx, coeffs, n, alpha, beta, eps_trunc, opts, hs);
   if (s != TCTL_OK) return s;
   Ctx *c = reinterpret_cast<Ctx *>(ctx);
   tctl_cp b{}, x{};
