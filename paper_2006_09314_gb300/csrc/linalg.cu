@@ -1256,9 +1256,9 @@ __device__ __forceinline__ void pivchol_body(int m, const double *__restrict__ G
                                              double thr_rel_or_abs, int relative, int rcap,
                                              int *perm_out, double *L_out, int *out_r) {
   __shared__ double G[JMAX][JMAX + 1];
-  __shared__ int used[JMAX], perm[JMAX];
-  __shared__ int piv;
-  __shared__ double thr, dpiv;
+  __shared__ int used[JMAX], perm[JMAX], rem[JMAX];
+  __shared__ int piv, nrem;
+  __shared__ double thr, dpiv, ipiv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int t = tid; t < m * m; t += blockDim.x) G[t % m][t / m] = Gin[t];
   for (int t = tid; t < m; t += blockDim.x) used[t] = 0;
@@ -1289,26 +1289,50 @@ __device__ __forceinline__ void pivchol_body(int m, const double *__restrict__ G
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
       }
+      // every lane holds the same (bv, bi) after the butterfly
+      const bool ok = bi < m && bv > thr && isfinite(bv);
       if (lane == 0) {
-        const bool ok = bi < m && bv > thr && isfinite(bv);
         piv = ok ? bi : -1;
         if (ok) {
           used[bi] = 1;
           perm[j] = bi;
-          dpiv = sqrt(bv);
+          // 1 / sqrt(pivot) as the hardware approximation refined by two Newton
+          // steps (a chain of a few FP64 operations instead of a correctly
+          // rounded square root and one division per column entry)
+          const double y = bv > 1e-300 ? jac_rsqrt(bv) : 1.0 / sqrt(bv);
+          dpiv = bv * y;
+          ipiv = y;
         }
+      }
+      if (ok) {
+        // the indices still to eliminate, in ascending order (ballot compaction)
+        int base = 0;
+        for (int c0 = 0; c0 < m; c0 += 32) {
+          const int i = c0 + lane;
+          const bool u = i < m && i != bi && !used[i];
+          const unsigned bal = __ballot_sync(0xffffffffu, u);
+          if (u) rem[base + __popc(bal & ((1u << lane) - 1u))] = i;
+          base += __popc(bal);
+        }
+        if (lane == 0) nrem = base;
       }
     }
     __syncthreads();
     const int p = piv;
     if (p < 0) break;
-    const double dp = dpiv;
+    const double dp = dpiv, ip = ipiv;
+    const int nr = nrem;
     for (int i = tid; i < m; i += blockDim.x)
-      G[i][p] = (i == p) ? dp : (used[i] ? 0.0 : G[i][p] / dp);
+      G[i][p] = (i == p) ? dp : (used[i] ? 0.0 : G[i][p] * ip);
     __syncthreads();
-    for (int t = tid; t < m * m; t += blockDim.x) {
-      const int i = t % m, k = t / m;
-      if (!used[i] && !used[k]) G[i][k] -= G[i][p] * G[k][p];
+    // Schur complement on the remaining indices: a 16 x 16 thread grid over nr x nr
+    for (int b = tid >> 4; b < nr; b += blockDim.x >> 4) {
+      const int k = rem[b];
+      const double lk = G[k][p];
+      for (int a = tid & 15; a < nr; a += 16) {
+        const int i = rem[a];
+        G[i][k] -= G[i][p] * lk;
+      }
     }
     __syncthreads();
     r = j + 1;
