@@ -149,6 +149,38 @@ def test_truncate_recovers_exact_tucker_rank_and_in_place():
         assert np.linalg.norm(_full_from_gpu(x) - X) <= 1e-11 * np.linalg.norm(X)
 
 
+@pytest.mark.parametrize("case", ["rank1", "equal_weights", "order64"])
+def test_truncate_eigenproblem_edge_cases(case):
+    """Edge cases of the HOSVD's symmetric eigenproblems (Jacobi on 4-CTA
+    clusters): 1 x 1 Grams (an exact rank-1 input), Grams with one repeated
+    eigenvalue that are diagonal from the start (equal-weight orthonormal
+    terms: no rotation at all), and order 64 (the largest)."""
+    rng = np.random.default_rng({"rank1": 11, "equal_weights": 12, "order64": 13}[case])
+    n = 96
+    if case == "rank1":
+        w = np.array([2.5])
+        U = [rng.standard_normal((n, 1)) for _ in range(3)]
+        eps, rmax = 1e-6, 1
+    elif case == "equal_weights":
+        R = 12
+        Q = [np.linalg.qr(rng.standard_normal((n, R)))[0] for _ in range(3)]
+        w = np.full(R, 1.5)
+        U = Q
+        eps, rmax = 1e-6, R
+    else:
+        R = 64
+        w = np.exp(-0.05 * np.arange(R))
+        U = [rng.standard_normal((n, R)) for _ in range(3)]
+        eps, rmax = 1e-7, R
+    X = F.cp_full(w, U)
+    pr = make_problem(n, 0.5, 1e-2, 1, 1)
+    with T.Context(pr.coeffs, n, 0.5, 1e-2, 1e-6) as ctx:
+        y = ctx.truncate(T.CP.from_numpy(w, U), eps)
+    Yg = _full_from_gpu(y)
+    assert np.linalg.norm(Yg - X) <= eps * np.linalg.norm(X)
+    assert y.rank <= rmax * rmax
+
+
 # ------------------------------------------------------------------ applies
 @pytest.mark.parametrize("n,alpha,beta", [(32, 0.5, 1e-2), (29, 0.25, 1e-4), (40, 0.75, 1.0),
                                           (24, 1.0, 1e-2)])
