@@ -534,7 +534,6 @@ TRAFFIC_PER_LAUNCH = {
     "row_exp_kernel": 5858475,
     "rowdot_group_kernel": 48150699,
     "contract_b_kernel": 18570169,
-    "ttm3_kernel": 216869,
     "core_proj_kernel": 631808,
     "tcg_reduce_group_kernel": 13552423,
     "trsm_rows_multi_kernel": 1116879,

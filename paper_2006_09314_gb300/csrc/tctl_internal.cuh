@@ -423,4 +423,34 @@ void set_noalloc_error(const std::string &msg);
 // ------------------------------------------------------------ pcg.cu
 int pcg_solve(Ctx &c, const tctl_cp *b, tctl_cp *x, tctl_stats *st);
 
+
+// Thread-block cluster helpers: this CTA's rank, the shared::cluster address of
+// a shared variable as held by another CTA of the cluster, remote stores and
+// loads, and the cluster-wide barrier (release / acquire).
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of this CTA's shared variable p as held by CTA `rank`
+__device__ __forceinline__ uint32_t cl_map(const void *p, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_st(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ int cl_ld(uint32_t addr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+
 }  // namespace tctl

@@ -245,39 +245,58 @@ struct Ttm3Args {
   double *out;
 };
 
-__global__ void __launch_bounds__(256) ttm3_kernel(Ttm3Args g) {
+// One output slab k per 4-CTA thread-block cluster. CTA c of the cluster takes
+// the columns b in [b0, b1) of S = sum_c M2(k, c) core[:, :, c] (r0 x r1) and
+// of T = A0 S (p0 x r1), and writes its columns of T into every CTA's copy
+// through distributed shared memory; after one cluster barrier it forms the
+// output rows j in [j0, j1) of out = T A1^T (p0 x p1). No work is repeated
+// across the cluster, and a slab's FP64 work runs on four SMs.
+constexpr int kTtmCluster = 4;
+
+__global__ void __cluster_dims__(kTtmCluster, 1, 1) __launch_bounds__(256) ttm3_kernel(Ttm3Args g) {
   extern __shared__ double sm3[];
-  const int k = blockIdx.x;
+  const int crank = (int)cl_rank();
+  const int k = blockIdx.x / kTtmCluster;
   const int r0 = g.r0, r1 = g.r1, r2 = g.r2, p0 = g.p0, p1 = g.p1;
-  double *S = sm3;                 // r0 x r1
-  double *T = S + r0 * r1;         // p0 x r1
-  double *A0 = T + p0 * r1;        // p0 x r0
-  double *A1 = A0 + p0 * r0;       // p1 x r1
+  const int nbq = (r1 + kTtmCluster - 1) / kTtmCluster;
+  const int b0 = min(r1, crank * nbq), b1 = min(r1, b0 + nbq), nb = b1 - b0;
+  const int njq = (p1 + kTtmCluster - 1) / kTtmCluster;
+  const int j0 = min(p1, crank * njq), j1 = min(p1, j0 + njq), nj = j1 - j0;
+  double *T = sm3;                 // p0 x r1 (every CTA: the whole T)
+  double *S = T + p0 * r1;         // r0 x nbq (this CTA's columns)
+  double *A0 = S + r0 * nbq;       // p0 x r0
+  double *A1 = A0 + p0 * r0;       // nj x r1 (this CTA's rows of op(M1))
   auto at = [&](int l, int x, int y) {
     return g.tr[l] ? g.M[l][y + (long long)x * g.ld[l]] : g.M[l][x + (long long)y * g.ld[l]];
   };
   for (int t = threadIdx.x; t < p0 * r0; t += blockDim.x) A0[t] = at(0, t % p0, t / p0);
-  for (int t = threadIdx.x; t < p1 * r1; t += blockDim.x) A1[t] = at(1, t % p1, t / p1);
+  for (int t = threadIdx.x; t < nj * r1; t += blockDim.x) A1[t] = at(1, j0 + t % nj, t / nj);
   const long long slab = (long long)r0 * r1;
-  for (int t = threadIdx.x; t < r0 * r1; t += blockDim.x) {
+  for (int t = threadIdx.x; t < r0 * nb; t += blockDim.x) {
+    const int a = t % r0, b = b0 + t / r0;
     double s = 0.0;
-    for (int c = 0; c < r2; ++c) s = fma(at(2, k, c), g.core[t + c * slab], s);
+    for (int c = 0; c < r2; ++c) s = fma(at(2, k, c), g.core[a + (long long)r0 * b + c * slab], s);
     S[t] = s;
   }
+  uint32_t tb[kTtmCluster];
+#pragma unroll
+  for (int q = 0; q < kTtmCluster; ++q) tb[q] = cl_map(T, (uint32_t)q);
   __syncthreads();
-  for (int t = threadIdx.x; t < p0 * r1; t += blockDim.x) {
-    const int i = t % p0, b = t / p0;
+  for (int t = threadIdx.x; t < p0 * nb; t += blockDim.x) {
+    const int i = t % p0, bl = t / p0;
     double s = 0.0;
-    for (int a = 0; a < r0; ++a) s = fma(A0[i + a * p0], S[a + b * r0], s);
-    T[t] = s;
+    for (int a = 0; a < r0; ++a) s = fma(A0[i + a * p0], S[a + bl * r0], s);
+    const uint32_t off = 8u * (uint32_t)(i + p0 * (b0 + bl));
+#pragma unroll
+    for (int q = 0; q < kTtmCluster; ++q) cl_st(tb[q] + off, s);
   }
-  __syncthreads();
+  cl_sync();  // every CTA holds the whole T; no remote access after this
   double *o = g.out + (long long)p0 * p1 * k;
-  for (int t = threadIdx.x; t < p0 * p1; t += blockDim.x) {
-    const int i = t % p0, j = t / p0;
+  for (int t = threadIdx.x; t < p0 * nj; t += blockDim.x) {
+    const int i = t % p0, jl = t / p0;
     double s = 0.0;
-    for (int b = 0; b < r1; ++b) s = fma(T[i + b * p0], A1[j + b * p1], s);
-    o[t] = s;
+    for (int b = 0; b < r1; ++b) s = fma(T[i + b * p0], A1[jl + b * nj], s);
+    o[i + (long long)p0 * (j0 + jl)] = s;
   }
 }
 
@@ -287,9 +306,11 @@ __global__ void __launch_bounds__(256) ttm3_kernel(Ttm3Args g) {
 // the GEMM route (p0 r1 r2 and p0 p1 r2 doubles).
 void ttm3(Ctx &c, const int r[3], const double *core, double *const M[3], const int ld[3],
           const bool tr[3], const int p[3], double *out, double *t1, double *t2) {
-  const size_t smem = sizeof(double) * ((size_t)r[0] * r[1] + (size_t)p[0] * r[1] + (size_t)p[0] * r[0] +
-                                        (size_t)p[1] * r[1]);
-  if (smem <= 96 * 1024 && p[2] > 0) {
+  const size_t nbq = (size_t)(r[1] + kTtmCluster - 1) / kTtmCluster;
+  const size_t njq = (size_t)(p[1] + kTtmCluster - 1) / kTtmCluster;
+  const size_t smem = sizeof(double) * ((size_t)p[0] * r[1] + (size_t)r[0] * nbq + (size_t)p[0] * r[0] +
+                                        njq * r[1]);
+  if (smem <= 96 * 1024 && p[2] > 0 && r[1] > 0) {
     static const cudaError_t attr =
         cudaFuncSetAttribute(ttm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     TCTL_CUDA(attr);
@@ -298,7 +319,7 @@ void ttm3(Ctx &c, const int r[3], const double *core, double *const M[3], const 
     c.next_flops = 2.0 * p[2] * ((double)r[0] * r[1] * r[2] + (double)p[0] * r[0] * r[1] +
                                  (double)p[0] * p[1] * r[1]);
     c.next_bytes = 8.0 * ((double)r[0] * r[1] * r[2] + (double)p[0] * p[1] * p[2]);
-    LAUNCH(c, ttm3_kernel, p[2], 256, smem, g);
+    LAUNCH(c, ttm3_kernel, p[2] * kTtmCluster, 256, smem, g);
     return;
   }
   int rc[3] = {r[0], r[1], r[2]};
