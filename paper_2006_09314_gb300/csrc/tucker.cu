@@ -1125,7 +1125,12 @@ void sep_apply_trunc(Ctx &c, const Sep &Dc, const Tucker &x, Tucker &y, double e
     // are one GEMM contracted over (b, k) (K = r1 nk instead of r1), with the
     // weights folded into a scaled copy of M_1: nc[a, b', c'] += sum_(b,k)
     // T2'[(a, c'), (b, k)] w_k M_1k[b', b].
-    const bool fused = c.o.tc_gemm && gemm_tc_fits(rn[0] * r[1], rn[2], r[2], kc) &&
+    // Only with 6 digits: one row of the merged GEMM's operands spans every
+    // operator term, whose magnitudes differ by orders, and the digit split
+    // keeps 7D bits below the row's largest; 42 bits hold the small terms'
+    // contributions, the 21 of the three-term split do not (the per-term chain
+    // below splits each term on its own).
+    const bool fused = c.o.tc_gemm && c.digits >= 6 && gemm_tc_fits(rn[0] * r[1], rn[2], r[2], kc) &&
                        gemm_tc_fits(rn[0] * rn[2], rn[1], r[1] * kc, 1);
     double *M1w = nullptr;
     if (fused) {
