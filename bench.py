@@ -539,6 +539,7 @@ TRAFFIC_PER_LAUNCH = {
     "rowdot_group_kernel": 48150699,
     "contract_b_kernel": 18570169,
     "core_proj_kernel": 631808,
+    "ttm3_kernel": 219968,
     "tcg_reduce_group_kernel": 13552423,
     "trsm_rows_multi_kernel": 1116879,
     "splitk_reduce_group": 239608,
