@@ -1014,7 +1014,10 @@ __device__ __forceinline__ void jac_rotation(double app, double aqq, double apq,
 // complete before the next parameters) suffices.
 // The sweep-exit tests are taken from rank 0's flags by every CTA, so all
 // CTAs run the same sequence of barriers whatever their replicas hold.
-constexpr int kJacCluster = 4;
+#ifndef TCTL_JAC_CLUSTER
+#define TCTL_JAC_CLUSTER 4
+#endif
+constexpr int kJacCluster = TCTL_JAC_CLUSTER;  // CTAs per eigenproblem (2, 4 or 8)
 
 __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(256)
     jacobi_kernel(const EigDesc *__restrict__ desc) {
