@@ -35,24 +35,9 @@ constexpr int kMaxRank = 64;
 // bits: the sketches must resolve directions down to the range tolerance, and
 // the core feeds the eps truncation).
 
-__global__ void permute3_kernel(int r0, int r1, int r2, const double *__restrict__ in, int p0,
-                                int p1, int p2, double *__restrict__ out) {
-  // out dims (r[p0], r[p1], r[p2]); out[i_p0, i_p1, i_p2] = in[i0, i1, i2]
-  const long long total = (long long)r0 * r1 * r2;
-  const int r[3] = {r0, r1, r2};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    int idx[3];
-    idx[0] = (int)(t % r0);
-    idx[1] = (int)((t / r0) % r1);
-    idx[2] = (int)(t / ((long long)r0 * r1));
-    const long long o = idx[p0] + (long long)r[p0] * (idx[p1] + (long long)r[p1] * idx[p2]);
-    out[o] = in[t];
-  }
-}
-
 // The mode-2 and mode-3 unfoldings of a core in one pass (and, with o0, a copy):
-// o1 = permute3(in, 1, 0, 2), o2 = permute3(in, 2, 0, 1).
+// for in[a, b, c] (dims r0 x r1 x r2, first index fastest), o1[b, a, c] and
+// o2[c, a, b] (dims r1 x r0 x r2 and r2 x r0 x r1).
 __global__ void unfold3_kernel(int r0, int r1, int r2, const double *__restrict__ in,
                                double *__restrict__ o0, double *__restrict__ o1,
                                double *__restrict__ o2) {
@@ -73,13 +58,6 @@ void unfold3(Ctx &c, const int r[3], const double *in, double *o0, double *o1, d
   const int blocks = (int)std::min<long long>((total + 255) / 256, 2048);
   c.next_bytes = 8.0 * total * (o0 ? 4 : 3);
   LAUNCH(c, unfold3_kernel, blocks, 256, 0, r[0], r[1], r[2], in, o0, o1, o2);
-}
-
-void permute3(Ctx &c, const int r[3], const double *in, int p0, int p1, int p2, double *out) {
-  const long long total = (long long)r[0] * r[1] * r[2];
-  if (!total) return;
-  const int blocks = (int)std::min<long long>((total + 255) / 256, 2048);
-  LAUNCH(c, permute3_kernel, blocks, 256, 0, r[0], r[1], r[2], in, p0, p1, p2, out);
 }
 
 // out[a + ra*(s + ls*k)] = w[k] * sum_b F[(a + ra*b) + ra*rb*(s + ls*k)] * P[(b + rb*s) + rb*ls*k]
