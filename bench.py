@@ -72,6 +72,8 @@ def parse():
                     help="skip the rank-structured solves at n = 256, 512, 1024")
     ap.add_argument("--tune", action="store_true",
                     help="--single only: the tensor-core GEMM autotuner instead of fixed chunks")
+    ap.add_argument("--op-tol", type=float, default=None,
+                    help="target of the fitted F2 exponential sum (default: the library's 1e-8)")
     ap.add_argument("--single", action="store_true",
                     help="one context and one solve per step (alpha = 0.5, beta = 1e-2), for "
                          "profiler captures: one problem's memory, no checks")
@@ -276,7 +278,8 @@ def ours_arm(args, rank, world):
         pool = _pool(len(os.sched_getaffinity(0)))  # spawn: safe after CUDA init
     master = torch.cuda.current_stream()
     streams = [torch.cuda.Stream() for _ in range(B)]
-    ctxs = [T.Context(p.coeffs, n, p.alpha, p.beta, EPS, stream=s.cuda_stream)
+    main_opts = T.tctl_default_opts(op_tol=args.op_tol) if args.op_tol else None
+    ctxs = [T.Context(p.coeffs, n, p.alpha, p.beta, EPS, opts=main_opts, stream=s.cuda_stream)
             for p, s in zip(probs, streams)]
     setup_ms = [c.stats()["t_setup_ms"] for c in ctxs]
     bs = []
