@@ -487,8 +487,9 @@ def ours_arm(args, rank, world):
                                     "products: 6 signed 7-bit BF16 digits per operand (42-bit "
                                     "fixed point under one exponent per row / column), 21 digit "
                                     "products on tcgen05 with FP32 accumulators, exact low levels, "
-                                    "FP64 K-chunk sums; Gram, QR, Jacobi, basis changes, PCG "
-                                    "scalars and residual updates in FP64"),
+                                    "FP64 K-chunk sums; the same split for the boundary basis "
+                                    "changes V_l^T U, V_l Q; Gram, QR, Jacobi, the triple core "
+                                    "products, PCG scalars and residual updates in FP64"),
                    "l2": "flushed between timed steps (256 MB write)",
                    "setup_ms_mean": statistics.mean(setup_ms),
                    "iters": [s["iters"] for s in stats],
