@@ -3,8 +3,9 @@
 // bases by pivoted Cholesky, and elementwise helpers.
 //
 // GB300 executes FP64 at a small fraction of its FP32 rate, so these kernels
-// are arithmetic-bound: shared-memory tiles, register micro-tiles, split-K for
-// tall-skinny reductions (Gram matrices with K = n) so that every SM has work.
+// are arithmetic-bound: exact-work tiles (no FMA spent on padding), split-K for
+// tall-skinny reductions (Gram matrices with K = n) so that every SM has work,
+// and the small eigenproblems spread over thread-block clusters.
 #include <algorithm>
 #include <cstdio>
 #include <cmath>
@@ -421,9 +422,8 @@ void gemm(Ctx &c, bool ta, bool tb, int m, int n, int k, double alpha, const dou
 // (the three modes' Gram matrices and projections of a Tucker step): each
 // item keeps its own shape, pointers and K-split; the launch's CTAs are dealt
 // out to the items in order (item i owns CTAs [cta0_i, cta0_{i+1})), and one
-// grouped reduction adds the split-K partial sums of all items. 32 x 32 tiles:
-// these products have a dimension of at most 64 (ranks), so larger tiles
-// would leave most of their lanes idle.
+// grouped reduction adds the split-K partial sums of all items. Every single
+// (unbatched) FP64 product of the library goes through it as a one-item group.
 constexpr int kGroupMax = 8;
 
 struct GItem {

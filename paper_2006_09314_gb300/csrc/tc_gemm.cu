@@ -22,8 +22,12 @@
 // measured to lose low bits), and levels >= 3 together (their FP32 rounding
 // is ~2^-21 x 2^-20 below the result). Every CTA contracts at most 256 k
 // (KCHUNK), and longer K is split across CTAs whose FP64 partial sums a second
-// kernel adds. The FP64 result is formed in the epilogue from the four FP32
-// accumulators.
+// kernel adds. The epilogue forms the FP64 result from the four FP32
+// accumulators in integer arithmetic: levels 0-2 as exact integers, levels >= 3
+// in units of 2^-35, summed in 64 bits and rounded once to FP64 by assembling
+// its fields (FP64 conversions and adds would run on this part's FP64 pipe, 2
+// per clock per SM). The digit cuts likewise read exponents and significands
+// from the IEEE-754 fields with integer instructions.
 //
 // Layout: the digit planes of A (B) are cut once per GEMM by split_kernel into
 // blocks of TM (TN) rows x 16 k per digit in the K-major core-matrix layout
