@@ -940,7 +940,7 @@ void to_dev(Ctx &c, double *dst, const double *src, size_t count) {
 // mass goes to zero rather than to the rounding level of the diagonal. A pair
 // is left unrotated when |a_pq| <= 1e-15 sqrt(a_pp a_qq) (the relative
 // accuracy threshold of one-sided and two-sided Jacobi, Demmel and Veselic)
-// or |a_pq| <= 1e-18 ||A||_F; the sweeps stop after a sweep without rotations.
+// or |a_pq| <= 1e-16 ||A||_F; the sweeps stop after a sweep without rotations.
 constexpr int JMAX = 64;
 
 struct EigDesc {
@@ -1056,7 +1056,10 @@ __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(256)
   __syncthreads();
   double tot = 0.0;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-  const double abs_floor = 1e-36 * tot;  // |a_pq|^2 below this: no rotation
+  // |a_pq|^2 below this: no rotation. The inputs are FP64 Gram products,
+  // whose entries already carry rounding errors of about 1e-16 ||A||_F, so
+  // annihilating smaller entries adds no accuracy
+  const double abs_floor = 1e-32 * tot;
   uint32_t abase[kJacCluster];
 #pragma unroll
   for (int r = 0; r < kJacCluster; ++r) abase[r] = cl_map(A, (uint32_t)r);
