@@ -938,9 +938,10 @@ void to_dev(Ctx &c, double *dst, const double *src, size_t count) {
 // are set to their exact values (a_pp - t a_pq, a_qq + t a_pq, 0) instead of
 // being recomputed from differences of large numbers, so that the off-diagonal
 // mass goes to zero rather than to the rounding level of the diagonal. A pair
-// is left unrotated when |a_pq| <= 1e-15 sqrt(a_pp a_qq) (the relative
+// is left unrotated when |a_pq| <= about 1e-15 sqrt(a_pp a_qq) (the relative
 // accuracy threshold of one-sided and two-sided Jacobi, Demmel and Veselic)
-// or |a_pq| <= 1e-16 ||A||_F; the sweeps stop after a sweep without rotations.
+// or |a_pq| <= 1e-16 ||A||_F (the rounding level of the FP64 Gram products
+// the kernel is given); the sweeps stop after a sweep without rotations.
 constexpr int JMAX = 64;
 
 struct EigDesc {
@@ -950,55 +951,70 @@ struct EigDesc {
   int m;
 };
 
-// The rotation parameters are one warp's chain of dependent FP64 operations
-// per step (a warp instruction of the FP64 pipe costs tens of cycles on this
-// part): divisions and square roots are taken as the hardware approximations
-// refined by Newton steps (r <- r + r (1 - q r) for 1/q; y <- y + y (1 - q y^2) / 2
-// for 1/sqrt(q); each doubles the correct bits), a few dependent operations
-// each instead of a long correctly rounded sequence. The rotation stays
-// orthogonal to rounding level (c = 1/sqrt(1 + t^2) to a few ulp, s = t c).
+// On this part one warp scheduler issues an FP64 instruction (any number of
+// active lanes) every 64 cycles, and a dependent FP64 operation takes as long,
+// while integer and FP32 operations take a few cycles; the FP64 conversions
+// are FP64-pipe operations too. The rotation parameters are one warp's chain
+// per step, so they are built from as few FP64 instructions as possible: the
+// rotation test is taken on integer words, signs and factors of two are set
+// on the bit patterns, and divisions and square roots are the hardware
+// approximations (relative error below 2^-20, measured over [1, 4) on this
+// part) refined by one third-order step each:
+//   1/q:       r <- r (1 + e + e^2),          e = 1 - q r
+//   1/sqrt(q): y <- y (1 + e/2 + 3 e^2 / 8),  e = 1 - q y^2
+// (error about e^3, below 2^-57, i.e. the result is good to rounding). The
+// rotation stays orthogonal to rounding level (c = 1/sqrt(1 + t^2) to a few
+// ulp, s = t c).
 __device__ __forceinline__ double jac_rcp(double q) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(q));
-  double e = fma(-q, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-q, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-q, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
 __device__ __forceinline__ double jac_rsqrt(double q) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(q));
-  double hy = 0.5 * y;
-  double e = fma(-q * y, y, 1.0);
-  y = fma(hy, e, y);
-  hy = 0.5 * y;
-  e = fma(-q * y, y, 1.0);
-  return fma(hy, e, y);
+  const double e = fma(-q, y * y, 1.0);
+  return fma(y, e * fma(0.375, e, 0.5), y);
 }
 
-// Rotate the pair when a_pq^2 is above the absolute floor and |a_pq| above
-// 1e-15 sqrt(|a_pp a_qq|) (compared squared: no square root).
-__device__ __forceinline__ bool jac_rotates(double app, double aqq, double apq, double abs_floor) {
-  const double a2 = apq * apq;
-  return a2 > abs_floor && a2 > 1e-30 * fabs(app * aqq);
+// -x on the bit pattern (an integer operation)
+__device__ __forceinline__ double jac_neg(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
 }
 
-// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / (2 a_pq);
-// c = 1 / sqrt(1 + t^2), s = t c. For |tau| > 2^64, tau^2 would lose the 1:
-// t = 1 / (2 tau) there.
+// |x| as an integer increasing with |x|: the high word without the sign bit.
+// (mag - (1023 << 20)) / 2^20 is log2|x| to within 0.09 (piecewise linear in
+// the mantissa).
+__device__ __forceinline__ int jac_mag(double x) { return __double2hiint(x) & 0x7fffffff; }
+
+// log2(1e-30) in the units of jac_mag
+constexpr int kJacRelMag = -104498822;
+
+// Rotate the pair when |a_pq| is above the absolute floor (given as its
+// jac_mag) and a_pq^2 above about 1e-30 |a_pp a_qq|; both compared on the
+// integer words (the relative test to within a factor 1.3 on a_pq^2).
+__device__ __forceinline__ bool jac_rotates(double app, double aqq, double apq, int floor_mag) {
+  const int g = jac_mag(apq);
+  return g > floor_mag && 2ll * g > (long long)jac_mag(app) + jac_mag(aqq) + kJacRelMag;
+}
+
+// The rotation that annihilates a_pq: tau2 = (a_qq - a_pp) / a_pq (twice the
+// usual tau), t = sign(tau2) 2 / (|tau2| + sqrt(tau2^2 + 4)) (the root of
+// t^2 + tau2 t - 1 = 0 with |t| <= 1), c = 1 / sqrt(1 + t^2), s = t c. A pair
+// that passes the rotation test has |a_pq| > 1e-16 ||A||_F while
+// |a_qq - a_pp| <= sqrt(2) ||A||_F, so |tau2| < 1.5e16: tau2^2 + 4 neither
+// overflows nor calls for another form. 2 / den is 1 / den with the exponent
+// raised by one (den in [2, 2e16], so 1 / den is a normal number) and the sign
+// of tau2 set on the bit pattern.
 __device__ __forceinline__ void jac_rotation(double app, double aqq, double apq, double &t, double &c,
                                              double &s) {
-  const double tau = (aqq - app) * jac_rcp(2.0 * apq);
-  const double at = fabs(tau);
-  double ta;
-  if (at > 1.8446744073709552e19) {
-    ta = 0.5 * jac_rcp(at);
-  } else {
-    const double q = fma(tau, tau, 1.0);
-    ta = jac_rcp(at + q * jac_rsqrt(q));
-  }
-  t = tau >= 0.0 ? ta : -ta;
+  const double tau2 = (aqq - app) * jac_rcp(apq);
+  const double q4 = fma(tau2, tau2, 4.0);
+  const double r = jac_rcp(fabs(tau2) + q4 * jac_rsqrt(q4));
+  const int hi = (__double2hiint(r) + (1 << 20)) | (__double2hiint(tau2) & (int)0x80000000);
+  t = __hiloint2double(hi, __double2loint(r));
   c = jac_rsqrt(fma(t, t, 1.0));
   s = t * c;
 }
@@ -1011,15 +1027,21 @@ __device__ __forceinline__ void jac_rotation(double app, double aqq, double apq,
 // distributed shared memory; each CTA owns a quarter of V's rows, whose
 // updates need nothing from the others. The diagonal blocks are rotated by
 // every CTA in its own replica, so one cluster barrier per step (every replica
-// complete before the next parameters) suffices.
+// complete before the next parameters) suffices. The step's cost is FP64
+// instructions per warp scheduler: the parameter chain of one warp, then the
+// block and V updates packed onto few warps.
 // The sweep-exit tests are taken from rank 0's flags by every CTA, so all
 // CTAs run the same sequence of barriers whatever their replicas hold.
 #ifndef TCTL_JAC_CLUSTER
 #define TCTL_JAC_CLUSTER 4
 #endif
 constexpr int kJacCluster = TCTL_JAC_CLUSTER;  // CTAs per eigenproblem (2, 4 or 8)
+// off-diagonal blocks one CTA updates at most (m <= JMAX)
+constexpr int kJacOwnMax = ((JMAX / 2) * (JMAX / 2 - 1) / 2 + kJacCluster - 1) / kJacCluster;
+constexpr int kJacThreads = 256;
+static_assert(kJacOwnMax <= kJacThreads, "one lane per block at least");
 
-__global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(256)
+__global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(kJacThreads)
     jacobi_kernel(const EigDesc *__restrict__ desc) {
   extern __shared__ double sm[];
   const int crank = (int)cl_rank();
@@ -1034,11 +1056,24 @@ __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(256)
   double *V = A + mp * ld;      // rows v0..v1 of V, row-major: V[(i - v0) * ld + j]
   double *rc = V + vr * ld;     // half: c
   double *rs = rc + half;       // half: s
-  double *rt = rs + half;       // half: t (0: no rotation)
-  int *rp = reinterpret_cast<int *>(rt + half);  // half: p
+  int *rp = reinterpret_cast<int *>(rs + half);  // half: p
   int *rq = rp + half;                           // half: q
+  int *rf = rq + half;                           // half: 1 if the pair rotates
   __shared__ double red[8];
   __shared__ int nrot, more, flag;
+  // The off-diagonal blocks (a, b), a < b, of pairs a and b this CTA updates:
+  // triangular indices b (b - 1) / 2 + a = crank, crank + kJacCluster, ...,
+  // as a | b << 8.
+  __shared__ int own[kJacOwnMax];
+  const int ntri = half * (half - 1) / 2;
+  const int nown = ntri > crank ? (ntri - crank + kJacCluster - 1) / kJacCluster : 0;
+  for (int k = threadIdx.x; k < nown; k += blockDim.x) {
+    const int kk = crank + kJacCluster * k;
+    int b = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)kk)) * 0.5f);
+    while (b * (b - 1) / 2 > kk) --b;
+    while ((b + 1) * b / 2 <= kk) ++b;
+    own[k] = (kk - b * (b - 1) / 2) | (b << 8);
+  }
   const double *Ab = dsc.A;
   double ss = 0.0;
   for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
@@ -1056,15 +1091,42 @@ __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(256)
   __syncthreads();
   double tot = 0.0;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-  // |a_pq|^2 below this: no rotation. The inputs are FP64 Gram products,
+  // |a_pq| below this: no rotation. The inputs are FP64 Gram products,
   // whose entries already carry rounding errors of about 1e-16 ||A||_F, so
   // annihilating smaller entries adds no accuracy
-  const double abs_floor = 1e-32 * tot;
+  const int floor_mag = jac_mag(1e-16 * sqrt(tot));
   uint32_t abase[kJacCluster];
 #pragma unroll
   for (int r = 0; r < kJacCluster; ++r) abase[r] = cl_map(A, (uint32_t)r);
   const uint32_t nrot0 = cl_map(&nrot, 0), more0 = cl_map(&more, 0);
   cl_sync();  // every replica is initialised before any remote write
+  // Entries (i, j), j in [j0, j0 + nj), of row i of the block (a, b) of
+  // B <- R_a^T B R_b (B = [b00 b01; b10 b11], read before any lane of the
+  // block writes), written into every replica (both triangles).
+  auto block_row = [&](int a, int b, int i, int j0, int nj, double b00, double b01, double b10,
+                       double b11) {
+    const int pa = rp[a], qa = rq[a], pb = rp[b], qb = rq[b];
+    const double ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
+    const double x = i ? sa : ca, z = i ? ca : jac_neg(sa);
+    const double l0 = fma(z, b10, x * b00);
+    const double l1 = fma(z, b11, x * b01);
+    const int row = i ? qa : pa;
+    for (int j = j0; j < j0 + nj; ++j) {
+      const double y = j ? sb : cb, w = j ? cb : jac_neg(sb);
+      const double n = fma(l1, w, l0 * y);
+      const int col = j ? qb : pb;
+#pragma unroll
+      for (int r = 0; r < kJacCluster; ++r) {
+        cl_st(abase[r] + 8u * (uint32_t)(row + col * ld), n);
+        cl_st(abase[r] + 8u * (uint32_t)(col + row * ld), n);
+      }
+    }
+  };
+  // Lanes per block: the blocks are packed onto as few warps as possible
+  // (an FP64 instruction costs a warp scheduler the same for 1 or 32 active
+  // lanes): 4 lanes (one entry each, 6 FP64 operations) while the blocks fit
+  // 32 to a warp, 2 lanes (one row, 8) while they fit 64, else 1 (16).
+  const int lsh = nown <= 32 ? 2 : nown <= 64 ? 1 : 0, lpb = 1 << lsh;
   for (int sweep = 0; sweep < 40 && mp > 1; ++sweep) {
     if (threadIdx.x == 0) nrot = 0;
     __syncthreads();
@@ -1076,70 +1138,67 @@ __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(256)
         int p = at(t), q = at(mp - 1 - t);
         if (p > q) { const int tmp = p; p = q; q = tmp; }
         const double app = A[p + p * ld], aqq = A[q + q * ld], apq = A[p + q * ld];
-        double cc = 1.0, sn = 0.0, tt = 0.0;
-        if (jac_rotates(app, aqq, apq, abs_floor)) {
+        double cc = 1.0, sn = 0.0;
+        const bool rot = jac_rotates(app, aqq, apq, floor_mag);
+        if (rot) {
+          double tt;
           jac_rotation(app, aqq, apq, tt, cc, sn);
           nrot = 1;
+          // The diagonal block (p, q), the only entries the parameters read,
+          // is rotated by every CTA in its own replica (identical operations
+          // on identical values), so no remote write can meet another CTA
+          // still reading its pivots.
+          A[p + p * ld] = fma(-tt, apq, app);
+          A[q + q * ld] = fma(tt, apq, aqq);
+          A[p + q * ld] = 0.0;
+          A[q + p * ld] = 0.0;
         }
         rc[t] = cc;
         rs[t] = sn;
-        rt[t] = tt;
+        rf[t] = rot;
         rp[t] = p;
         rq[t] = q;
       }
       __syncthreads();
-      // The diagonal blocks (a, a), the only entries the parameters read, are
-      // rotated by every CTA in its own replica (identical operations on
-      // identical values), so no remote write can meet another CTA still
-      // reading its pivots; the off-diagonal blocks (a, b), a < b, are dealt
-      // out and written into every replica.
-      if (threadIdx.x < half) {
-        const int a = threadIdx.x;
-        const double ta = rt[a];
-        if (ta != 0.0) {
-          const int pa = rp[a], qa = rq[a];
-          const double apq = A[pa + qa * ld];
-          const double vpp = A[pa + pa * ld] - ta * apq, vqq = A[qa + qa * ld] + ta * apq;
-          A[pa + pa * ld] = vpp;
-          A[qa + qa * ld] = vqq;
-          A[pa + qa * ld] = 0.0;
-          A[qa + pa * ld] = 0.0;
+      // This CTA's off-diagonal blocks (nown * lpb <= blockDim.x lanes, the
+      // lanes of a block in one warp), written into every replica; a block's
+      // lanes read its four entries before any of them writes.
+      {
+        const int e = threadIdx.x;
+        int a = 0, b = 0, j = 0;
+        bool go = false;
+        double b00 = 0.0, b01 = 0.0, b10 = 0.0, b11 = 0.0;
+        if (e < nown * lpb) {
+          const int k = e >> lsh;
+          j = e & (lpb - 1);
+          a = own[k] & 255;
+          b = own[k] >> 8;
+          go = rf[a] || rf[b];
+          if (go) {
+            const int pa = rp[a], qa = rq[a], pb = rp[b], qb = rq[b];
+            b00 = A[pa + pb * ld];
+            b01 = A[pa + qb * ld];
+            b10 = A[qa + pb * ld];
+            b11 = A[qa + qb * ld];
+          }
         }
-      }
-      for (int w = threadIdx.x;; w += blockDim.x) {
-        const int u = crank + kJacCluster * w;
-        if (u >= half * half) break;
-        const int a = u % half, b = u / half;
-        if (a >= b) continue;
-        const double ta = rt[a], tb = rt[b];
-        if (ta == 0.0 && tb == 0.0) continue;
-        const int pa = rp[a], qa = rq[a];
-        const int pb = rp[b], qb = rq[b];
-        const double ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
-        const double b00 = A[pa + pb * ld], b01 = A[pa + qb * ld];
-        const double b10 = A[qa + pb * ld], b11 = A[qa + qb * ld];
-        const double l00 = ca * b00 - sa * b10, l01 = ca * b01 - sa * b11;
-        const double l10 = sa * b00 + ca * b10, l11 = sa * b01 + ca * b11;
-        const double n00 = l00 * cb - l01 * sb, n01 = l00 * sb + l01 * cb;
-        const double n10 = l10 * cb - l11 * sb, n11 = l10 * sb + l11 * cb;
-#pragma unroll
-        for (int r = 0; r < kJacCluster; ++r) {
-          const uint32_t B0 = abase[r];
-          cl_st(B0 + 8u * (uint32_t)(pa + pb * ld), n00);
-          cl_st(B0 + 8u * (uint32_t)(pa + qb * ld), n01);
-          cl_st(B0 + 8u * (uint32_t)(qa + pb * ld), n10);
-          cl_st(B0 + 8u * (uint32_t)(qa + qb * ld), n11);
-          cl_st(B0 + 8u * (uint32_t)(pb + pa * ld), n00);
-          cl_st(B0 + 8u * (uint32_t)(qb + pa * ld), n01);
-          cl_st(B0 + 8u * (uint32_t)(pb + qa * ld), n10);
-          cl_st(B0 + 8u * (uint32_t)(qb + qa * ld), n11);
+        __syncwarp();
+        if (go) {
+          if (lpb == 4) {
+            block_row(a, b, j >> 1, j & 1, 1, b00, b01, b10, b11);
+          } else if (lpb == 2) {
+            block_row(a, b, j, 0, 2, b00, b01, b10, b11);
+          } else {
+            block_row(a, b, 0, 0, 2, b00, b01, b10, b11);
+            block_row(a, b, 1, 0, 2, b00, b01, b10, b11);
+          }
         }
       }
       // columns p, q of this CTA's rows of V
       const int nv = v1 - v0;
       for (int u = threadIdx.x; u < half * nv; u += blockDim.x) {
         const int a = u % half, i = u / half;
-        if (rt[a] == 0.0) continue;
+        if (!rf[a]) continue;
         const double cc = rc[a], sn = rs[a];
         const int p = rp[a], q = rq[a];
         double *row = V + i * ld;
@@ -1162,7 +1221,7 @@ __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(256)
     for (int u = threadIdx.x; u < m * m; u += blockDim.x) {
       const int i = u % m, j = u / m;
       if (i >= j) continue;
-      if (jac_rotates(A[i + i * ld], A[j + j * ld], A[i + j * ld], abs_floor)) more = 1;
+      if (jac_rotates(A[i + i * ld], A[j + j * ld], A[i + j * ld], floor_mag)) more = 1;
     }
     cl_sync();  // rank 0's flag is final
     if (threadIdx.x == 0) flag = cl_ld(more0);
@@ -1194,7 +1253,7 @@ static void jacobi_launch(Ctx &c, const std::vector<EigDesc> &d) {
   if (mmax <= 0) return;
   const int mp = (mmax + 1) & ~1;
   const int vr = (mp + kJacCluster - 1) / kJacCluster;
-  const size_t smem = sizeof(double) * ((size_t)(mp + vr) * (mp + 1) + 3 * (mp / 2)) + sizeof(int) * mp;
+  const size_t smem = sizeof(double) * ((size_t)(mp + vr) * (mp + 1) + 2 * (mp / 2)) + sizeof(int) * 3 * (mp / 2);
   // set once per process, thread-safely (function-local static initialisation)
   static const cudaError_t attr =
       cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -1202,7 +1261,7 @@ static void jacobi_launch(Ctx &c, const std::vector<EigDesc> &d) {
   size_t mk = c.ws.mark();
   EigDesc *dd = static_cast<EigDesc *>(c.ws.alloc(sizeof(EigDesc) * d.size()));
   TCTL_CUDA(cudaMemcpyAsync(dd, d.data(), sizeof(EigDesc) * d.size(), cudaMemcpyHostToDevice, c.st));
-  LAUNCH(c, jacobi_kernel, (int)d.size() * kJacCluster, 256, smem, dd);
+  LAUNCH(c, jacobi_kernel, (int)d.size() * kJacCluster, kJacThreads, smem, dd);
   // the descriptor buffer must outlive the (asynchronous) launch
   TCTL_CUDA(cudaStreamSynchronize(c.st));
   c.ws.reset(mk);
