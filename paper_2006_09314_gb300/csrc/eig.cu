@@ -269,31 +269,41 @@ __global__ void eig_prep_kernel(int n, const double *d0, const double *d1, const
   }
 }
 
-// FP64 reciprocal: the hardware approximation refined by two Newton-Raphson
-// steps r <- r + r (1 - q r), each of which doubles the number of correct bits.
-// The inertia counts need a quotient with a relative error of a few units in
-// the last place, not a correctly rounded one (Kahan's backward-error argument
-// for Sturm counts holds for any operation with a small relative error).
-// |q| >= pivmin > 0 is never subnormal here.
+// On this part a warp scheduler issues one FP64 instruction per 64 cycles
+// (FP64 compares included), so the recurrences below keep the FP64 pipe for
+// their arithmetic: magnitude and sign tests are taken on the bit patterns
+// (a non-negative double orders as its 64-bit pattern), exactly as the FP64
+// compares would decide them.
+__device__ __forceinline__ long long mag_bits(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffll;
+}
+__device__ __forceinline__ bool neg_bit(double x) { return __double_as_longlong(x) < 0; }
+
+// FP64 reciprocal: the hardware approximation (relative error below 2^-20)
+// refined by one third-order step r <- r (1 + e + e^2), e = 1 - q r (error
+// about e^3, below rounding). The inertia counts need a quotient with a
+// relative error of a few units in the last place, not a correctly rounded one
+// (Kahan's backward-error argument for Sturm counts holds for any operation
+// with a small relative error). |q| >= pivmin > 0 is never subnormal here.
 __device__ __forceinline__ double rcp_nr(double q) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(q));
-  double t = fma(-q, r, 1.0);
-  r = fma(r, t, r);
-  t = fma(-q, r, 1.0);
-  return fma(r, t, r);
+  const double t = fma(-q, r, 1.0);
+  return fma(r, fma(t, t, t), r);
 }
 
-// number of eigenvalues below x, FP64 (ee = e^2)
+// number of eigenvalues below x, FP64 (ee = e^2); |q| < pivmin is replaced by
+// -pivmin, so q is never -0 and its sign bit is the test q < 0
 __device__ int count64(int n, const double *__restrict__ d, const double *__restrict__ ee, double x,
                        double pivmin) {
+  const long long pm = mag_bits(pivmin);
   double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  int cnt = q < 0.0;
+  if (mag_bits(q) < pm) q = -pivmin;
+  int cnt = neg_bit(q);
   for (int i = 1; i < n; ++i) {
     q = fma(-ee[i - 1], rcp_nr(q), d[i] - x);
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    if (mag_bits(q) < pm) q = -pivmin;
+    cnt += neg_bit(q);
   }
   return cnt;
 }
@@ -334,8 +344,14 @@ struct Pair {
 
 __device__ __forceinline__ double xchg(const Pair &p, double v) { return __shfl_xor_sync(p.mask, v, 1); }
 __device__ __forceinline__ int xchg(const Pair &p, int v) { return __shfl_xor_sync(p.mask, v, 1); }
+__device__ __forceinline__ long long xchg(const Pair &p, long long v) {
+  return __shfl_xor_sync(p.mask, v, 1);
+}
 
-__device__ __forceinline__ double piv(double q, double pivmin) { return fabs(q) < pivmin ? pivmin : q; }
+// |q| < pivmin is replaced by pivmin (so a pivot is never -0: its sign bit is the test q < 0)
+__device__ __forceinline__ double piv(double q, double pivmin) {
+  return mag_bits(q) < mag_bits(pivmin) ? pivmin : q;
+}
 
 // Twisted factorization of T - sigma I by the pair: side 0 the forward
 // multipliers L_i = e_i / D+_i (to L[i ld]) and the inertia count, side 1 the
@@ -351,14 +367,14 @@ __device__ Twist twisted_pair(const Pair &pr, int n, const double *__restrict__ 
   const int s = pr.side;
   double *Mo = s ? U : L;
   double p = piv(d[s ? n - 1 : 0] - sigma, pivmin);
-  int cnt = p < 0.0;
+  int cnt = neg_bit(p);
   for (int t = 0; t < n - 1; ++t) {
     const int ie = s ? n - 2 - t : t;
     const int id = s ? n - 2 - t : t + 1;
     const double m = e[ie] * rcp_nr(p);
     Mo[(size_t)ie * ld] = m;
     p = piv(fma(-m, e[ie], d[id] - sigma), pivmin);
-    cnt += p < 0.0;
+    cnt += neg_bit(p);
   }
   __syncwarp(pr.mask);  // each lane reads the other's multipliers below
   Twist t;
@@ -369,8 +385,11 @@ __device__ Twist twisted_pair(const Pair &pr, int n, const double *__restrict__ 
   // candidates: side 0 takes i in [0, h), side 1 [h, n)
   const int h = n / 2;
   const int i0 = s ? h : 0, i1 = s ? n : h;
-  double best = 1e308, bgam = 0.0;
+  // |gamma| compared on the bit patterns (exactly as fabs(gam) <= best)
+  long long best = __double_as_longlong(1e308);
+  double bgam = 0.0;
   int br = -1;
+#pragma unroll 4
   for (int i = i0; i < i1; ++i) {
     const double ci = d[i] - sigma;
     double gam;
@@ -381,16 +400,17 @@ __device__ Twist twisted_pair(const Pair &pr, int n, const double *__restrict__ 
       const double dm = piv(fma(-U[(size_t)i * ld], e[i], ci), pivmin);
       gam = dp + dm - ci;
     }
-    if (fabs(gam) <= best) {
-      best = fabs(gam);
+    if (mag_bits(gam) <= best) {
+      best = mag_bits(gam);
       bgam = gam;
       br = i;
     }
   }
   {
-    const double ob = xchg(pr, best), og = xchg(pr, bgam);
+    const long long ob = xchg(pr, best);
+    const double og = xchg(pr, bgam);
     const int orr = xchg(pr, br);
-    const double b0 = s ? ob : best, b1 = s ? best : ob;
+    const long long b0 = s ? ob : best, b1 = s ? best : ob;
     const double g0 = s ? og : bgam, g1 = s ? bgam : og;
     const int r0 = s ? orr : br, r1 = s ? br : orr;
     if (r1 >= 0 && (r0 < 0 || b1 <= b0)) {
@@ -408,6 +428,7 @@ __device__ Twist twisted_pair(const Pair &pr, int n, const double *__restrict__ 
   // ||z||^2
   const int len = s ? n - 1 - t.r : t.r;
   double z = 1.0, acc = 0.0;
+#pragma unroll 4
   for (int q = 0; q < len; ++q) {
     const int i = s ? t.r + q : t.r - 1 - q;
     z = -Mo[(size_t)i * ld] * z;

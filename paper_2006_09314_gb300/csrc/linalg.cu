@@ -1315,31 +1315,40 @@ __device__ __forceinline__ void pivchol_body(int m, const double *__restrict__ G
   __syncthreads();
   int r = 0;
   const int rmax = min(m, rcap);
+  // The pivot search compares bit patterns as integers: a non-negative double
+  // orders as its bit pattern, a negative one (sign bit set) as a negative
+  // integer, below every candidate; the FP64 pipe (one instruction per 64
+  // cycles per warp scheduler on this part) is kept for the arithmetic.
+  const long long thr_bits = __double_as_longlong(thr);
+  constexpr long long kInfBits = 0x7ff0000000000000ll;
+  const long long tiny_bits = __double_as_longlong(1e-300);
   for (int j = 0; j < rmax; ++j) {
     if (warp == 0) {
-      double bv = -1.0;
+      long long bk = -1;
       int bi = m;
       for (int i = lane; i < m; i += 32) {
         if (used[i]) continue;
-        const double d = G[i][i];
-        if (d > bv) { bv = d; bi = i; }  // lanes scan ascending i: ties keep the lower index
+        const long long k = __double_as_longlong(G[i][i]);
+        if (k > bk) { bk = k; bi = i; }  // lanes scan ascending i: ties keep the lower index
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const long long ok_ = __shfl_xor_sync(0xffffffffu, bk, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        if (ok_ > bk || (ok_ == bk && oi < bi)) { bk = ok_; bi = oi; }
       }
-      // every lane holds the same (bv, bi) after the butterfly
-      const bool ok = bi < m && bv > thr && isfinite(bv);
+      // every lane holds the same (bk, bi) after the butterfly; the pivot is
+      // above the threshold and finite
+      const bool ok = bi < m && bk > thr_bits && bk < kInfBits;
       if (lane == 0) {
         piv = ok ? bi : -1;
         if (ok) {
           used[bi] = 1;
           perm[j] = bi;
-          // 1 / sqrt(pivot) as the hardware approximation refined by two Newton
-          // steps (a chain of a few FP64 operations instead of a correctly
+          // 1 / sqrt(pivot) as the hardware approximation refined by one
+          // third-order step (a few FP64 operations instead of a correctly
           // rounded square root and one division per column entry)
-          const double y = bv > 1e-300 ? jac_rsqrt(bv) : 1.0 / sqrt(bv);
+          const double bv = __longlong_as_double(bk);
+          const double y = bk > tiny_bits ? jac_rsqrt(bv) : 1.0 / sqrt(bv);
           dpiv = bv * y;
           ipiv = y;
         }
@@ -1362,17 +1371,25 @@ __device__ __forceinline__ void pivchol_body(int m, const double *__restrict__ G
     if (p < 0) break;
     const double dp = dpiv, ip = ipiv;
     const int nr = nrem;
-    for (int i = tid; i < m; i += blockDim.x)
-      G[i][p] = (i == p) ? dp : (used[i] ? 0.0 : G[i][p] * ip);
+    // The Schur complement is kept in the lower triangle only (entry {i, k}
+    // at G[max][min]); column p of L is written whole into G[.][p] (its slots
+    // above the diagonal belong to no pair, those below to pairs with p,
+    // which are eliminated now).
+    for (int i = tid; i < m; i += blockDim.x) {
+      const double g = G[max(i, p)][min(i, p)];
+      G[i][p] = (i == p) ? dp : (used[i] ? 0.0 : g * ip);
+    }
     __syncthreads();
-    // Schur complement on the remaining indices: a 16 x 16 thread grid over nr x nr
-    for (int b = tid >> 4; b < nr; b += blockDim.x >> 4) {
-      const int k = rem[b];
-      const double lk = G[k][p];
-      for (int a = tid & 15; a < nr; a += 16) {
-        const int i = rem[a];
-        G[i][k] -= G[i][p] * lk;
-      }
+    // Schur complement on the remaining indices: the nr (nr + 1) / 2 pairs
+    // a >= b of rem, t = a (a + 1) / 2 + b, dealt out over the threads
+    const int ntri = nr * (nr + 1) / 2;
+    for (int t = tid; t < ntri; t += blockDim.x) {
+      int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      while (a * (a + 1) / 2 > t) --a;
+      while ((a + 1) * (a + 2) / 2 <= t) ++a;
+      const int i = rem[a], k = rem[t - a * (a + 1) / 2];
+      const int hi = max(i, k), lo = min(i, k);
+      G[hi][lo] = fma(-G[i][p], G[k][p], G[hi][lo]);
     }
     __syncthreads();
     r = j + 1;
