@@ -98,7 +98,10 @@ void sinc_nodes(double g, const SincRule &s, std::vector<double> &t, std::vector
 // before it and contributes one new reflector (O(M P) work, P passive
 // columns), and Q^T b is updated the same way. When coordinates leave the
 // passive set the factorization is rebuilt from the remaining columns, in
-// their order of entry.
+// their order of entry: the reflectors of the columns ahead of the first one
+// that left depend on those columns only, so they are kept (truncate) and
+// only the columns after it are added again (the same operations as a
+// rebuild from scratch, the same result).
 class IncQR {
  public:
   IncQR(const std::vector<double> &A, int M, const std::vector<double> &b)
@@ -110,6 +113,18 @@ class IncQR {
     V_.clear();
     vn_.clear();
     qb_ = b_;
+  }
+
+  // keeps the first P columns of the factorization (Q^T b re-formed from b
+  // by their reflectors, in the order of a rebuild)
+  void truncate(int P) {
+    if (P >= (int)cols_.size()) return;
+    cols_.resize(P);
+    R_.resize(P);
+    V_.resize(P);
+    vn_.resize(P);
+    qb_ = b_;
+    for (int p = 0; p < P; ++p) reflect(p, qb_);
   }
 
   // appends column j of A to the factorization
@@ -216,10 +231,13 @@ std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::
       x[imin] = 0.0;
       for (size_t j = 0; j < cols.size(); ++j)
         if (x[cols[j]] <= 0.0) { passive[cols[j]] = 0; x[cols[j]] = 0.0; }
-      // rebuild the factorization from the columns still passive (order of entry)
-      qr.reset();
-      for (int cj : cols)
-        if (passive[cj]) qr.add(cj);
+      // rebuild the factorization from the columns still passive (order of
+      // entry), keeping the part ahead of the first column that left
+      size_t keep = 0;
+      while (keep < cols.size() && passive[cols[keep]]) ++keep;
+      qr.truncate((int)keep);
+      for (size_t q = keep; q < cols.size(); ++q)
+        if (passive[cols[q]]) qr.add(cols[q]);
       // the entering coordinate left at once: it cannot improve the fit now
       if (imin == jmax && amin == 0.0) { blocked[jmax] = 1; break; }
     }
