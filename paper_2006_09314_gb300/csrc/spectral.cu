@@ -129,9 +129,34 @@ class IncQR {
 
   // appends column j of A to the factorization
   void add(int j) {
-    const int P = (int)cols_.size();
     std::vector<double> c(A_.begin() + (size_t)j * M_, A_.begin() + (size_t)(j + 1) * M_);
-    for (int p = 0; p < P; ++p) reflect(p, c);
+    for (int p = 0; p < (int)cols_.size(); ++p) reflect(p, c);
+    append(j, c);
+  }
+
+  // appends columns js of A in order, as add(js[0]), add(js[1]), ... would:
+  // the reflectors already present are applied to all of them together (each
+  // column's operations in the same order, several independent sums at a
+  // time), then each column in turn takes the reflectors of those before it
+  void add_many(const std::vector<int> &js) {
+    const int P0 = (int)cols_.size(), nq = (int)js.size();
+    std::vector<std::vector<double>> C(nq);
+    for (int q = 0; q < nq; ++q)
+      C[q].assign(A_.begin() + (size_t)js[q] * M_, A_.begin() + (size_t)(js[q] + 1) * M_);
+    for (int q0 = 0; q0 < nq; q0 += 4) {
+      const int qn = std::min(4, nq - q0);
+      for (int p = 0; p < P0; ++p) reflect4(p, C, q0, qn);
+    }
+    for (int q = 0; q < nq; ++q) {
+      for (int p = P0; p < (int)cols_.size(); ++p) reflect(p, C[q]);
+      append(js[q], C[q]);
+    }
+  }
+
+ private:
+  // the new reflector of column j (already reflected by those before it)
+  void append(int j, const std::vector<double> &c) {
+    const int P = (int)cols_.size();
     double nrm = 0;
     for (int i = P; i < M_; ++i) nrm += c[i] * c[i];
     nrm = std::sqrt(nrm);
@@ -153,6 +178,7 @@ class IncQR {
     reflect(P, qb_);
   }
 
+ public:
   // least-squares coefficients of the passive columns (in order of entry)
   std::vector<double> solve() const {
     const int P = (int)cols_.size();
@@ -178,6 +204,26 @@ class IncQR {
     for (int i = p; i < M_; ++i) y[i] -= s * v[i];
   }
 
+  // reflect(p, .) on columns C[q0 .. q0 + qn), qn <= 4, their sums interleaved
+  void reflect4(int p, std::vector<std::vector<double>> &C, int q0, int qn) const {
+    if (vn_[p] == 0) return;
+    const std::vector<double> &v = V_[p];
+    double *y[4];
+    for (int q = 0; q < 4; ++q) y[q] = C[q0 + std::min(q, qn - 1)].data();
+    double s[4] = {0, 0, 0, 0};
+    for (int i = p; i < M_; ++i) {
+      s[0] += v[i] * y[0][i];
+      s[1] += v[i] * y[1][i];
+      s[2] += v[i] * y[2][i];
+      s[3] += v[i] * y[3][i];
+    }
+    for (int q = 0; q < qn; ++q) {
+      const double sq = 2 * s[q] / vn_[p];
+      double *yq = y[q];
+      for (int i = p; i < M_; ++i) yq[i] -= sq * v[i];
+    }
+  }
+
   const std::vector<double> &A_;
   int M_;
   const std::vector<double> &b_;
@@ -197,13 +243,28 @@ std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::
     for (int k = 0; k < K; ++k)
       if (x[k] != 0)
         for (int i = 0; i < M; ++i) res[i] -= A[i + (size_t)k * M] * x[k];
+    // (four duals at a time, each summed in the order of i)
     int jmax = -1;
     double wmax = tol;
-    for (int k = 0; k < K; ++k) {
-      if (passive[k] || blocked[k]) continue;
-      double w = 0;
-      for (int i = 0; i < M; ++i) w += A[i + (size_t)k * M] * res[i];
-      if (w > wmax) { wmax = w; jmax = k; }
+    for (int k0 = 0; k0 < K; k0 += 4) {
+      const double *col[4];
+      bool use[4], any = false;
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + q;
+        use[q] = k < K && !passive[k] && !blocked[k];
+        any = any || use[q];
+        col[q] = A.data() + (size_t)(use[q] ? k : k0) * M;
+      }
+      if (!any) continue;
+      double w[4] = {0, 0, 0, 0};
+      for (int i = 0; i < M; ++i) {
+        w[0] += col[0][i] * res[i];
+        w[1] += col[1][i] * res[i];
+        w[2] += col[2][i] * res[i];
+        w[3] += col[3][i] * res[i];
+      }
+      for (int q = 0; q < 4; ++q)
+        if (use[q] && w[q] > wmax) { wmax = w[q]; jmax = k0 + q; }
     }
     if (jmax < 0) break;
     passive[jmax] = 1;
@@ -236,8 +297,10 @@ std::vector<double> nnls(const std::vector<double> &A, int M, int K, const std::
       size_t keep = 0;
       while (keep < cols.size() && passive[cols[keep]]) ++keep;
       qr.truncate((int)keep);
+      std::vector<int> again;
       for (size_t q = keep; q < cols.size(); ++q)
-        if (passive[cols[q]]) qr.add(cols[q]);
+        if (passive[cols[q]]) again.push_back(cols[q]);
+      qr.add_many(again);
       // the entering coordinate left at once: it cannot improve the fit now
       if (imin == jmax && amin == 0.0) { blocked[jmax] = 1; break; }
     }
